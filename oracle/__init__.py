@@ -1,0 +1,14 @@
+"""CPU oracle (test infrastructure only; see lyap_oracle's docstring)."""
+from .lyap_oracle import (  # noqa: F401
+    param_matrix,
+    lyap_kron,
+    lyap_exact,
+    lyap_bartels_stewart,
+    lyap_solve,
+    trace_product,
+    solve,
+    trace_EX,
+    gradient,
+    check_solution,
+    sweep,
+)

@@ -1,0 +1,22 @@
+"""Seeded synthetic inputs for parametrized Lyapunov sweeps.
+
+This package holds only problem generators (the application models of the
+paper's §3 and the parameter sweeps of its experiments). It contains none of
+the solution method's arithmetic, so both the CPU oracle and the GPU library's
+tests and benchmark can draw their inputs from it.
+"""
+from .generators import (  # noqa: F401
+    Problem,
+    mass_spring_chain,
+    multi_agent,
+    haar_orthogonal,
+    generic_dense,
+    config_rngs,
+    workload_small_fp64,
+    workload_precision,
+    workload_serving_seeds,
+    workload_serving_requests,
+    workload_differentiation,
+    workload_multi_agent,
+    order_nearest_neighbour,
+)

@@ -1,0 +1,310 @@
+"""Synthetic problem generators (paper §3 application models, §4 sweeps).
+
+Every generator returns a :class:`Problem` in the convention used by the
+library and the oracle:
+
+    A(v)^T X + X A(v) = -G G^T,     A(v) = A0 - U diag(v) V^T,
+    f(v) = trace(E X(v)).
+
+The paper writes the same family transposed (§1, eqs. (Ljap jdba 1) and
+(formA)): A_p(v) X + X A_p(v)^T = -Q with A_p = A0^T, B_l = V, B_r = U,
+Q = G G^T. For the damped vibrational system the energy integral of §3.1
+yields the form above directly with A(v) the phase-space matrix of eq.
+(MatrixA).
+
+Nothing here solves a Lyapunov equation; the only linear algebra is the
+modal transformation that defines the application model (eq. (MatrixPhi)).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Problem:
+    """One seed: fixed matrices of a parametrized Lyapunov family.
+
+    Arrays are float64. ``A0`` is n x n, ``U`` and ``V`` are n x k, ``G`` is
+    n x g and ``E`` is n x n (symmetric).
+    """
+
+    name: str
+    A0: np.ndarray
+    U: np.ndarray
+    V: np.ndarray
+    G: np.ndarray
+    E: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.A0.shape[0]
+
+    @property
+    def k(self) -> int:
+        return self.U.shape[1]
+
+    @property
+    def g(self) -> int:
+        return self.G.shape[1]
+
+
+def config_rngs(count: int = 5):
+    """Independent generators per workload: SeedSequence(0) spawned."""
+    return [np.random.default_rng(s) for s in np.random.SeedSequence(0).spawn(count)]
+
+
+def haar_orthogonal(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Haar-distributed orthogonal matrix (QR of a Gaussian, sign-fixed)."""
+    z = rng.standard_normal((n, n))
+    q, r = np.linalg.qr(z)
+    q *= np.sign(np.diag(r))[None, :]
+    return q
+
+
+def generic_dense(p: Problem, rng: np.random.Generator) -> Problem:
+    """Apply an orthogonal similarity S to (A0, U, V, G, E).
+
+    f(v) is unchanged (X -> S X S^T), but the block structure of the modal
+    matrices is hidden, so a solver cannot exploit it.
+    """
+    S = haar_orthogonal(rng, p.n)
+    return Problem(
+        name=p.name + "+dense",
+        A0=S @ p.A0 @ S.T,
+        U=S @ p.U,
+        V=S @ p.V,
+        G=S @ p.G,
+        E=S @ p.E @ S.T,
+        meta=dict(p.meta, similarity="haar"),
+    )
+
+
+def mass_spring_chain(
+    springs,
+    alpha: float,
+    dampers,
+    masses=None,
+    energy_modes: int | None = None,
+) -> Problem:
+    """Damped chain of m masses between two fixed walls (§3.1).
+
+    * ``springs``: m+1 stiffnesses k_0..k_m; spring i joins mass i-1 and i
+      (walls at both ends), so K is tridiagonal.
+    * Internal damping is the critical fraction of eq. (Ccrit), which the
+      modal basis of eq. (MatrixPhi) turns into alpha*Omega.
+    * ``dampers``: 1-based mass indices of grounded external dampers, so
+      B = [e_i1, ..., e_ik] and C_ext(v) = B diag(v) B^T (eq. (Cext)).
+    * State y = [Omega Phi^{-1} x ; Phi^{-1} xdot] (eq. (MatrixA)):
+      A0 = [[0, Omega], [-Omega, -alpha Omega]], U = V = [0 ; Phi^T B].
+    * G = I. E = I, or, with ``energy_modes = s``, the projector onto the
+      first s modal displacements (a reading of eq. (matrix Z)).
+    """
+    springs = np.asarray(springs, dtype=np.float64)
+    m = springs.size - 1
+    if masses is None:
+        masses = np.ones(m)
+    masses = np.asarray(masses, dtype=np.float64)
+    K = np.zeros((m, m))
+    for i in range(m):
+        K[i, i] = springs[i] + springs[i + 1]
+        if i + 1 < m:
+            K[i, i + 1] = K[i + 1, i] = -springs[i + 1]
+    minv_half = 1.0 / np.sqrt(masses)
+    w2, S = np.linalg.eigh(minv_half[:, None] * K * minv_half[None, :])
+    Phi = minv_half[:, None] * S  # Phi^T K Phi = Omega^2, Phi^T M Phi = I
+    omega = np.sqrt(w2)
+    n = 2 * m
+    A0 = np.zeros((n, n))
+    A0[:m, m:] = np.diag(omega)
+    A0[m:, :m] = -np.diag(omega)
+    A0[m:, m:] = -alpha * np.diag(omega)
+    k = len(dampers)
+    B = np.zeros((m, k))
+    for c, d in enumerate(dampers):
+        if not 1 <= d <= m:
+            raise ValueError("damper position out of range")
+        B[d - 1, c] = 1.0
+    U = np.zeros((n, k))
+    U[m:, :] = Phi.T @ B
+    E = np.eye(n)
+    if energy_modes is not None:
+        E = np.zeros((n, n))
+        E[np.arange(energy_modes), np.arange(energy_modes)] = 1.0
+    return Problem(
+        name=f"chain{m}",
+        A0=A0,
+        U=U,
+        V=U.copy(),
+        G=np.eye(n),
+        E=E,
+        meta=dict(omega=omega, alpha=alpha, dampers=list(dampers), masses=m),
+    )
+
+
+def erdos_renyi_edges(rng: np.random.Generator, nodes: int, p: float):
+    iu = np.triu_indices(nodes, 1)
+    keep = rng.random(iu[0].size) < p
+    return np.stack([iu[0][keep], iu[1][keep]], axis=1)
+
+
+def multi_agent(
+    rng: np.random.Generator,
+    agents: int = 256,
+    p: float = 0.05,
+    tunable_edges: int = 8,
+    gain: float = 0.3,
+) -> Problem:
+    """Output-synchronising agents on an Erdos-Renyi graph (§3.2, Ex. 2 data).
+
+    Each agent has state dimension 4, A_agent = blkdiag(Abar, Abar) with
+    Abar = [[-10, 5], [5, -8]], output row c = [1, 1, -1, 1]/2 and gain
+    kappa; B^(i) = c^T, K^(i) = kappa, C^(i) = c, so the coupling block is
+    S = kappa c^T c. ``tunable_edges`` edges of the graph are taken out of
+    the base Laplacian and become the parameters: with
+    u_e = (e_i - e_j) (x) sqrt(kappa) c^T,
+
+        A(w) = I (x) A_agent - L_base (x) S - sum_e w_e u_e u_e^T,
+
+    i.e. A0 = I (x) A_agent - L_base (x) S and U = V = [u_e]. The H2 target
+    of §3.2 is trace(EE^T X) with A^T X + X A = -C^T C, so G = C^T =
+    I (x) c^T and E = I.
+    """
+    Abar = np.array([[-10.0, 5.0], [5.0, -8.0]])
+    A_agent = np.kron(np.eye(2), Abar)
+    c = np.array([[1.0, 1.0, -1.0, 1.0]]) / 2.0
+    S = gain * (c.T @ c)
+    edges = erdos_renyi_edges(rng, agents, p)
+    if edges.shape[0] < tunable_edges:
+        raise ValueError("graph has too few edges")
+    pick = rng.choice(edges.shape[0], tunable_edges, replace=False)
+    tun = edges[np.sort(pick)]
+    base = np.delete(edges, pick, axis=0)
+    L = np.zeros((agents, agents))
+    for i, j in base:
+        L[i, i] += 1
+        L[j, j] += 1
+        L[i, j] -= 1
+        L[j, i] -= 1
+    A0 = np.kron(np.eye(agents), A_agent) - np.kron(L, S)
+    n = 4 * agents
+    U = np.zeros((n, tunable_edges))
+    for col, (i, j) in enumerate(tun):
+        e = np.zeros(agents)
+        e[i] = 1.0
+        e[j] = -1.0
+        U[:, col] = np.kron(e, np.sqrt(gain) * c[0])
+    G = np.kron(np.eye(agents), c.T)
+    return Problem(
+        name=f"agents{agents}",
+        A0=A0,
+        U=U,
+        V=U.copy(),
+        G=G,
+        E=np.eye(n),
+        meta=dict(edges=tun.tolist(), agents=agents, p=p),
+    )
+
+
+def order_nearest_neighbour(vs: np.ndarray) -> np.ndarray:
+    """Greedy nearest-neighbour path through log(v), from the smallest v.
+
+    The recycled solver of §2.1 assumes consecutive parameter vectors vary
+    slowly; this ordering presents a random sweep that way.
+    """
+    lv = np.log(vs)
+    n = lv.shape[0]
+    left = np.ones(n, dtype=bool)
+    cur = int(np.argmin(lv.sum(axis=1)))
+    order = [cur]
+    left[cur] = False
+    for _ in range(n - 1):
+        d = np.where(left, ((lv - lv[cur]) ** 2).sum(axis=1), np.inf)
+        cur = int(np.argmin(d))
+        order.append(cur)
+        left[cur] = False
+    return vs[np.array(order)]
+
+
+def _log_uniform(rng, lo, hi, shape):
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=shape))
+
+
+def workload_small_fp64(dense: bool = False):
+    """50 unit masses (n=100), unit springs, alpha=0.04, dampers at masses
+    10 and 35, G = E = I; v on a linear 10 x 10 grid over [0.1, 10]^2."""
+    rng = config_rngs()[0]
+    p = mass_spring_chain(np.ones(51), 0.04, [10, 35])
+    if dense:
+        p = generic_dense(p, rng)
+    g = np.linspace(0.1, 10.0, 10)
+    vs = np.array([(a, b) for a in g for b in g])
+    return p, vs
+
+
+def workload_precision(dense: bool = True, count: int = 1000, ordered: bool = True):
+    """400 unit masses (n=800), 401 springs U[0.5, 2], alpha=0.04, two dampers
+    at distinct random masses; v log-uniform on [1e-2, 1e2]^2."""
+    rng = config_rngs()[1]
+    springs = rng.uniform(0.5, 2.0, 401)
+    dampers = sorted((rng.choice(400, 2, replace=False) + 1).tolist())
+    p = mass_spring_chain(springs, 0.04, dampers)
+    vs = _log_uniform(rng, 1e-2, 1e2, (count, 2))
+    if dense:
+        p = generic_dense(p, rng)
+    if ordered:
+        vs = order_nearest_neighbour(vs)
+    return p, vs
+
+
+def workload_serving_seeds(dense: bool = True, sizes=(200, 400, 800, 1600)):
+    """Eight seeds: unit-spring chains of 200/400/800/1600 masses, two each,
+    rank k in {2, 3, 4} drawn per seed, dampers at random masses."""
+    rng = config_rngs()[2]
+    seeds = []
+    for m in sizes:
+        for _ in range(2):
+            k = int(rng.integers(2, 5))
+            dampers = sorted((rng.choice(m, k, replace=False) + 1).tolist())
+            p = mass_spring_chain(np.ones(m + 1), 0.04, dampers)
+            if dense:
+                p = generic_dense(p, rng)
+            seeds.append(p)
+    return seeds
+
+
+def workload_serving_requests(seeds, rate_hz: float, count: int, per_request: int = 64, seed: int = 0):
+    """Poisson arrivals: list of (arrival_s, seed_index, v[per_request, k])."""
+    rng = np.random.default_rng(np.random.SeedSequence([0, 3, seed]))
+    t = 0.0
+    out = []
+    for _ in range(count):
+        t += rng.exponential(1.0 / rate_hz)
+        si = int(rng.integers(0, len(seeds)))
+        k = seeds[si].k
+        out.append((t, si, _log_uniform(rng, 0.1, 10.0, (per_request, k))))
+    return out
+
+
+def workload_differentiation(dense: bool = True, count: int = 256):
+    """1000 unit masses (n=2000), unit springs, four dampers at random masses,
+    E = projector on the first 100 modal displacements; v log-uniform on
+    [0.1, 10]^4."""
+    rng = config_rngs()[3]
+    dampers = sorted((rng.choice(1000, 4, replace=False) + 1).tolist())
+    p = mass_spring_chain(np.ones(1001), 0.04, dampers, energy_modes=100)
+    vs = _log_uniform(rng, 0.1, 10.0, (count, 4))
+    if dense:
+        p = generic_dense(p, rng)
+    return p, vs
+
+
+def workload_multi_agent(count: int = 512):
+    """256 agents (n=1024), ER(p=0.05) graph, 8 tunable edge weights,
+    weights uniform on [0.1, 5]."""
+    rng = config_rngs()[4]
+    p = multi_agent(rng)
+    ws = rng.uniform(0.1, 5.0, (count, 8))
+    return p, ws
