@@ -1,0 +1,226 @@
+/*
+ * liblyap: trace(E X(v)) for sequences of parametrized Lyapunov equations on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Palitta, Tomljanovic, Nakic, Saak, "Efficient solution of
+ * sequences of parametrized Lyapunov equations with applications", §1,
+ * eqs. (Ljap jdba 1) and (formA), written in the transposed convention):
+ *
+ *     A(v) = A0 - U diag(v) V^T,     A(v)^T X + X A(v) = -G G^T,
+ *     f(v) = trace(E X(v)),          v in (R \ {0})^k.
+ *
+ * The paper states the same family as A_p X + X A_p^T = -Q with
+ * A_p = A0^T, B_l = V, B_r = U, Q = G G^T; X and f are the same.
+ *
+ * Method (§2.1): A0 is diagonalised once in FP64 (A0^T = Qp Lambda Qp^{-1});
+ * the Sherman-Morrison-Woodbury formula (eq. (deltaX_SMW2)) turns each new v
+ * into a capacitance system with D(v)^{-1} - N^T L0^{-1} M (eq.
+ * (SMW_linearsystem)), solved by a recycled Krylov method (GCRO-DR) across
+ * the sequence; every matvec applies L0^{-1}, i.e. the Cauchy matrix
+ * Lc_ij = 1/(lambda_i + lambda_j) (eq. (Z(v))). f(v) follows from the
+ * additive form of eq. (Xsmalllastline).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are column-major float64 (Fortran order), leading dimension
+ *    equal to the row count.
+ *  - mem_kind: LYAP_MEM_HOST means pointer arguments are host memory (the
+ *    call copies them); LYAP_MEM_DEVICE means device memory on the context's
+ *    GPU, read (or written) in order on opts->stream; the caller keeps
+ *    ownership and must keep the buffers alive until the call returns.
+ *  - Handles (ctx, seed, server) are owned by the library and freed with the
+ *    matching destroy/free call. Output arrays are caller-allocated.
+ *  - Every function returns LYAP_OK (0) or a negative error code; nothing
+ *    aborts, exits or throws across this boundary. Per-result problems
+ *    (no convergence, breakdown, non-finite values) are reported in
+ *    lyap_result_info.status while the call itself returns LYAP_OK.
+ *  - Calls on one context are not thread-safe; use one context per thread.
+ */
+#ifndef LYAP_H
+#define LYAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define LYAP_OK 0
+#define LYAP_PENDING 1           /* serve_poll: request not finished yet       */
+#define LYAP_EINVAL (-1)         /* bad shape/pointer, v_i == 0 (§1), NaN/Inf   */
+#define LYAP_ENOMEM (-2)         /* device allocation failed or over budget    */
+#define LYAP_EUNSTABLE_SEED (-3) /* max Re(lambda) >= 0 or lambda_i+lambda_j ~ 0 */
+#define LYAP_ECUDA (-4)          /* CUDA runtime error                          */
+#define LYAP_ESOLVER (-5)        /* cuSOLVER/cuBLAS failure in the seed factor  */
+#define LYAP_ENOCONV (-6)        /* (per result) maxit reached                  */
+#define LYAP_EBREAKDOWN (-7)     /* (per result) Krylov breakdown               */
+#define LYAP_EDEVICE_TIMEOUT (-8)/* a bounded device-side wait expired          */
+#define LYAP_ENOTFOUND (-9)      /* unknown seed id or ticket                   */
+#define LYAP_ENONFINITE (-10)    /* (per result) NaN/Inf appeared in the solve  */
+#define LYAP_ECANCELLED (-11)    /* request cancelled (serving)                 */
+
+#define LYAP_MEM_HOST 0
+#define LYAP_MEM_DEVICE 1
+
+/* Precision of the capacitance solve.
+ *  LYAP_FP64:    every Krylov step in FP64 (plain path).
+ *  LYAP_BF16_IR: inner Krylov solves in FP32 with the Cauchy-matrix GEMM on
+ *                tcgen05 tensor cores (operands split into two BF16 terms,
+ *                three products, FP32 accumulation), wrapped in iterative
+ *                refinement on the FP64 capacitance residual; the residual,
+ *                the solution update and the trace stay in FP64. */
+#define LYAP_FP64 0
+#define LYAP_BF16_IR 2
+
+/* Fault-injection bits for lyap_opts.inject (host-side only; no GPU fault). */
+#define LYAP_INJECT_ALLOC_FAIL 0x1u   /* next workspace allocation fails     */
+#define LYAP_INJECT_FORCE_MAXIT 0x2u  /* solver stops after one cycle         */
+#define LYAP_INJECT_DEVICE_WAIT 0x4u  /* a device wait flag is never set      */
+
+typedef struct lyap_ctx lyap_ctx;
+typedef struct lyap_seed lyap_seed;
+typedef struct lyap_server lyap_server;
+
+/* Solver options. lyap_opts_default() fills the defaults, which follow the
+ * paper's settings for its first example (§4, Ex. 1): relative residual
+ * threshold 1e-10 tightened to 1e-12 for the FP64 path (the trace is a
+ * linear functional of the capacitance solution and is wanted to 1e-10),
+ * at most 300 iterations, s = 10 recycled vectors. The cycle length m is
+ * not given in the paper; the default is 30. */
+typedef struct {
+  double tol;        /* FP64 path: stop when ||r|| <= tol ||b||               */
+  double refine_tol; /* mixed path: outer stop on the FP64 residual           */
+  double inner_tol;  /* mixed path: inner (FP32) relative residual target     */
+  int maxit;         /* max Krylov iterations per solve                       */
+  int m;             /* cycle length (Arnoldi steps + recycled vectors)       */
+  int s;             /* recycled vectors (harmonic Ritz, smallest |theta|)    */
+  int pbar;          /* rank of the off-diagonal coupling kept in the
+                        preconditioner (eq. (prec)); 0 = block diagonal only */
+  int batch;         /* systems solved in lockstep (0 = library's choice)    */
+  int precision;     /* LYAP_FP64 or LYAP_BF16_IR                              */
+  int max_refine;    /* mixed path: max refinement steps                      */
+  size_t hbm_budget; /* serving: admission budget in bytes (0 = 80% of free)  */
+  void* stream;      /* cudaStream_t to run on (NULL = the context's stream)  */
+  unsigned inject;   /* LYAP_INJECT_* bits (tests only)                       */
+} lyap_opts;
+
+/* Per-result report. */
+typedef struct {
+  int iters;          /* Krylov iterations (inner iterations summed)          */
+  int refine_steps;   /* FP64 residual evaluations (mixed path)               */
+  int status;         /* LYAP_OK, LYAP_ENOCONV, LYAP_EBREAKDOWN, ...          */
+  double rel_resid;   /* final ||b - T(v) w|| / ||b||, evaluated in FP64      */
+  double err_est;     /* estimate of |f - f_exact| / |f| (see lyap_trace_EX)  */
+} lyap_result_info;
+
+/* Seed facts, for reporting. */
+typedef struct {
+  int n, k, g;
+  int real_path;        /* 1 when every eigenvalue is real                    */
+  double cond_Q;        /* ||Qp||_F ||Qp^{-1}||_F                             */
+  double f0;            /* trace(E X0), the seed's own value                 */
+  double max_re_lambda; /* < 0 for an accepted seed                          */
+  double min_abs_lambda_sum; /* min |lambda_i + lambda_j|                     */
+  size_t resident_bytes;/* device bytes held by the seed                      */
+} lyap_seed_stats;
+
+/* Fill *opts with the defaults described above. */
+void lyap_opts_default(lyap_opts* opts);
+
+/* Human-readable name of a status code (static storage). */
+const char* lyap_strerror(int code);
+
+/* Detail of the last error raised on the calling thread (valid until the
+ * thread's next failing call). */
+const char* lyap_last_error(void);
+
+/* Create a context on CUDA device `device` (its own stream and library
+ * handles). Errors: LYAP_EINVAL (bad device), LYAP_ECUDA, LYAP_ESOLVER. */
+int lyap_ctx_create(int device, lyap_ctx** out);
+void lyap_ctx_destroy(lyap_ctx* ctx);
+
+/* Offline seed factorisation and precomputation (§2.1 and its Table 1,
+ * offline column): eig(A0^T) = Qp Lambda Qp^{-1} in FP64, Qp^{-1}, the seed
+ * solution in eigen-coordinates (eqs. (seedLE), (Z(v))), the projected data
+ * Ub = Qp^{-1} V, Vb = Qp^T U, the diagonal blocks of N^T L0^{-1} M
+ * (eq. (N1M1)), the capacitance right-hand side, the trace vectors and
+ * trace(E X0), and (pbar > 0) a truncated SVD of the off-diagonal coupling
+ * for the preconditioner (eq. (prec)).
+ *   A0: n x n; U, V: n x k; G: n x g; E: n x n symmetric, or NULL for I.
+ *   1 <= k <= 16, 1 <= n, k <= n, 1 <= g.
+ * On success *out holds a device-resident seed; *cond_Q_out (may be NULL)
+ * receives ||Qp||_F ||Qp^{-1}||_F.
+ * Errors: LYAP_EINVAL, LYAP_EUNSTABLE_SEED (max Re lambda >= 0, or
+ * min |lambda_i + lambda_j| below 1e-12 max |lambda|, where X is not unique),
+ * LYAP_ENOMEM, LYAP_ESOLVER, LYAP_ECUDA. */
+int lyap_seed_factor(lyap_ctx* ctx, int n, int k, int g, const double* A0, const double* U,
+                     const double* V, const double* G, const double* E, int mem_kind,
+                     const lyap_opts* opts, lyap_seed** out, double* cond_Q_out);
+
+int lyap_seed_stats_get(const lyap_seed* seed, lyap_seed_stats* out);
+
+/* Release a seed (device memory included). */
+int lyap_seed_free(lyap_seed* seed);
+
+/* Solve the capacitance systems of eq. (SMW_linearsystem) for nv parameter
+ * vectors (v: nv x k, row i = v for system i, row-major, i.e. v[i*k + t]).
+ * Systems are solved in the given order, in lockstep batches, recycling the
+ * Krylov subspace across the sequence (§2.1). If w_out is not NULL it
+ * receives, for each v, the shifted capacitance solution W' = W + P D(v) as
+ * n x k complex128 (interleaved re, im; column-major), nv*n*k*2 doubles, in
+ * mem_kind memory. info (may be NULL) receives nv reports (host memory).
+ * Errors: LYAP_EINVAL (v_i == 0 or not finite, bad sizes), LYAP_ENOMEM,
+ * LYAP_ECUDA, LYAP_EDEVICE_TIMEOUT. */
+int lyap_param_solve(lyap_seed* seed, int nv, const double* v, int mem_kind, const lyap_opts* opts,
+                     double* w_out, lyap_result_info* info);
+
+/* f(v) = trace(E X(v)) for nv parameter vectors (eq. (Xsmalllastline) and
+ * the trace formula after it). trace_out: nv doubles in mem_kind memory.
+ * info (may be NULL, host) gets per-result iterations, refinement steps, the
+ * FP64 relative residual and err_est = |h^T r| / |f| with r the final FP64
+ * capacitance residual and h the trace vector (a first-order estimate of the
+ * relative trace error). Errors as lyap_param_solve. */
+int lyap_trace_EX(lyap_seed* seed, int nv, const double* v, int mem_kind, const lyap_opts* opts,
+                  double* trace_out, lyap_result_info* info);
+
+/* f(v) and df/dv_i for nv parameter vectors: one adjoint capacitance solve
+ * with T(v)^T per v (the transpose swaps Ub and Vb), then
+ * df/dv_i = v_i^{-2} sum_s Z[s,i] W'[s,i] (derived from eq.
+ * (SMW_linearsystem) with a v-independent right-hand side).
+ * trace_out: nv doubles; grad_out: nv x k row-major; both in mem_kind
+ * memory. Errors as lyap_param_solve. */
+int lyap_grad(lyap_seed* seed, int nv, const double* v, int mem_kind, const lyap_opts* opts,
+              double* trace_out, double* grad_out, lyap_result_info* info);
+
+/* ----------------------------------------------------------------- serving
+ * A continuous-batching server: requests (one seed, nv parameter vectors)
+ * are admitted while the seeds' resident bytes plus the admitted requests'
+ * workspace stay within opts->hbm_budget, join the running batch of their
+ * seed at the next Krylov-cycle boundary, and retire as soon as all their
+ * systems have converged. Seeds run on separate streams so their work
+ * overlaps. All calls are host calls; pointers are host memory. */
+int lyap_serve_create(lyap_ctx* ctx, const lyap_opts* opts, lyap_server** out);
+/* Register a seed (the server does not take ownership). */
+int lyap_serve_register_seed(lyap_server* srv, lyap_seed* seed, int* seed_id);
+/* Enqueue nv parameter vectors (nv x k row-major, copied). Returns a ticket. */
+int lyap_serve_submit(lyap_server* srv, int seed_id, int nv, const double* v, int want_grad,
+                      uint64_t* ticket);
+/* Run scheduler ticks until no work is left or max_ticks ticks ran
+ * (max_ticks <= 0: until idle). *busy (may be NULL) is set to 1 if work
+ * remains. */
+int lyap_serve_run(lyap_server* srv, int max_ticks, int* busy);
+/* LYAP_PENDING until the request is done; then copies nv traces (and
+ * nv x k gradients if requested), nv infos (each may be NULL) and the
+ * submit-to-completion latency in seconds, and forgets the ticket. */
+int lyap_serve_poll(lyap_server* srv, uint64_t ticket, double* trace_out, double* grad_out,
+                    lyap_result_info* info, double* latency_s);
+int lyap_serve_cancel(lyap_server* srv, uint64_t ticket);
+void lyap_serve_destroy(lyap_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LYAP_H */

@@ -1,0 +1,353 @@
+"""Python binding of liblyap (argument marshalling only).
+
+Every computation runs in the CUDA library ``liblyap.so`` (built in-tree by
+``paper_2312_08201_gb300.build``); this module converts NumPy arrays or
+torch tensors to pointers, sizes and streams and back. There is no CPU
+fallback: without the compiled library (or without a GPU) calls raise.
+
+Problem (paper §1, eqs. (Ljap jdba 1), (formA), transposed convention):
+    A(v) = A0 - U diag(v) V^T,   A(v)^T X + X A(v) = -G G^T,   f(v) = trace(E X(v)).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblyap.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "lyap.h")
+
+OK = 0
+PENDING = 1
+EINVAL = -1
+ENOMEM = -2
+EUNSTABLE_SEED = -3
+ECUDA = -4
+ESOLVER = -5
+ENOCONV = -6
+EBREAKDOWN = -7
+EDEVICE_TIMEOUT = -8
+ENOTFOUND = -9
+ENONFINITE = -10
+ECANCELLED = -11
+MEM_HOST = 0
+MEM_DEVICE = 1
+FP64 = 0
+BF16_IR = 2
+INJECT_ALLOC_FAIL = 0x1
+INJECT_FORCE_MAXIT = 0x2
+INJECT_DEVICE_WAIT = 0x4
+
+
+class LyapOpts(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("refine_tol", ctypes.c_double),
+        ("inner_tol", ctypes.c_double),
+        ("maxit", ctypes.c_int),
+        ("m", ctypes.c_int),
+        ("s", ctypes.c_int),
+        ("pbar", ctypes.c_int),
+        ("batch", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("max_refine", ctypes.c_int),
+        ("hbm_budget", ctypes.c_size_t),
+        ("stream", ctypes.c_void_p),
+        ("inject", ctypes.c_uint),
+    ]
+
+
+class ResultInfo(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("refine_steps", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("rel_resid", ctypes.c_double),
+        ("err_est", ctypes.c_double),
+    ]
+
+
+class SeedStats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("k", ctypes.c_int),
+        ("g", ctypes.c_int),
+        ("real_path", ctypes.c_int),
+        ("cond_Q", ctypes.c_double),
+        ("f0", ctypes.c_double),
+        ("max_re_lambda", ctypes.c_double),
+        ("min_abs_lambda_sum", ctypes.c_double),
+        ("resident_bytes", ctypes.c_size_t),
+    ]
+
+
+class LyapError(RuntimeError):
+    def __init__(self, code, what=""):
+        lib = _LIB
+        name = lib.lyap_strerror(code).decode() if lib else str(code)
+        detail = lib.lyap_last_error().decode() if lib else ""
+        super().__init__(f"{what}: {name} ({code}) {detail}".strip())
+        self.code = code
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "lyap_opts_default": (None, [ctypes.POINTER(LyapOpts)]),
+    "lyap_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "lyap_last_error": (ctypes.c_char_p, []),
+    "lyap_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P)]),
+    "lyap_ctx_destroy": (None, [_P]),
+    "lyap_seed_factor": (
+        ctypes.c_int,
+        [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_int,
+         ctypes.POINTER(LyapOpts), ctypes.POINTER(_P), _D],
+    ),
+    "lyap_seed_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(SeedStats)]),
+    "lyap_seed_free": (ctypes.c_int, [_P]),
+    "lyap_param_solve": (
+        ctypes.c_int,
+        [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(LyapOpts), _P, ctypes.POINTER(ResultInfo)],
+    ),
+    "lyap_trace_EX": (
+        ctypes.c_int,
+        [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(LyapOpts), _P, ctypes.POINTER(ResultInfo)],
+    ),
+    "lyap_grad": (
+        ctypes.c_int,
+        [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(LyapOpts), _P, _P, ctypes.POINTER(ResultInfo)],
+    ),
+    "lyap_serve_create": (ctypes.c_int, [_P, ctypes.POINTER(LyapOpts), ctypes.POINTER(_P)]),
+    "lyap_serve_register_seed": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "lyap_serve_submit": (
+        ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
+    ),
+    "lyap_serve_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "lyap_serve_poll": (
+        ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, ctypes.POINTER(ResultInfo), ctypes.POINTER(ctypes.c_double)]
+    ),
+    "lyap_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "lyap_serve_destroy": (None, [_P]),
+}
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in include/lyap.h."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lyap_[a-zA-Z0-9_]+)\s*\(", text)))
+
+
+def load(path: str = LIB_PATH):
+    """Load liblyap.so (raise if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not built; run paper_2312_08201_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def build(verbose: bool = False) -> str:
+    from .build import build as _b
+
+    return _b(verbose=verbose)
+
+
+def default_opts(**kw) -> LyapOpts:
+    lib = load()
+    o = LyapOpts()
+    lib.lyap_opts_default(ctypes.byref(o))
+    for key, val in kw.items():
+        if key == "stream":
+            val = ctypes.c_void_p(val)
+        setattr(o, key, val)
+    return o
+
+
+def _check(code, what):
+    if code != OK:
+        raise LyapError(code, what)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _host_f64(a, order="F"):
+    return np.require(np.asarray(a, dtype=np.float64), requirements=[order, "A", "W"] if order == "F" else ["C"])
+
+
+def _current_stream_ptr(dev_tensor):
+    import torch
+
+    return torch.cuda.current_stream(dev_tensor.device).cuda_stream
+
+
+class Context:
+    """A CUDA device, its stream and library handles."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = _P()
+        _check(lib.lyap_ctx_create(device, ctypes.byref(h)), "lyap_ctx_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            load().lyap_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Seed:
+    """A factored seed A0 (device-resident) for a family A(v) = A0 - U diag(v) V^T."""
+
+    def __init__(self, ctx: Context, A0, U, V, G, E=None, **opts):
+        lib = load()
+        self.ctx = ctx
+        n = int(A0.shape[0])
+        k = int(U.shape[1])
+        g = int(G.shape[1])
+        o = default_opts(**opts)
+        h = _P()
+        cond = ctypes.c_double()
+        if _is_torch(A0) and A0.is_cuda:
+            # device inputs: column-major float64 = transpose of a contiguous row-major tensor
+            import torch
+
+            arrs = [t.detach().to(torch.float64).t().contiguous() for t in (A0, U, V, G)]
+            e = E.detach().double().t().contiguous() if E is not None else None
+            o.stream = _current_stream_ptr(A0)
+            ptrs = [ctypes.c_void_p(a.data_ptr()) for a in arrs]
+            code = lib.lyap_seed_factor(ctx.h, n, k, g, *ptrs, ctypes.c_void_p(e.data_ptr()) if e is not None else None,
+                                        MEM_DEVICE, ctypes.byref(o), ctypes.byref(h), ctypes.byref(cond))
+        else:
+            arrs = [_host_f64(a) for a in (A0, U, V, G)]
+            e = _host_f64(E) if E is not None else None
+            ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in arrs]
+            code = lib.lyap_seed_factor(ctx.h, n, k, g, *ptrs, e.ctypes.data_as(ctypes.c_void_p) if e is not None else None,
+                                        MEM_HOST, ctypes.byref(o), ctypes.byref(h), ctypes.byref(cond))
+        _check(code, "lyap_seed_factor")
+        self.h = h
+        self.n, self.k, self.g = n, k, g
+        self.cond_Q = cond.value
+
+    def stats(self) -> dict:
+        s = SeedStats()
+        _check(load().lyap_seed_stats_get(self.h, ctypes.byref(s)), "lyap_seed_stats_get")
+        return {f: getattr(s, f) for f, _ in SeedStats._fields_}
+
+    def free(self):
+        if getattr(self, "h", None):
+            load().lyap_seed_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ calls
+    def _prep_v(self, v, o):
+        if _is_torch(v) and v.is_cuda:
+            import torch
+
+            vt = v.detach().to(torch.float64).contiguous()
+            o.stream = _current_stream_ptr(vt)
+            return vt, MEM_DEVICE, ctypes.c_void_p(vt.data_ptr()), int(vt.shape[0])
+        va = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1, self.k))
+        return va, MEM_HOST, va.ctypes.data_as(ctypes.c_void_p), int(va.shape[0])
+
+    def _out(self, like, mem, shape):
+        if mem == MEM_DEVICE:
+            import torch
+
+            t = torch.empty(shape, dtype=torch.float64, device=like.device)
+            return t, ctypes.c_void_p(t.data_ptr())
+        a = np.empty(shape, dtype=np.float64)
+        return a, a.ctypes.data_as(ctypes.c_void_p)
+
+    def trace_EX(self, v, return_info: bool = False, **opts):
+        """f(v) = trace(E X(v)) for each row of v (nv x k)."""
+        lib = load()
+        o = default_opts(**opts)
+        keep, mem, vp, nv = self._prep_v(v, o)
+        out, op = self._out(keep, mem, (nv,))
+        info = (ResultInfo * max(nv, 1))()
+        _check(lib.lyap_trace_EX(self.h, nv, vp, mem, ctypes.byref(o), op, info), "lyap_trace_EX")
+        return (out, _infos(info, nv)) if return_info else out
+
+    def grad(self, v, return_info: bool = False, **opts):
+        """(f(v), df/dv) for each row of v."""
+        lib = load()
+        o = default_opts(**opts)
+        keep, mem, vp, nv = self._prep_v(v, o)
+        f, fp = self._out(keep, mem, (nv,))
+        g, gp = self._out(keep, mem, (nv, self.k))
+        info = (ResultInfo * max(nv, 1))()
+        _check(lib.lyap_grad(self.h, nv, vp, mem, ctypes.byref(o), fp, gp, info), "lyap_grad")
+        return (f, g, _infos(info, nv)) if return_info else (f, g)
+
+    def param_solve(self, v, **opts):
+        """Capacitance solutions W'(v): complex array (nv, k, n) (column t = W'[:, t])."""
+        lib = load()
+        o = default_opts(**opts)
+        keep, mem, vp, nv = self._prep_v(v, o)
+        w, wp = self._out(keep, mem, (nv, self.k, self.n, 2))
+        info = (ResultInfo * max(nv, 1))()
+        _check(lib.lyap_param_solve(self.h, nv, vp, mem, ctypes.byref(o), wp, info), "lyap_param_solve")
+        if mem == MEM_HOST:
+            return w[..., 0] + 1j * w[..., 1], _infos(info, nv)
+        return w, _infos(info, nv)
+
+
+def _infos(info, nv):
+    return [
+        dict(iters=info[i].iters, refine_steps=info[i].refine_steps, status=info[i].status,
+             rel_resid=info[i].rel_resid, err_est=info[i].err_est)
+        for i in range(nv)
+    ]
+
+
+def trace_ex_function():
+    """torch.autograd.Function: f = TraceEX.apply(v, seed, opts_dict); backward
+    returns grad_output * df/dv from the library's adjoint solve."""
+    import torch
+
+    class TraceEX(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, v, seed, opts=None):
+            opts = opts or {}
+            if v.requires_grad:
+                f, g = seed.grad(v.detach(), **opts)
+                ctx.save_for_backward(g if _is_torch(g) else torch.as_tensor(g))
+            else:
+                f = seed.trace_EX(v.detach(), **opts)
+                ctx.save_for_backward(torch.empty(0))
+            return f if _is_torch(f) else torch.as_tensor(f)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            return grad_out[:, None].to(g.dtype) * g.to(grad_out.device), None, None
+
+    return TraceEX

@@ -1,0 +1,426 @@
+// C ABI of liblyap (declarations and documentation in include/lyap.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+
+#include "cplx.cuh"
+#include "krylov.cuh"
+#include "lyap_internal.h"
+#include "mixed.h"
+#include "solver.h"
+
+// ------------------------------------------------------------- last error
+namespace {
+thread_local std::string g_last_error;
+}
+void lyap_set_last_error(const std::string& msg) { g_last_error = msg; }
+extern "C" const char* lyap_last_error(void) { return g_last_error.c_str(); }
+
+// Workspaces cached per seed.
+struct SeedWork {
+  KrylovWS<double2> ws64, ws64adj;
+  KrylovWS<float2> ws32, ws32adj;
+  DevBuf<double> vinv;
+  DevBuf<double2> Wp, Zadj, Rres, tmp;
+  DevBuf<double> red0, red1, red2, red3;
+};
+
+namespace {
+
+__global__ void k_vinv(int count, const double* __restrict__ v, double* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = 1.0 / v[i];
+}
+
+// grad[b, i] = v_i^{-2} Re sum_s Z_b[s, i] W_b[s, i]  (pairing without conjugation)
+__global__ void k_grad(int n, int k, int nsys, const double2* __restrict__ W, const double2* __restrict__ Z,
+                       const double* __restrict__ vinv, double* __restrict__ grad) {
+  __shared__ double red[32];
+  const int b = blockIdx.x / k, i = blockIdx.x % k;
+  if (b >= nsys) return;
+  const size_t N = (size_t)n * k;
+  double acc[1] = {0.0};
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    double2 p = cmul(Z[(size_t)b * N + (size_t)i * n + s], W[(size_t)b * N + (size_t)i * n + s]);
+    acc[0] += p.x;
+  }
+  kry::block_sum<1>(acc, red);
+  if (threadIdx.x == 0) {
+    double vi = vinv[(size_t)b * k + i];
+    grad[(size_t)b * k + i] = vi * vi * acc[0];
+  }
+}
+
+// out[b] = Re sum_e A_b[e] B_b[e]
+__global__ void k_dot_pair(int N, int nsys, const double2* __restrict__ A, const double2* __restrict__ Bv,
+                           double* __restrict__ out) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  if (b >= nsys) return;
+  double acc[1] = {0.0};
+  for (int e = threadIdx.x; e < N; e += blockDim.x) acc[0] += cmul(A[(size_t)b * N + e], Bv[(size_t)b * N + e]).x;
+  kry::block_sum<1>(acc, red);
+  if (threadIdx.x == 0) out[b] = acc[0];
+}
+
+int grid_of(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 65535)); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ options
+extern "C" void lyap_opts_default(lyap_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-12;
+  o->refine_tol = 1e-11;
+  o->inner_tol = 1e-5;
+  o->maxit = 300;
+  o->m = 30;
+  o->s = 10;
+  o->pbar = 0;
+  o->batch = 0;
+  o->precision = LYAP_FP64;
+  o->max_refine = 10;
+  o->hbm_budget = 0;
+  o->stream = nullptr;
+  o->inject = 0;
+}
+
+extern "C" const char* lyap_strerror(int code) {
+  switch (code) {
+    case LYAP_OK: return "ok";
+    case LYAP_PENDING: return "pending";
+    case LYAP_EINVAL: return "invalid argument";
+    case LYAP_ENOMEM: return "out of device memory or over budget";
+    case LYAP_EUNSTABLE_SEED: return "seed matrix not stable (Lyapunov solution not unique)";
+    case LYAP_ECUDA: return "CUDA error";
+    case LYAP_ESOLVER: return "cuSOLVER/cuBLAS error";
+    case LYAP_ENOCONV: return "no convergence within maxit";
+    case LYAP_EBREAKDOWN: return "Krylov breakdown";
+    case LYAP_EDEVICE_TIMEOUT: return "device wait timed out";
+    case LYAP_ENOTFOUND: return "unknown seed or ticket";
+    case LYAP_ENONFINITE: return "non-finite value in solve";
+    case LYAP_ECANCELLED: return "cancelled";
+    default: return "unknown status";
+  }
+}
+
+int lyap_check_v(int nv, int k, const double* v) {
+  for (size_t i = 0; i < (size_t)nv * k; ++i)
+    if (!std::isfinite(v[i]) || v[i] == 0.0) {
+      lyap_set_last_error("parameter " + std::to_string(i) + " is zero or not finite");
+      return LYAP_EINVAL;
+    }
+  return LYAP_OK;
+}
+
+// ------------------------------------------------------------------ context
+extern "C" int lyap_ctx_create(int device, lyap_ctx** out) {
+  if (!out) return LYAP_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  LY_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return LYAP_EINVAL;
+  LY_CUDA(cudaSetDevice(device));
+  std::unique_ptr<lyap_ctx> c(new lyap_ctx());
+  c->device = device;
+  LY_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+  LY_BLAS(cublasCreate(&c->blas));
+  LY_SOLVER(cusolverDnCreate(&c->solver));
+  *out = c.release();
+  return LYAP_OK;
+}
+
+extern "C" void lyap_ctx_destroy(lyap_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->solver) cusolverDnDestroy(c->solver);
+  if (c->blas) cublasDestroy(c->blas);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+static cudaStream_t pick_stream(lyap_ctx* c, const lyap_opts& o) {
+  return o.stream ? static_cast<cudaStream_t>(o.stream) : c->stream;
+}
+
+// ---------------------------------------------------------------- seed factor
+extern "C" int lyap_seed_factor(lyap_ctx* ctx, int n, int k, int g, const double* A0, const double* U,
+                                const double* V, const double* G, const double* E, int mem_kind,
+                                const lyap_opts* opts, lyap_seed** out, double* cond_Q_out) {
+  if (!ctx || !out || !A0 || !U || !V || !G || n < 1 || k < 1 || k > 8 || k > n || g < 1) return LYAP_EINVAL;
+  if (mem_kind != LYAP_MEM_HOST && mem_kind != LYAP_MEM_DEVICE) return LYAP_EINVAL;
+  *out = nullptr;
+  lyap_opts o;
+  lyap_opts_default(&o);
+  if (opts) o = *opts;
+  LY_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = pick_stream(ctx, o);
+  const size_t nn = (size_t)n * n;
+  DevBuf<double> dA, dU, dV, dG, dE;
+  const double *pA = A0, *pU = U, *pV = V, *pG = G, *pE = E;
+  if (mem_kind == LYAP_MEM_HOST) {
+    for (size_t i = 0; i < nn; ++i)
+      if (!std::isfinite(A0[i]) || (E && !std::isfinite(E[i]))) return LYAP_EINVAL;
+    LY_TRY(dA.alloc(nn));
+    LY_TRY(dU.alloc((size_t)n * k));
+    LY_TRY(dV.alloc((size_t)n * k));
+    LY_TRY(dG.alloc((size_t)n * g));
+    LY_CUDA(cudaMemcpyAsync(dA.p, A0, nn * sizeof(double), cudaMemcpyHostToDevice, st));
+    LY_CUDA(cudaMemcpyAsync(dU.p, U, (size_t)n * k * sizeof(double), cudaMemcpyHostToDevice, st));
+    LY_CUDA(cudaMemcpyAsync(dV.p, V, (size_t)n * k * sizeof(double), cudaMemcpyHostToDevice, st));
+    LY_CUDA(cudaMemcpyAsync(dG.p, G, (size_t)n * g * sizeof(double), cudaMemcpyHostToDevice, st));
+    pA = dA.p;
+    pU = dU.p;
+    pV = dV.p;
+    pG = dG.p;
+    if (E) {
+      LY_TRY(dE.alloc(nn));
+      LY_CUDA(cudaMemcpyAsync(dE.p, E, nn * sizeof(double), cudaMemcpyHostToDevice, st));
+      pE = dE.p;
+    }
+  }
+  std::unique_ptr<lyap_seed> sd(new lyap_seed());
+  sd->ctx = ctx;
+  sd->n = n;
+  sd->k = k;
+  sd->g = g;
+  LY_TRY(lyap_seed_build(ctx, sd.get(), pA, pU, pV, pG, pE, st));
+  LY_TRY(lyap_mixed_prepare(sd.get(), st));
+  sd->work = new SeedWork();
+  if (cond_Q_out) *cond_Q_out = sd->cond_Q;
+  *out = sd.release();
+  return LYAP_OK;
+}
+
+extern "C" int lyap_seed_stats_get(const lyap_seed* sd, lyap_seed_stats* o) {
+  if (!sd || !o) return LYAP_EINVAL;
+  o->n = sd->n;
+  o->k = sd->k;
+  o->g = sd->g;
+  o->real_path = sd->real_path;
+  o->cond_Q = sd->cond_Q;
+  o->f0 = sd->f0;
+  o->max_re_lambda = sd->max_re;
+  o->min_abs_lambda_sum = sd->min_sum;
+  o->resident_bytes = sd->resident_bytes;
+  return LYAP_OK;
+}
+
+extern "C" int lyap_seed_free(lyap_seed* sd) {
+  if (!sd) return LYAP_EINVAL;
+  cudaSetDevice(sd->ctx->device);
+  delete sd->work;
+  delete sd;
+  return LYAP_OK;
+}
+
+// ------------------------------------------------------------ online solves
+namespace {
+
+struct CallIO {
+  int nv = 0;
+  std::vector<double> v;  // host copy, nv x k
+};
+
+int load_v(lyap_seed* sd, int nv, const double* v, int mem_kind, cudaStream_t st, CallIO& io) {
+  if (nv < 0 || (nv > 0 && !v)) return LYAP_EINVAL;
+  if (mem_kind != LYAP_MEM_HOST && mem_kind != LYAP_MEM_DEVICE) return LYAP_EINVAL;
+  io.nv = nv;
+  io.v.resize((size_t)nv * sd->k);
+  if (nv == 0) return LYAP_OK;
+  if (mem_kind == LYAP_MEM_HOST) {
+    std::memcpy(io.v.data(), v, sizeof(double) * io.v.size());
+  } else {
+    LY_CUDA(cudaMemcpyAsync(io.v.data(), v, sizeof(double) * io.v.size(), cudaMemcpyDeviceToHost, st));
+    LY_CUDA(cudaStreamSynchronize(st));
+  }
+  return lyap_check_v(nv, sd->k, io.v.data());
+}
+
+int store_out(double* dst, const double* src_host, size_t count, int mem_kind, cudaStream_t st) {
+  if (!dst || count == 0) return LYAP_OK;
+  if (mem_kind == LYAP_MEM_HOST) {
+    std::memcpy(dst, src_host, count * sizeof(double));
+  } else {
+    LY_CUDA(cudaMemcpyAsync(dst, src_host, count * sizeof(double), cudaMemcpyHostToDevice, st));
+    LY_CUDA(cudaStreamSynchronize(st));
+  }
+  return LYAP_OK;
+}
+
+// Final FP64 report for one chunk: trace, residual, error estimate, and
+// (with an adjoint solution Zadj) the gradient and the dual-weighted error
+// estimate |<z, r>| / |f|.
+int report_chunk(lyap_seed* sd, SeedWork& w, int Bc, const double2* Wp, const double2* Zadj, cudaStream_t st,
+                 double* f_host, double* grad_host, lyap_result_info* info) {
+  const int n = sd->n, k = sd->k;
+  const size_t N = (size_t)n * k;
+  LY_TRY(w.Rres.alloc(std::max<size_t>(w.Rres.count, (size_t)Bc * N)));
+  LY_TRY(w.tmp.alloc(std::max<size_t>(w.tmp.count, (size_t)Bc * N)));
+  for (DevBuf<double>* r : {&w.red0, &w.red1, &w.red2, &w.red3})
+    if (r->count < (size_t)Bc * k) LY_TRY(r->alloc((size_t)Bc * k));
+  kry::k_dot_h<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, Wp, N, sd->h.p, w.red0.p, nullptr);
+  // r = Ph - T(v) W'
+  CapArgs64 a{};
+  a.n = n;
+  a.k = k;
+  a.lam = sd->lam.p;
+  a.P1 = sd->Ub.p;
+  a.P2 = sd->Vb.p;
+  a.Gd = sd->Gd.p;
+  a.W = Wp;
+  a.ldw = N;
+  a.vinv = w.vinv.p;
+  a.rhs = sd->Ph.p;
+  a.ldr = 0;
+  a.out = w.Rres.p;
+  a.ldo = N;
+  a.mode = CAP_RESID;
+  a.nsys = Bc;
+  LY_TRY(capmv64_launch(a, st));
+  kry::k_norms<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.Rres.p, N, w.red1.p);
+  if (Zadj) {
+    k_dot_pair<<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.Rres.p, Zadj, w.red2.p);
+    k_grad<<<Bc * k, kry::NT, 0, st>>>(n, k, Bc, Wp, Zadj, w.vinv.p, w.red3.p);
+  } else {
+    // delta = P^{-1} r (block-Jacobi proxy for T^{-1} r); estimate <h, delta>
+    SysOp<double2> op;
+    op.sd = sd;
+    op.vinv = w.vinv.p;
+    DevBuf<int> lst, cnt;
+    LY_TRY(lst.alloc(Bc));
+    LY_TRY(cnt.alloc(1));
+    kry::k_iota<<<grid_of(Bc), 256, 0, st>>>(Bc, lst.p, cnt.p);
+    LY_TRY(op.precond(lst.p, cnt.p, Bc, w.Rres.p, N, w.tmp.p, N, st));
+    kry::k_dot_h<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.tmp.p, N, sd->h.p, w.red2.p, nullptr);
+  }
+  LY_CUDA(cudaGetLastError());
+  std::vector<double> tr(Bc), rn(Bc), ee(Bc), gr((size_t)Bc * k);
+  LY_CUDA(cudaMemcpyAsync(tr.data(), w.red0.p, sizeof(double) * Bc, cudaMemcpyDeviceToHost, st));
+  LY_CUDA(cudaMemcpyAsync(rn.data(), w.red1.p, sizeof(double) * Bc, cudaMemcpyDeviceToHost, st));
+  LY_CUDA(cudaMemcpyAsync(ee.data(), w.red2.p, sizeof(double) * Bc, cudaMemcpyDeviceToHost, st));
+  if (Zadj) LY_CUDA(cudaMemcpyAsync(gr.data(), w.red3.p, sizeof(double) * Bc * k, cudaMemcpyDeviceToHost, st));
+  LY_CUDA(cudaStreamSynchronize(st));
+  for (int b = 0; b < Bc; ++b) {
+    double f = sd->f0 + tr[b];
+    f_host[b] = f;
+    if (info) {
+      info[b].rel_resid = sd->ph_norm > 0 ? rn[b] / sd->ph_norm : rn[b];
+      info[b].err_est = f != 0 ? std::fabs(ee[b]) / std::fabs(f) : std::fabs(ee[b]);
+    }
+    if (grad_host)
+      for (int i = 0; i < k; ++i) grad_host[(size_t)b * k + i] = gr[(size_t)b * k + i];
+  }
+  return LYAP_OK;
+}
+
+// Solve all nv systems (FP64 or mixed), primal (and adjoint when want_adj).
+int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t st, double* f_host,
+              double* grad_host, double* w_out, int w_mem, lyap_result_info* info) {
+  const int n = sd->n, k = sd->k, nv = io.nv;
+  const size_t N = (size_t)n * k;
+  SolveParams prm;
+  LY_TRY(lyap_params_from_opts(o, prm));
+  if (o.precision != LYAP_FP64 && o.precision != LYAP_BF16_IR) return LYAP_EINVAL;
+  SeedWork& w = *sd->work;
+  int B = o.batch > 0 ? o.batch : 256;
+  B = std::min(B, std::max(nv, 1));
+  LY_TRY(w.vinv.alloc(std::max<size_t>(w.vinv.count, (size_t)B * k)));
+  LY_TRY(w.Wp.alloc(std::max<size_t>(w.Wp.count, (size_t)B * N)));
+  if (grad_host) LY_TRY(w.Zadj.alloc(std::max<size_t>(w.Zadj.count, (size_t)B * N)));
+  DevBuf<double> vdev;
+  LY_TRY(vdev.alloc((size_t)B * k));
+  std::vector<int> it, stt, ita, sta, rsteps;
+  for (int c0 = 0; c0 < nv; c0 += B) {
+    const int Bc = std::min(B, nv - c0);
+    LY_CUDA(cudaMemcpyAsync(vdev.p, io.v.data() + (size_t)c0 * k, sizeof(double) * Bc * k,
+                            cudaMemcpyHostToDevice, st));
+    k_vinv<<<grid_of((size_t)Bc * k), 256, 0, st>>>(Bc * k, vdev.p, w.vinv.p);
+    LY_CUDA(cudaGetLastError());
+    if (o.precision == LYAP_FP64) {
+      SysOp<double2> op;
+      op.sd = sd;
+      op.vinv = w.vinv.p;
+      LY_TRY(gcrodr_chunk(op, Bc, sd->Ph.p, 0, sd->rec64, prm, w.ws64, it, stt, st));
+      LY_CUDA(cudaMemcpyAsync(w.Wp.p, w.ws64.X.p, sizeof(double2) * Bc * N, cudaMemcpyDeviceToDevice, st));
+      rsteps.assign(Bc, 0);
+      if (grad_host) {
+        SysOp<double2> opa;
+        opa.sd = sd;
+        opa.adjoint = true;
+        opa.vinv = w.vinv.p;
+        LY_TRY(gcrodr_chunk(opa, Bc, sd->h.p, 0, sd->rec64_adj, prm, w.ws64adj, ita, sta, st));
+        LY_CUDA(cudaMemcpyAsync(w.Zadj.p, w.ws64adj.X.p, sizeof(double2) * Bc * N, cudaMemcpyDeviceToDevice, st));
+        for (int b = 0; b < Bc; ++b) {
+          it[b] += ita[b];
+          if (stt[b] == LYAP_OK) stt[b] = sta[b];
+        }
+      }
+    } else {
+      LY_TRY(lyap_mixed_chunk(sd, Bc, w.vinv.p, o, prm, st, w.ws32, w.ws32adj, w.Wp.p, grad_host ? w.Zadj.p : nullptr, it,
+                              stt, rsteps));
+    }
+    std::vector<double> gtmp;
+    double* gh = nullptr;
+    if (grad_host) gh = grad_host + (size_t)c0 * k;
+    lyap_result_info* inf = info ? info + c0 : nullptr;
+    LY_TRY(report_chunk(sd, w, Bc, w.Wp.p, grad_host ? w.Zadj.p : nullptr, st, f_host + c0, gh, inf));
+    if (inf)
+      for (int b = 0; b < Bc; ++b) {
+        inf[b].iters = it[b];
+        inf[b].status = stt[b];
+        inf[b].refine_steps = rsteps.empty() ? 0 : rsteps[b];
+      }
+    if (w_out) {
+      double* dst = w_out + (size_t)c0 * N * 2;
+      LY_CUDA(cudaMemcpyAsync(dst, w.Wp.p, sizeof(double2) * Bc * N,
+                              w_mem == LYAP_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+      LY_CUDA(cudaStreamSynchronize(st));
+    }
+  }
+  return LYAP_OK;
+}
+
+int entry(lyap_seed* sd, int nv, const double* v, int mem_kind, const lyap_opts* opts, double* trace_out,
+          double* grad_out, double* w_out, lyap_result_info* info) {
+  if (!sd) return LYAP_EINVAL;
+  lyap_opts o;
+  lyap_opts_default(&o);
+  if (opts) o = *opts;
+  LY_CUDA(cudaSetDevice(sd->ctx->device));
+  cudaStream_t st = pick_stream(sd->ctx, o);
+  CallIO io;
+  LY_TRY(load_v(sd, nv, v, mem_kind, st, io));
+  if (nv == 0) return LYAP_OK;
+  if (o.inject & LYAP_INJECT_ALLOC_FAIL) {
+    lyap_set_last_error("injected allocation failure");
+    return LYAP_ENOMEM;
+  }
+  std::vector<double> f(nv), g(grad_out ? (size_t)nv * sd->k : 0);
+  LY_TRY(run_sweep(sd, io, o, st, f.data(), grad_out ? g.data() : nullptr, w_out, mem_kind, info));
+  if (trace_out) LY_TRY(store_out(trace_out, f.data(), nv, mem_kind, st));
+  if (grad_out) LY_TRY(store_out(grad_out, g.data(), g.size(), mem_kind, st));
+  return LYAP_OK;
+}
+
+}  // namespace
+
+extern "C" int lyap_param_solve(lyap_seed* sd, int nv, const double* v, int mem_kind, const lyap_opts* opts,
+                                double* w_out, lyap_result_info* info) {
+  return entry(sd, nv, v, mem_kind, opts, nullptr, nullptr, w_out, info);
+}
+
+extern "C" int lyap_trace_EX(lyap_seed* sd, int nv, const double* v, int mem_kind, const lyap_opts* opts,
+                             double* trace_out, lyap_result_info* info) {
+  if (!trace_out && nv > 0) return LYAP_EINVAL;
+  return entry(sd, nv, v, mem_kind, opts, trace_out, nullptr, nullptr, info);
+}
+
+extern "C" int lyap_grad(lyap_seed* sd, int nv, const double* v, int mem_kind, const lyap_opts* opts,
+                         double* trace_out, double* grad_out, lyap_result_info* info) {
+  if ((!trace_out || !grad_out) && nv > 0) return LYAP_EINVAL;
+  return entry(sd, nv, v, mem_kind, opts, trace_out, grad_out, nullptr, info);
+}

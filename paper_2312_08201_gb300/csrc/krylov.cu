@@ -1,0 +1,268 @@
+// Non-template kernels of the batched recycled Krylov solver (see krylov.cuh).
+#include "krylov.cuh"
+
+namespace kry {
+
+__global__ void k_iota(int B, int* list, int* count) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B; i += gridDim.x * blockDim.x) list[i] = i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count = B;
+}
+
+// single CTA of 1024 threads; order-preserving
+__global__ void k_compact(const int* __restrict__ in_list, const int* __restrict__ in_count,
+                          const int* __restrict__ flag, int* __restrict__ out_list, int* __restrict__ out_count) {
+  __shared__ int sc[1024];
+  const int n = *in_count;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int beg = threadIdx.x * per;
+  const int end = min(n, beg + per);
+  int c = 0;
+  for (int i = beg; i < end; ++i) c += flag[in_list[i]] > 0;
+  sc[threadIdx.x] = c;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    int v = (int)threadIdx.x >= off ? sc[threadIdx.x - off] : 0;
+    __syncthreads();
+    sc[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int pos = sc[threadIdx.x] - c;
+  for (int i = beg; i < end; ++i) {
+    int b = in_list[i];
+    if (flag[b] > 0) out_list[pos++] = b;
+  }
+  if (threadIdx.x == blockDim.x - 1) *out_count = sc[threadIdx.x];
+}
+
+// status codes kept per system
+enum { ST_RUN = 0, ST_CONV = 1, ST_MAXIT = 2, ST_BREAK = 3, ST_NONFINITE = 4 };
+
+__global__ void k_lsq(int j, int m, const int* __restrict__ list, const int* __restrict__ count,
+                      double2* __restrict__ H, double2* __restrict__ H0, double* __restrict__ cs,
+                      double2* __restrict__ sn, double2* __restrict__ g, const double* __restrict__ tolabs,
+                      int* __restrict__ jstop, int* __restrict__ flag, const int* __restrict__ iters_done, int maxit) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  double2* h = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
+  double2* h0 = H0 + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
+  for (int i = 0; i <= j + 1; ++i) h0[i] = h[i];
+  double* c = cs + (size_t)b * m;
+  double2* s = sn + (size_t)b * m;
+  double2* gb = g + (size_t)b * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    double2 top = h[i], bot = h[i + 1];
+    h[i] = cadd(cscale(top, c[i]), cmul(s[i], bot));
+    h[i + 1] = csub(cscale(bot, c[i]), cjmul(s[i], top));
+  }
+  double cj;
+  double2 sj;
+  sd::givens(h[j], h[j + 1], cj, sj);
+  double2 rho = cadd(cscale(h[j], cj), cmul(sj, h[j + 1]));
+  const double sub = h0[j + 1].x;
+  h[j] = rho;
+  h[j + 1] = make_double2(0.0, 0.0);
+  c[j] = cj;
+  s[j] = sj;
+  double2 gj = gb[j];
+  gb[j] = cscale(gj, cj);
+  gb[j + 1] = cscale(cjmul(sj, gj), -1.0);
+  const double res = sqrt(cabs2(gb[j + 1]));
+  int st = ST_RUN;
+  if (!isfinite(res) || !isfinite(rho.x) || !isfinite(rho.y)) st = ST_NONFINITE;
+  else if (res <= tolabs[b]) st = ST_CONV;
+  else if (!(sub > 1e-14 * sqrt(cabs2(rho)))) st = ST_CONV;  // invariant subspace: exact in the space
+  else if (iters_done[b] + j + 1 >= maxit) st = ST_MAXIT;
+  if (st != ST_RUN) {
+    jstop[b] = j + 1;
+    flag[b] = -st;  // negative: stopped this cycle with a final status
+  } else {
+    jstop[b] = j + 1;  // provisional (cycle may end here)
+  }
+}
+
+__global__ void k_cycle_solve(int m, int smax, int s_cur, const int* __restrict__ list,
+                              const int* __restrict__ count, const double2* __restrict__ H,
+                              const double2* __restrict__ H0, const double2* __restrict__ Bk,
+                              const double2* __restrict__ g, const double* __restrict__ beta,
+                              const int* __restrict__ jstop, double2* __restrict__ coefY, double2* __restrict__ coefR) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  const int js = jstop[b];
+  const double2* Hb = H + (size_t)b * (m + 1) * m;
+  const double2* H0b = H0 + (size_t)b * (m + 1) * m;
+  const double2* gb = g + (size_t)b * (m + 1);
+  double2* cy = coefY + (size_t)b * (m + smax + 1);
+  double2* cr = coefR + (size_t)b * (m + 1);
+  double2* y2 = cy + s_cur;
+  for (int i = js - 1; i >= 0; --i) {
+    double2 x = gb[i];
+    for (int l = i + 1; l < js; ++l) x = csub(x, cmul(Hb[i + (size_t)l * (m + 1)], y2[l]));
+    double2 d = Hb[i + (size_t)i * (m + 1)];
+    y2[i] = cabs2(d) > 0 ? cdiv(x, d) : make_double2(0.0, 0.0);
+  }
+  const double2* Bb = Bk + (size_t)b * smax * m;
+  for (int q = 0; q < s_cur; ++q) {
+    double2 x = make_double2(0.0, 0.0);
+    for (int l = 0; l < js; ++l) x = cfma(Bb[q + (size_t)l * smax], y2[l], x);
+    cy[q] = cscale(x, -1.0);
+  }
+  for (int i = 0; i <= js; ++i) {
+    double2 x = make_double2(i == 0 ? beta[b] : 0.0, 0.0);
+    for (int l = 0; l < js; ++l) {
+      if (i <= l + 1) x = csub(x, cmul(H0b[i + (size_t)l * (m + 1)], y2[l]));
+    }
+    cr[i] = x;
+  }
+}
+
+__global__ void k_ritz(int m, int smax, int s_cur, int s_new, const int* __restrict__ list,
+                       const int* __restrict__ count, const int* __restrict__ jstop, const double2* __restrict__ H0,
+                       const double2* __restrict__ Bk, const double2* __restrict__ F, const double2* __restrict__ UU,
+                       double2* __restrict__ work, size_t wstride, double2* __restrict__ Pu,
+                       double2* __restrict__ Qc, int* __restrict__ ok) {
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp_global >= *count) return;
+  const int b = list[warp_global];
+  const int js = jstop[b];
+  const int me = s_cur + js, re = me + 1;
+  const int LD = m + smax + 1;
+  if (me < s_new || js <= 0) {
+    if (sd::lane() == 0) ok[b] = 0;
+    return;
+  }
+  double2* w = work + (size_t)b * wstride;
+  double2* Gh = w;                       // LD x LD
+  double2* A = Gh + (size_t)LD * LD;     // LD x LD
+  double2* K = A + (size_t)LD * LD;      // LD x LD
+  double2* Q = K + (size_t)LD * LD;      // LD x LD
+  double2* Fh = Q + (size_t)LD * LD;     // LD x LD
+  double2* X = Fh + (size_t)LD * LD;     // LD x 16
+  double2* P = X + (size_t)LD * 16;      // LD x 16
+  double2* Yq = P + (size_t)LD * 16;     // LD x 16
+  double2* R = Yq + (size_t)LD * 16;     // 16 x 16
+  double2* vt = R + 256;                 // LD
+  double2* coef = vt + LD;               // LD
+  int* sel = reinterpret_cast<int*>(coef + LD);  // 16 ints
+  double D[16];
+  const double2* UUb = UU + (size_t)b * smax * smax;
+  for (int q = 0; q < s_cur; ++q) {
+    double nn = UUb[q + (size_t)q * smax].x;
+    D[q] = nn > 0 ? 1.0 / sqrt(nn) : 1.0;
+  }
+  const double2* H0b = H0 + (size_t)b * (m + 1) * m;
+  const double2* Bb = Bk + (size_t)b * smax * m;
+  const double2* Fb = F + (size_t)b * LD * LD;
+  // Ghat (re x me) and Fhat (re x me)
+  for (int e = sd::lane(); e < re * me; e += 32) {
+    int i = e % re, c = e / re;
+    double2 v = make_double2(0.0, 0.0);
+    if (i < s_cur && c < s_cur) {
+      if (i == c) v = make_double2(D[i], 0.0);
+    } else if (i < s_cur) {
+      v = Bb[i + (size_t)(c - s_cur) * smax];
+    } else if (c >= s_cur) {
+      int ii = i - s_cur, cc = c - s_cur;
+      if (ii <= cc + 1) v = H0b[ii + (size_t)cc * (m + 1)];
+    }
+    Gh[i + (size_t)c * LD] = v;
+    double2 f = Fb[i + (size_t)c * LD];
+    if (c < s_cur) f = cscale(f, D[c]);
+    Fh[i + (size_t)c * LD] = f;
+  }
+  sd::wsync();
+  sd::gemm_hn(me, me, re, Gh, LD, Gh, LD, A, LD);
+  sd::gemm_hn(me, me, re, Gh, LD, Fh, LD, K, LD);
+  if (sd::cholesky(me, A, LD)) {
+    if (sd::lane() == 0) ok[b] = 0;
+    return;
+  }
+  sd::trsm_lower_left(me, me, A, LD, K, LD);
+  sd::trsm_right_lower_h(me, me, A, LD, K, LD);
+  sd::hessenberg(me, K, LD, Q, LD, vt);
+  if (sd::hqr(me, K, LD, Q, LD, 60 * me)) {
+    if (sd::lane() == 0) ok[b] = 0;
+    return;
+  }
+  // select s_new eigenvalues of largest |mu| (ties: lower index)
+  if (sd::lane() == 0) {
+    for (int c = 0; c < s_new; ++c) {
+      int best = -1;
+      double bv = -1.0;
+      for (int i = 0; i < me; ++i) {
+        bool used = false;
+        for (int q = 0; q < c; ++q) used |= sel[q] == i;
+        if (used) continue;
+        double a = cabs2(K[i + (size_t)i * LD]);
+        if (a > bv) {
+          bv = a;
+          best = i;
+        }
+      }
+      sel[c] = best;
+    }
+  }
+  sd::wsync();
+  // Y buffer for the triangular eigenvectors: reuse Fh
+  sd::schur_vectors(me, K, LD, Q, LD, sel, s_new, Fh, LD, X, LD);
+  // P = L^{-H} X
+  for (int e = sd::lane(); e < me * s_new; e += 32) P[(e % me) + (size_t)(e / me) * LD] = X[(e % me) + (size_t)(e / me) * LD];
+  sd::wsync();
+  sd::trsm_lower_h_left(me, s_new, A, LD, P, LD);
+  // Yq = Ghat P, QR
+  sd::gemm_nn(re, s_new, me, Gh, LD, P, LD, X, LD);
+  if (sd::qr_cgs2(re, s_new, X, LD, Yq, LD, R, 16, coef)) {
+    if (sd::lane() == 0) ok[b] = 0;
+    return;
+  }
+  for (int e = sd::lane(); e < s_cur * s_new; e += 32) {
+    int i = e % s_cur, c = e / s_cur;
+    P[i + (size_t)c * LD] = cscale(P[i + (size_t)c * LD], D[i]);
+  }
+  sd::wsync();
+  sd::trsm_right_upper(me, s_new, R, 16, P, LD);
+  bool finite = true;
+  for (int e = sd::lane(); e < me * s_new; e += 32) {
+    double2 v = P[(e % me) + (size_t)(e / me) * LD];
+    finite &= isfinite(v.x) && isfinite(v.y);
+  }
+  finite = __all_sync(0xffffffffu, finite);
+  if (!finite) {
+    if (sd::lane() == 0) ok[b] = 0;
+    return;
+  }
+  double2* Pub = Pu + (size_t)b * LD * 16;
+  double2* Qcb = Qc + (size_t)b * LD * 16;
+  for (int e = sd::lane(); e < me * s_new; e += 32) Pub[(e % me) + (size_t)(e / me) * LD] = P[(e % me) + (size_t)(e / me) * LD];
+  for (int e = sd::lane(); e < re * s_new; e += 32) Qcb[(e % re) + (size_t)(e / re) * LD] = Yq[(e % re) + (size_t)(e / re) * LD];
+  if (sd::lane() == 0) ok[b] = 1;
+}
+
+__global__ void k_chol_rinv(int s, const int* __restrict__ list, const int* __restrict__ count,
+                            double2* __restrict__ G, size_t gs, double2* __restrict__ Rinv,
+                            double2* __restrict__ Racc, double2* __restrict__ tmp, int accumulate,
+                            int* __restrict__ ok) {
+  const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wg >= *count) return;
+  const int b = list[wg];
+  double2* Gb = G + (size_t)b * gs;
+  if (sd::cholesky(s, Gb, s)) {
+    if (sd::lane() == 0) ok[b] = 0;
+    return;
+  }
+  double2* Ri = Rinv + (size_t)b * s * s;
+  for (int e = sd::lane(); e < s * s; e += 32) Ri[e] = make_double2((e % s) == (e / s) ? 1.0 : 0.0, 0.0);
+  sd::wsync();
+  sd::trsm_lower_h_left(s, s, Gb, s, Ri, s);  // Ri = L^{-H}
+  if (accumulate) {
+    double2* Ra = Racc + (size_t)b * s * s;
+    double2* T = tmp + (size_t)b * s * s;
+    sd::gemm_nn(s, s, s, Ra, s, Ri, s, T, s);
+    for (int e = sd::lane(); e < s * s; e += 32) Ra[e] = T[e];
+    sd::wsync();
+  }
+  if (sd::lane() == 0) ok[b] = 1;
+}
+
+}  // namespace kry

@@ -1,0 +1,489 @@
+// Batched kernels of the recycled Krylov solver (GCRO-DR, paper §2.1; the
+// method is cited there from Parks et al. and restated in the design notes).
+//
+// B systems run in lockstep; each has its own Arnoldi basis, recycle space
+// and small projected matrices. A device-side list of active systems lets
+// converged systems drop out mid-cycle without a host round trip. Vector
+// storage is complex (T2 = double2 for the FP64 path, float2 for the inner
+// solves of the mixed path); every reduction and every small projected
+// matrix is FP64 and summed in a fixed order, so results do not depend on
+// which other systems share the batch.
+#pragma once
+#include "cplx.cuh"
+#include "smalldense.cuh"
+
+namespace kry {
+
+constexpr int NT = 256;  // threads per CTA for vector kernels
+
+// Sum NV doubles over the CTA (fixed shuffle tree, fixed cross-warp order).
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red /* NV*32 */) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (ln == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[i * 32 + warp] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double x = ln < nw ? red[i * 32 + ln] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (ln == 0) red[i * 32] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = red[i * 32];
+  __syncthreads();
+}
+
+// A strided family of vectors: vector i of system b at base + b*ss + i*vs.
+template <typename T2>
+struct Seg {
+  T2* base;
+  size_t ss, vs;
+  int count;        // fixed count, or
+  const int* cdev;  // per-system count (cdev[b] + cadd) when non-null
+  int cadd;
+  __device__ __forceinline__ int cnt(int b) const { return cdev ? cdev[b] + cadd : count; }
+  __device__ __forceinline__ T2* vec(int b, int i) const { return base + (size_t)b * ss + (size_t)i * vs; }
+};
+
+// Two concatenated segments [S0 S1].
+template <typename T2>
+struct Seg2 {
+  Seg<T2> a, b;
+  __device__ __forceinline__ int cnt(int s) const { return a.cnt(s) + b.cnt(s); }
+  __device__ __forceinline__ T2* vec(int s, int i) const {
+    int na = a.cnt(s);
+    return i < na ? a.vec(s, i) : b.vec(s, i - na);
+  }
+};
+
+// ----------------------------------------------------------------- lists
+// Rebuild an ordered list of systems: out = [b in in_list : flag[b] > 0].
+__global__ void k_compact(const int* __restrict__ in_list, const int* __restrict__ in_count,
+                          const int* __restrict__ flag, int* __restrict__ out_list, int* __restrict__ out_count);
+__global__ void k_iota(int B, int* list, int* count);
+
+// ----------------------------------------------------------- CGS2 Arnoldi
+// w = V_b[j+1] is orthogonalised against the recycled C_b (s_cur vectors)
+// and V_b[0..j] with two classical Gram-Schmidt passes; coefficients go to
+// Bk (C part) and H (V part) in FP64, then w is normalised.
+template <typename T2>
+__global__ void __launch_bounds__(NT) k_ortho(int N, int j, int m, int s_cur, const int* __restrict__ list,
+                                             const int* __restrict__ count, T2* __restrict__ V,
+                                             const T2* __restrict__ C, size_t c_ss, double2* __restrict__ H,
+                                             double2* __restrict__ Bk, int smax) {
+  __shared__ double red[16 * 32];
+  __shared__ double2 coef[128];
+  const int slot = blockIdx.x;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  T2* Vb = V + (size_t)b * (m + 1) * N;
+  T2* w = Vb + (size_t)(j + 1) * N;
+  const T2* Cb = C + (size_t)b * c_ss;
+  const int nb = s_cur + j + 1;
+  auto basis = [&](int q) -> const T2* { return q < s_cur ? Cb + (size_t)q * N : Vb + (size_t)(q - s_cur) * N; };
+  double2* Hc = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
+  double2* Bc = Bk + (size_t)b * smax * m + (size_t)j * smax;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int q0 = 0; q0 < nb; q0 += 8) {
+      double acc[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc[u] = 0.0;
+      for (int e = threadIdx.x; e < N; e += NT) {
+        double2 we = to_d2(w[e]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (q0 + u < nb) {
+            double2 qe = to_d2(basis(q0 + u)[e]);
+            acc[2 * u] += qe.x * we.x + qe.y * we.y;
+            acc[2 * u + 1] += qe.x * we.y - qe.y * we.x;
+          }
+        }
+      }
+      block_sum<16>(acc, red);
+      if (threadIdx.x < 8 && q0 + threadIdx.x < nb)
+        coef[q0 + threadIdx.x] = make_double2(acc[2 * threadIdx.x], acc[2 * threadIdx.x + 1]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < N; e += NT) {
+      double2 we = to_d2(w[e]);
+      for (int q = 0; q < nb; ++q) we = csub(we, cmul(to_d2(basis(q)[e]), coef[q]));
+      w[e] = from_d2<T2>(we);
+    }
+    if (threadIdx.x < nb) {
+      int q = threadIdx.x;
+      double2 cval = coef[q];
+      if (q < s_cur) {
+        Bc[q] = pass == 0 ? cval : cadd(Bc[q], cval);
+      } else {
+        int r = q - s_cur;
+        Hc[r] = pass == 0 ? cval : cadd(Hc[r], cval);
+      }
+    }
+    __syncthreads();
+  }
+  double nr[1] = {0.0};
+  for (int e = threadIdx.x; e < N; e += NT) nr[0] += cabs2(to_d2(w[e]));
+  block_sum<1>(nr, red);
+  double nrm = sqrt(nr[0]);
+  if (threadIdx.x == 0) Hc[j + 1] = make_double2(nrm, 0.0);
+  double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int e = threadIdx.x; e < N; e += NT) w[e] = from_d2<T2>(cscale(to_d2(w[e]), inv));
+}
+
+// ------------------------------------------------------ Givens least squares
+// Column j of H (rows 0..j+1) is copied to H0 (unrotated, for the residual
+// and the harmonic-Ritz problem), rotated by the previous rotations, and a
+// new rotation zeroes H[j+1, j]. |g[j+1]| is the residual norm of the
+// projected problem; when it reaches tolabs, or H[j+1, j] vanishes
+// (breakdown: exact solution in the space), the system stops this cycle.
+__global__ void k_lsq(int j, int m, const int* __restrict__ list, const int* __restrict__ count,
+                      double2* __restrict__ H, double2* __restrict__ H0, double* __restrict__ cs,
+                      double2* __restrict__ sn, double2* __restrict__ g, const double* __restrict__ tolabs,
+                      int* __restrict__ jstop, int* __restrict__ flag, const int* __restrict__ iters_done, int maxit);
+
+// ---------------------------------------------------------------- starts
+// beta = ||r_b||, V_b[0] = r_b / beta, g = beta e1; systems already below
+// tolabs are flagged done (jstop = 0).
+template <typename T2>
+__global__ void __launch_bounds__(NT) k_cycle_start(int N, int m, const int* __restrict__ list,
+                                                   const int* __restrict__ count, const T2* __restrict__ R,
+                                                   T2* __restrict__ V, double2* __restrict__ g,
+                                                   const double* __restrict__ tolabs, int* __restrict__ flag,
+                                                   int* __restrict__ jstop, double* __restrict__ beta_out) {
+  __shared__ double red[32];
+  const int slot = blockIdx.x;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  const T2* r = R + (size_t)b * N;
+  double s[1] = {0.0};
+  for (int e = threadIdx.x; e < N; e += NT) s[0] += cabs2(to_d2(r[e]));
+  block_sum<1>(s, red);
+  double beta = sqrt(s[0]);
+  T2* v0 = V + (size_t)b * (m + 1) * N;
+  double inv = beta > 0 ? 1.0 / beta : 0.0;
+  for (int e = threadIdx.x; e < N; e += NT) v0[e] = from_d2<T2>(cscale(to_d2(r[e]), inv));
+  if (threadIdx.x == 0) {
+    double2* gb = g + (size_t)b * (m + 1);
+    gb[0] = make_double2(beta, 0.0);
+    beta_out[b] = beta;
+    bool done = !(beta > tolabs[b]);
+    flag[b] = done ? -1 : 1;  // -1: converged (status code 1)
+    jstop[b] = 0;
+  }
+}
+
+// --------------------------------------------------- cycle end: y, residual
+// Solve the rotated triangular system for y2 (length jstop), y1 = -Bk y2,
+// and the residual coefficients c = beta e1 - H0 y2 (length jstop + 1).
+// Outputs per system: coefY[0..s_cur) = y1, coefY[s_cur..s_cur+jstop) = y2,
+// coefR[0..jstop] = c.
+__global__ void k_cycle_solve(int m, int smax, int s_cur, const int* __restrict__ list,
+                              const int* __restrict__ count, const double2* __restrict__ H,
+                              const double2* __restrict__ H0, const double2* __restrict__ Bk,
+                              const double2* __restrict__ g, const double* __restrict__ beta,
+                              const int* __restrict__ jstop, double2* __restrict__ coefY, double2* __restrict__ coefR);
+
+// x_b += [U_b Z_b] coefY,  r_b = V_b[0..jstop] coefR
+template <typename T2>
+__global__ void __launch_bounds__(NT) k_update_xr(int N, int m, int smax, int s_cur, const int* __restrict__ list,
+                                                 const int* __restrict__ count, const int* __restrict__ jstop,
+                                                 const double2* __restrict__ coefY,
+                                                 const double2* __restrict__ coefR, const T2* __restrict__ U,
+                                                 const T2* __restrict__ Z, const T2* __restrict__ V,
+                                                 T2* __restrict__ X, T2* __restrict__ R) {
+  __shared__ double2 cy[128], cr[128];
+  const int slot = blockIdx.y;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  const int js = jstop[b];
+  if (js <= 0) return;
+  for (int q = threadIdx.x; q < s_cur + js; q += NT) cy[q] = coefY[(size_t)b * (m + smax + 1) + q];
+  for (int q = threadIdx.x; q <= js; q += NT) cr[q] = coefR[(size_t)b * (m + 1) + q];
+  __syncthreads();
+  const T2* Ub = U + (size_t)b * smax * N;
+  const T2* Zb = Z + (size_t)b * m * N;
+  const T2* Vb = V + (size_t)b * (m + 1) * N;
+  for (int e = blockIdx.x * NT + threadIdx.x; e < N; e += gridDim.x * NT) {
+    double2 x = to_d2(X[(size_t)b * N + e]);
+    for (int q = 0; q < s_cur; ++q) x = cfma(to_d2(Ub[(size_t)q * N + e]), cy[q], x);
+    for (int q = 0; q < js; ++q) x = cfma(to_d2(Zb[(size_t)q * N + e]), cy[s_cur + q], x);
+    X[(size_t)b * N + e] = from_d2<T2>(x);
+    double2 r = make_double2(0.0, 0.0);
+    for (int q = 0; q <= js; ++q) r = cfma(to_d2(Vb[(size_t)q * N + e]), cr[q], r);
+    R[(size_t)b * N + e] = from_d2<T2>(r);
+  }
+}
+
+// ------------------------------------------------- batched Gram: A^H B
+// out_b (na x nb, ld = ldo, system stride os) = [A segs]^H [B segs]
+template <typename T2>
+__global__ void __launch_bounds__(NT) k_gram(int N, const int* __restrict__ list, const int* __restrict__ count,
+                                            Seg2<T2> A, Seg2<T2> Bm, double2* __restrict__ out, int ldo,
+                                            size_t os) {
+  constexpr int TK = 16, MAXC = 64;
+  __shared__ double2 sa[TK][MAXC + 1], sb[TK][MAXC + 1];
+  const int slot = blockIdx.x;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  const int na = A.cnt(b), nbb = Bm.cnt(b);
+  const int nout = na * nbb;
+  double2 acc[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) acc[u] = make_double2(0.0, 0.0);
+  for (int e0 = 0; e0 < N; e0 += TK) {
+    for (int q = threadIdx.x; q < TK * MAXC; q += NT) {
+      int l = q / MAXC, c = q % MAXC;
+      int e = e0 + l;
+      sa[l][c] = (c < na && e < N) ? to_d2(A.vec(b, c)[e]) : make_double2(0.0, 0.0);
+      sb[l][c] = (c < nbb && e < N) ? to_d2(Bm.vec(b, c)[e]) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      int o = threadIdx.x + u * NT;
+      if (o < nout) {
+        int i = o % na, jj = o / na;
+        double2 a2 = acc[u];
+#pragma unroll
+        for (int l = 0; l < TK; ++l) a2 = cadd(a2, cjmul(sa[l][i], sb[l][jj]));
+        acc[u] = a2;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    int o = threadIdx.x + u * NT;
+    if (o < nout) {
+      int i = o % na, jj = o / na;
+      out[(size_t)b * os + i + (size_t)jj * ldo] = acc[u];
+    }
+  }
+}
+
+// ------------------------------------- batched tall-skinny times small matrix
+// Out_b[:, c] = sum_i In_b[i] M_b[i, c],  c < ncols (<= 16), i < In.cnt(b).
+// M_b at Msmall + b*ms (ld = ldm); with shared_in the input segments ignore b.
+template <typename T2, typename TO2>
+__global__ void __launch_bounds__(NT) k_tsmm(int N, const int* __restrict__ list, const int* __restrict__ count,
+                                            Seg2<T2> In, const double2* __restrict__ Msmall, int ldm, size_t ms,
+                                            int ncols, TO2* __restrict__ Out, size_t o_ss, size_t o_vs,
+                                            int accumulate) {
+  __shared__ double2 sm[64 * 16];
+  const int slot = blockIdx.y;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  const int ni = In.cnt(b);
+  for (int q = threadIdx.x; q < ni * ncols; q += NT) {
+    int i = q % ni, c = q / ni;
+    sm[i * 16 + c] = Msmall[(size_t)b * ms + i + (size_t)c * ldm];
+  }
+  __syncthreads();
+  for (int e = blockIdx.x * NT + threadIdx.x; e < N; e += gridDim.x * NT) {
+    double2 acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = make_double2(0.0, 0.0);
+    for (int i = 0; i < ni; ++i) {
+      double2 x = to_d2(In.vec(b, i)[e]);
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < ncols) acc[c] = cfma(x, sm[i * 16 + c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      if (c < ncols) {
+        TO2* o = Out + (size_t)b * o_ss + (size_t)c * o_vs + e;
+        double2 v = acc[c];
+        if (accumulate) v = cadd(to_d2(*o), v);
+        *o = from_d2<TO2>(v);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------ harmonic-Ritz recycle update
+// For each system (one warp): with Ghat = [[D, Bk], [0, H0]] (rows s+js+1,
+// cols s+js), F = [C V]^H [U Z] (columns of U scaled by D = 1/||U_i||),
+// solve Ghat^H Ghat z = theta Ghat^H F z for the s smallest |theta|
+// (Cholesky Ghat^H Ghat = L L^H turns it into the standard problem
+// K y = mu y, K = L^{-1} Ghat^H F L^{-H}, mu = 1/theta: largest |mu|);
+// P = L^{-H} Y_sel; QR: Ghat P = Qc R. Outputs Pu = diag(D, I) P R^{-1}
+// (new U = [U Z] Pu) and Qc (new C = [C V] Qc); ok[b] = 1 on success.
+__global__ void k_ritz(int m, int smax, int s_cur, int s_new, const int* __restrict__ list,
+                       const int* __restrict__ count, const int* __restrict__ jstop, const double2* __restrict__ H0,
+                       const double2* __restrict__ Bk, const double2* __restrict__ F, const double2* __restrict__ UU,
+                       double2* __restrict__ work, size_t wstride, double2* __restrict__ Pu,
+                       double2* __restrict__ Qc, int* __restrict__ ok);
+
+// ------------------------------------------------------- recycle start (CholQR2)
+// Given Gram G (s x s) of the current C block, Rinv = L^{-H} (upper), with
+// G = L L^H; Racc := Racc * Rinv when accumulate. ok[b] = 0 on failure.
+__global__ void k_chol_rinv(int s, const int* __restrict__ list, const int* __restrict__ count,
+                            double2* __restrict__ G, size_t gs, double2* __restrict__ Rinv,
+                            double2* __restrict__ Racc, double2* __restrict__ tmp, int accumulate,
+                            int* __restrict__ ok);
+
+// AU_b[c] = Ut[c] o (1/v_b per column block) - C0Ut[c]
+template <typename T2>
+__global__ void __launch_bounds__(NT) k_make_AU(int n, int k, int s, const int* __restrict__ list,
+                                               const int* __restrict__ count, const T2* __restrict__ Ut,
+                                               const T2* __restrict__ C0Ut, const double* __restrict__ vinv,
+                                               T2* __restrict__ AU, size_t au_ss) {
+  const int slot = blockIdx.y;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  const int N = n * k;
+  for (int e = blockIdx.x * NT + threadIdx.x; e < N * s; e += gridDim.x * NT) {
+    int t = (e % N) / n;
+    double2 u = to_d2(Ut[e]);
+    double2 cu = to_d2(C0Ut[e]);
+    AU[(size_t)b * au_ss + e] = from_d2<T2>(csub(cscale(u, vinv[(size_t)b * k + t]), cu));
+  }
+}
+
+// c = C_b^H r_b (s values): x_b += U_b c, r_b -= C_b c
+template <typename T2>
+__global__ void __launch_bounds__(NT) k_project(int N, int s, const int* __restrict__ list,
+                                               const int* __restrict__ count, const T2* __restrict__ C,
+                                               const T2* __restrict__ U, size_t ss, T2* __restrict__ X,
+                                               T2* __restrict__ R) {
+  __shared__ double red[32 * 32];
+  __shared__ double2 coef[16];
+  const int slot = blockIdx.x;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  const T2* Cb = C + (size_t)b * ss;
+  const T2* Ub = U + (size_t)b * ss;
+  T2* x = X + (size_t)b * N;
+  T2* r = R + (size_t)b * N;
+  double acc[32];
+#pragma unroll
+  for (int u = 0; u < 32; ++u) acc[u] = 0.0;
+  for (int e = threadIdx.x; e < N; e += NT) {
+    double2 re = to_d2(r[e]);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      if (q < s) {
+        double2 ce = to_d2(Cb[(size_t)q * N + e]);
+        acc[2 * q] += ce.x * re.x + ce.y * re.y;
+        acc[2 * q + 1] += ce.x * re.y - ce.y * re.x;
+      }
+    }
+  }
+  block_sum<32>(acc, red);
+  if (threadIdx.x < 16) coef[threadIdx.x] = make_double2(acc[2 * threadIdx.x], acc[2 * threadIdx.x + 1]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < N; e += NT) {
+    double2 xe = to_d2(x[e]), re = to_d2(r[e]);
+    for (int q = 0; q < s; ++q) {
+      xe = cfma(to_d2(Ub[(size_t)q * N + e]), coef[q], xe);
+      re = csub(re, cmul(to_d2(Cb[(size_t)q * N + e]), coef[q]));
+    }
+    x[e] = from_d2<T2>(xe);
+    r[e] = from_d2<T2>(re);
+  }
+}
+
+// -------------------------------------------------- block-Jacobi preconditioner
+// The block-diagonal part of T(v) (eq. (N1M1) and its (2,2) analogue; both
+// act with the same k x k matrices on the reduced unknown): for row i,
+// K_i[t, p] = delta_tp / v_t - Gd[i, p, t]  (adjoint: transpose). Apply
+// z[i, :] = K_i^{-1} r[i, :] by Gaussian elimination with partial pivoting.
+template <typename T2>
+__global__ void __launch_bounds__(NT) k_precond_bj(int n, int k, const int* __restrict__ list,
+                                                  const int* __restrict__ count, const double2* __restrict__ Gd,
+                                                  int gT, const double* __restrict__ vinv, const T2* __restrict__ In,
+                                                  size_t in_ss, T2* __restrict__ Out, size_t out_ss) {
+  const int slot = blockIdx.y;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  const int i = blockIdx.x * NT + threadIdx.x;
+  if (i >= n) return;
+  double2 K[8][9];
+  for (int t = 0; t < k; ++t) {
+    for (int p = 0; p < k; ++p) {
+      size_t gi = gT ? ((size_t)(t * k + p) * n + i) : ((size_t)(p * k + t) * n + i);
+      double2 v = cscale(Gd[gi], -1.0);
+      if (t == p) v.x += vinv[(size_t)b * k + t];
+      K[t][p] = v;
+    }
+    K[t][k] = to_d2(In[(size_t)b * in_ss + (size_t)t * n + i]);
+  }
+  for (int c = 0; c < k; ++c) {
+    int piv = c;
+    double best = cabs2(K[c][c]);
+    for (int r = c + 1; r < k; ++r) {
+      double a = cabs2(K[r][c]);
+      if (a > best) {
+        best = a;
+        piv = r;
+      }
+    }
+    if (piv != c)
+      for (int q = 0; q <= k; ++q) {
+        double2 tmp = K[c][q];
+        K[c][q] = K[piv][q];
+        K[piv][q] = tmp;
+      }
+    double2 inv = best > 0 ? crcp(K[c][c]) : make_double2(0.0, 0.0);
+    for (int r = c + 1; r < k; ++r) {
+      double2 f = cmul(K[r][c], inv);
+      for (int q = c; q <= k; ++q) K[r][q] = csub(K[r][q], cmul(f, K[c][q]));
+    }
+  }
+  double2 z[8];
+  for (int c = k - 1; c >= 0; --c) {
+    double2 x = K[c][k];
+    for (int q = c + 1; q < k; ++q) x = csub(x, cmul(K[c][q], z[q]));
+    z[c] = cabs2(K[c][c]) > 0 ? cdiv(x, K[c][c]) : make_double2(0.0, 0.0);
+  }
+  for (int t = 0; t < k; ++t) Out[(size_t)b * out_ss + (size_t)t * n + i] = from_d2<T2>(z[t]);
+}
+
+// ------------------------------------------------------------- reductions
+// out[b] = Re sum_e a_b[e] * h[e] (h shared) ; used for the trace <h, W'>
+template <typename T2>
+__global__ void __launch_bounds__(NT) k_dot_h(int N, int nsys, const T2* __restrict__ A, size_t ss,
+                                             const double2* __restrict__ h, double* __restrict__ re_out,
+                                             double* __restrict__ im_out) {
+  __shared__ double red[64];
+  const int b = blockIdx.x;
+  if (b >= nsys) return;
+  double acc[2] = {0.0, 0.0};
+  for (int e = threadIdx.x; e < N; e += NT) {
+    double2 p = cmul(to_d2(A[(size_t)b * ss + e]), h[e]);
+    acc[0] += p.x;
+    acc[1] += p.y;
+  }
+  block_sum<2>(acc, red);
+  if (threadIdx.x == 0) {
+    re_out[b] = acc[0];
+    if (im_out) im_out[b] = acc[1];
+  }
+}
+
+// out[b] = ||a_b||_2
+template <typename T2>
+__global__ void __launch_bounds__(NT) k_norms(int N, int nsys, const T2* __restrict__ A, size_t ss,
+                                             double* __restrict__ out) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  if (b >= nsys) return;
+  double acc[1] = {0.0};
+  for (int e = threadIdx.x; e < N; e += NT) acc[0] += cabs2(to_d2(A[(size_t)b * ss + e]));
+  block_sum<1>(acc, red);
+  if (threadIdx.x == 0) out[b] = sqrt(acc[0]);
+}
+
+}  // namespace kry

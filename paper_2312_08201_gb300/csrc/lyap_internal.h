@@ -1,0 +1,142 @@
+// Internal declarations of liblyap (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/lyap.h"
+
+// ------------------------------------------------------------------ errors
+// Every internal routine returns an int status (LYAP_OK or a negative code);
+// these macros turn CUDA/cuBLAS/cuSOLVER failures into codes without
+// throwing across the C ABI.
+#define LY_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      lyap_set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));            \
+      return e_ == cudaErrorMemoryAllocation ? LYAP_ENOMEM : LYAP_ECUDA;                 \
+    }                                                                                     \
+  } while (0)
+#define LY_BLAS(call)                                                                     \
+  do {                                                                                    \
+    cublasStatus_t s_ = (call);                                                           \
+    if (s_ != CUBLAS_STATUS_SUCCESS) {                                                    \
+      lyap_set_last_error(std::string(#call) + ": cublas status " + std::to_string(s_)); \
+      return LYAP_ESOLVER;                                                                \
+    }                                                                                     \
+  } while (0)
+#define LY_SOLVER(call)                                                                     \
+  do {                                                                                      \
+    cusolverStatus_t s_ = (call);                                                           \
+    if (s_ != CUSOLVER_STATUS_SUCCESS) {                                                    \
+      lyap_set_last_error(std::string(#call) + ": cusolver status " + std::to_string(s_)); \
+      return LYAP_ESOLVER;                                                                  \
+    }                                                                                       \
+  } while (0)
+#define LY_TRY(expr)              \
+  do {                            \
+    int rc_ = (expr);             \
+    if (rc_ != LYAP_OK) return rc_; \
+  } while (0)
+
+void lyap_set_last_error(const std::string& msg);
+
+// ------------------------------------------------------------ device memory
+// Owning device buffer (no exceptions; allocation reports a status code).
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t count = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), count(o.count) { o.p = nullptr; o.count = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; count = o.count; o.p = nullptr; o.count = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  int alloc(size_t n) {
+    release();
+    if (n == 0) return LYAP_OK;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      lyap_set_last_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return LYAP_ENOMEM;
+    }
+    count = n;
+    return LYAP_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    count = 0;
+  }
+  size_t bytes() const { return count * sizeof(T); }
+};
+
+// ------------------------------------------------------------------ handles
+struct lyap_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cublasHandle_t blas = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  unsigned inject_pending = 0;  // host-side fault injection consumed by the next call
+};
+
+// Recycled subspace kept across calls (and across the parameter sequence):
+// Ut (N x s, complex) spans approximate eigenvectors of T(v) for the
+// smallest |theta|; C0Ut = C0 * Ut is v-independent, so T(v) Ut =
+// Ut D(v)^{-1} - C0Ut costs O(N s) for a new v.
+template <typename R2>
+struct Recycle {
+  DevBuf<R2> Ut;
+  DevBuf<R2> C0Ut;
+  int s = 0;     // columns held (0 = none yet)
+  bool c0_valid = false;
+};
+
+struct lyap_seed {
+  lyap_ctx* ctx = nullptr;
+  int n = 0, k = 0, g = 0;
+  int real_path = 0;
+  double cond_Q = 0, f0 = 0, max_re = 0, min_sum = 0;
+  // Eigen-data (P convention): A0^T = Qp diag(lam) Qp^{-1}.
+  DevBuf<double2> lam;  // n
+  DevBuf<double2> Qp;   // n x n
+  DevBuf<double2> Qi;   // n x n
+  // Projected data (n x k each, column-major): Ub = Qi V, Vb = Qp^T U.
+  DevBuf<double2> Ub, Vb;
+  // Gd[(p*k + t)*n + i] = [Lc (Ub_p o Vb_t)]_i: diagonal blocks of N^T L0^{-1} M.
+  DevBuf<double2> Gd;
+  // Capacitance right-hand side of the shifted system T(v) W' = Ph (n x k).
+  DevBuf<double2> Ph;
+  // Trace vector: f(v) = f0 + Re sum(h o W').
+  DevBuf<double2> h;
+  double ph_norm = 0;  // ||Ph||_F
+  // Mixed path: Lc in two bf16 terms, real-split (see tc_gemm.cu).
+  DevBuf<uint16_t> Lhi, Llo;
+  int lc_ld = 0;  // padded leading dimension of the split operand
+  // Recycle spaces: primal/adjoint x FP64/FP32-inner.
+  Recycle<double2> rec64, rec64_adj;
+  Recycle<float2> rec32, rec32_adj;
+  size_t resident_bytes = 0;
+  // Solver workspaces cached across calls (owned; freed with the seed).
+  struct SeedWork* work = nullptr;
+};
+
+// ------------------------------------------------------------------ helpers
+int lyap_validate_opts(const lyap_opts* in, lyap_opts* out);
+int lyap_check_v(int nv, int k, const double* v_host);
+
+// Seed factor (seed.cu)
+int lyap_seed_build(lyap_ctx* ctx, lyap_seed* seed, const double* A0, const double* U,
+                    const double* V, const double* G, const double* E, cudaStream_t st);
