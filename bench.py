@@ -1,0 +1,324 @@
+"""Benchmark: trace(E X(v)) evaluations per second on one GB300.
+
+A step is one pass of the hot path over the 800-state damped chain
+(400 unit masses, 401 springs U[0.5, 2], alpha = 0.04, two dampers at
+random masses, seeded Haar similarity so the solver sees dense data) for
+1000 parameter pairs drawn log-uniformly on [1e-2, 1e2]^2 and ordered along
+a nearest-neighbour path: the seed stays factored on the device, and each
+step evaluates f(v) = trace(E X(v)) for all 1000 v through the library
+(capacitance solves, refinement, trace epilogue).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--precision best|fp64|bf16_ir]
+Prints one JSON line (rank 0). Multi-GPU runs are independent replicas
+(weak scaling): each rank sweeps its own copy of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "trace(EX(v)) evals/sec at rel err<=1e-8 vs FP64 path; p50/p99 request latency"
+WORKLOAD = "chain400 n=800 k=2, 1000 v log-uniform [1e-2,1e2]^2 NN-ordered, Haar-dense"
+FP64_PEAK_FLOPS_PER_CLK_SM = 4.0  # 2 FP64 FMA per clock per SM (1.25 TFLOP/s at 2070 MHz x 152 SMs)
+SMS = 152
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["best", "fp64", "bf16_ir"], default="best")
+    ap.add_argument("--cpu-sample", type=int, default=4, help="oracle evaluations in the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("swp", "sw_power_cap")):
+                if r[key].lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        loaded = [r["sm"] for r in rows if r["power"] > 200] or [r["sm"] for r in rows]
+        return dict(sm_mhz=statistics.median(loaded), sm_max_mhz=max(r["smax"] for r in rows),
+                    reasons=sorted(reasons), samples=len(rows), power_w_max=max(r["power"] for r in rows))
+
+
+# ---------------------------------------------------------------- baseline
+CPU_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle
+from workloads import workload_precision
+p, vs = workload_precision()
+sample = vs[:{count}]
+t = time.perf_counter()
+f = [oracle.trace_EX(p.A0, p.U, p.V, p.G, p.E, v) for v in sample]
+dt = time.perf_counter() - t
+print(json.dumps(dict(evals=len(sample), seconds=dt, f=f)))
+"""
+
+
+def cpu_oracle(count: int):
+    """Time the oracle on `count` parameter vectors in a fresh process using
+    every host core for BLAS (returns evals/s, cores, traces)."""
+    cores = len(os.sched_getaffinity(0))
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = str(cores)
+    r = subprocess.run([sys.executable, "-c", CPU_SNIPPET.format(root=ROOT, count=count)], capture_output=True,
+                       text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["evals"] / d["seconds"], cores, d["f"], d["seconds"]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, sm_max_mhz=2070.0), "fallback"
+
+
+# --------------------------------------------------------------- reference
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    per_step = 2
+    vals = []
+    cores = None
+    for i in range(args.warmup + args.steps):
+        rate, cores, _, secs = cpu_oracle(per_step)
+        if i >= args.warmup:
+            vals.append(secs)
+    total = sum(vals)
+    value = per_step * args.steps / total
+    line = dict(metric=METRIC, value=value, unit="evals/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1000 * total / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, sample_per_step=per_step),
+                cpu_baseline=dict(kind="oracle", value=value, unit="evals/s", cores=cores,
+                                  sample=f"first {per_step} parameter pairs of the sweep per step, "
+                                         "Bartels-Stewart per v in float64"),
+                e2e=dict(value=value, unit="evals/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- ours
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    import paper_2312_08201_gb300 as ly
+    from workloads import workload_precision
+
+    ly.build()
+    p, vs = workload_precision()
+    nv, k = vs.shape
+    ctx = ly.Context(local)
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    stats = seed.stats()
+    dev = torch.device("cuda", local)
+    v_dev = torch.tensor(vs, dtype=torch.float64, device=dev)
+
+    precision = args.precision
+    if precision == "best":
+        precision = "bf16_ir" if _mixed_available(seed, v_dev) else "fp64"
+    opts = dict(precision=ly.BF16_IR if precision == "bf16_ir" else ly.FP64)
+
+    # reference values of the FP64 GPU path (outside the timed region)
+    f64 = seed.trace_EX(v_dev, precision=ly.FP64).cpu().numpy()
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        seed.trace_EX(v_dev, **opts)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ly.prof_enable(True)
+    stream = torch.cuda.current_stream(dev)
+    evs = []
+    outs = []
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()  # evict L2 (256 MiB write) between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f, info = seed.trace_EX(v_dev, return_info=True, **opts)
+        e1.record(stream)
+        evs.append((e0, e1))
+        outs.append(f)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    prof, launches = ly.prof_read()
+    ly.prof_enable(False)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * nv * args.steps / (total_ms / 1000.0)
+
+    f_last = outs[-1].cpu().numpy()
+    acc = np.abs(f_last - f64) / np.abs(f64)
+    iters = [i["iters"] for i in info]
+    rsteps = [i["refine_steps"] for i in info]
+
+    # end to end through the public API with host buffers (pinned inputs)
+    v_pin = torch.from_numpy(vs.copy()).pin_memory()
+    v_host = v_pin.numpy()
+    seed.trace_EX(v_host, **opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fh = seed.trace_EX(v_host, **opts)
+    e2e_s = time.perf_counter() - t0
+    e2e = dict(value=nv * args.steps / e2e_s, unit="evals/s", h2d_bytes_per_step=int(nv * k * 8),
+               d2h_bytes_per_step=int(nv * 8))
+
+    # roofline of the dominant kernel (largest device time in the timed region)
+    pk, how = peaks()
+    dom_name = max(prof, key=lambda kname: prof[kname]["total_ms"]) if prof else None
+    roof = None
+    if dom_name:
+        d = prof[dom_name]
+        sec = d["total_ms"] / 1000.0
+        if dom_name == "capmv64":
+            sm_clock = float(pk.get("sm_max_mhz", 2070.0))
+            peak = FP64_PEAK_FLOPS_PER_CLK_SM * SMS * sm_clock * 1e6 / 1e12
+            ach = d["flops"] / sec / 1e12
+            roof = dict(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=None,
+                        kernel=dom_name, peak_source="FP64 FMA pipe: 152 SMs x 4 flop/clk x max SM clock",
+                        launches=d["launches"], avg_launch_ms=d["total_ms"] / d["launches"])
+        elif dom_name == "tc_gemm":
+            peak = float(pk["bf16_tflops_sustained"])
+            ach = d["flops"] / sec / 1e12
+            roof = dict(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=None,
+                        kernel=dom_name, peak_source=f"bf16 sustained ({how})", launches=d["launches"],
+                        avg_launch_ms=d["total_ms"] / d["launches"])
+        else:
+            peak = float(pk["hbm_gbs"])
+            ach = d["bytes"] / sec / 1e9
+            roof = dict(bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak, traffic=None,
+                        kernel=dom_name, peak_source=f"hbm copy ({how})", launches=d["launches"],
+                        avg_launch_ms=d["total_ms"] / d["launches"])
+    kernels = {kname: dict(launches=v["launches"], ms=round(v["total_ms"], 3),
+                           share=round(v["total_ms"] / max(1e-9, sum(x["total_ms"] for x in prof.values())), 4))
+               for kname, v in prof.items()}
+
+    line = dict(
+        metric=METRIC, value=value, unit="evals/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f64" if precision == "fp64" else "bf16x3-gemm/f32-krylov/f64-refine", data="synthetic",
+        config=dict(workload=WORKLOAD, n=int(p.n), k=int(k), nv=int(nv), precision=precision,
+                    l2="flushed between steps (256 MiB device write outside the timed events)",
+                    parallelism="replicas" if world > 1 else "single-gpu", cond_Q=stats["cond_Q"]),
+        accuracy=dict(max_rel_err_vs_fp64_path=float(acc.max()), median_rel_err=float(np.median(acc)),
+                      iters_mean=float(np.mean(iters)), refine_steps_mean=float(np.mean(rsteps))),
+        latency_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99)),
+                        request="one 1000-vector sweep"),
+        roofline=roof, kernels=kernels, e2e=e2e, gpu_launches=int(launches), clocks=clk)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, fcpu, secs = cpu_oracle(args.cpu_sample)
+        err = max(abs(a - b) / abs(b) for a, b in zip(f_last[: len(fcpu)], fcpu))
+        line["cpu_baseline"] = dict(value=rate, unit="evals/s", cores=cores, kind="oracle",
+                                    sample=f"first {len(fcpu)} of the 1000 parameter pairs, {secs:.1f} s",
+                                    max_rel_err_gpu_vs_oracle=err)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _mixed_available(seed, v_dev):
+    import paper_2312_08201_gb300 as ly
+
+    try:
+        seed.trace_EX(v_dev[:2], precision=ly.BF16_IR)
+        return True
+    except ly.LyapError:
+        return False
+
+
+if __name__ == "__main__":
+    main()

@@ -219,6 +219,26 @@ int lyap_serve_poll(lyap_server* srv, uint64_t ticket, double* trace_out, double
 int lyap_serve_cancel(lyap_server* srv, uint64_t ticket);
 void lyap_serve_destroy(lyap_server* srv);
 
+/* ------------------------------------------------------- kernel accounting
+ * For measurement only. lyap_prof_enable(1) clears the records and starts
+ * timing selected kernels with CUDA events on their launch stream, together
+ * with the algorithmic work of each launch (flops/bytes the method needs per
+ * unit times the units, e.g. system-matvecs, the launch processed);
+ * lyap_prof_enable(0) stops. lyap_prof_read synchronises the device and
+ * returns one entry per kernel that ran, plus (launches != NULL) the number
+ * of library kernel launches since the last enable. */
+typedef struct {
+  char name[32];
+  long long launches;
+  double total_ms;
+  double units;
+  double flops;
+  double bytes;
+} lyap_prof_kernel;
+
+int lyap_prof_enable(int on);
+int lyap_prof_read(lyap_prof_kernel* out, int max, int* count, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

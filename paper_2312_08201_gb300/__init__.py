@@ -84,6 +84,17 @@ class SeedStats(ctypes.Structure):
     ]
 
 
+class ProfKernel(ctypes.Structure):
+    _fields_ = [
+        ("name", ctypes.c_char * 32),
+        ("launches", ctypes.c_longlong),
+        ("total_ms", ctypes.c_double),
+        ("units", ctypes.c_double),
+        ("flops", ctypes.c_double),
+        ("bytes", ctypes.c_double),
+    ]
+
+
 class LyapError(RuntimeError):
     def __init__(self, code, what=""):
         lib = _LIB
@@ -133,6 +144,11 @@ _SIGS = {
     ),
     "lyap_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "lyap_serve_destroy": (None, [_P]),
+    "lyap_prof_enable": (ctypes.c_int, [ctypes.c_int]),
+    "lyap_prof_read": (
+        ctypes.c_int,
+        [ctypes.POINTER(ProfKernel), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)],
+    ),
 }
 
 
@@ -318,6 +334,25 @@ class Seed:
         if mem == MEM_HOST:
             return w[..., 0] + 1j * w[..., 1], _infos(info, nv)
         return w, _infos(info, nv)
+
+
+def prof_enable(on: bool = True):
+    """Start (clear) or stop the library's per-kernel event timing."""
+    _check(load().lyap_prof_enable(1 if on else 0), "lyap_prof_enable")
+
+
+def prof_read():
+    """(per-kernel records, library kernel launches since prof_enable)."""
+    arr = (ProfKernel * 16)()
+    cnt = ctypes.c_int()
+    launches = ctypes.c_longlong()
+    _check(load().lyap_prof_read(arr, 16, ctypes.byref(cnt), ctypes.byref(launches)), "lyap_prof_read")
+    recs = {
+        arr[i].name.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms, units=arr[i].units,
+                                   flops=arr[i].flops, bytes=arr[i].bytes)
+        for i in range(cnt.value)
+    }
+    return recs, launches.value
 
 
 def _infos(info, nv):

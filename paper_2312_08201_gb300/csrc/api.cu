@@ -8,6 +8,7 @@
 #include "cplx.cuh"
 #include "krylov.cuh"
 #include "lyap_internal.h"
+#include "prof.h"
 #include "mixed.h"
 #include "solver.h"
 
@@ -262,7 +263,7 @@ int report_chunk(lyap_seed* sd, SeedWork& w, int Bc, const double2* Wp, const do
   LY_TRY(w.tmp.alloc(std::max<size_t>(w.tmp.count, (size_t)Bc * N)));
   for (DevBuf<double>* r : {&w.red0, &w.red1, &w.red2, &w.red3})
     if (r->count < (size_t)Bc * k) LY_TRY(r->alloc((size_t)Bc * k));
-  kry::k_dot_h<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, Wp, N, sd->h.p, w.red0.p, nullptr);
+  kry::k_dot_h<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, Wp, N, sd->h.p, w.red0.p, nullptr); lyap_count_launch();
   // r = Ph - T(v) W'
   CapArgs64 a{};
   a.n = n;
@@ -281,10 +282,10 @@ int report_chunk(lyap_seed* sd, SeedWork& w, int Bc, const double2* Wp, const do
   a.mode = CAP_RESID;
   a.nsys = Bc;
   LY_TRY(capmv64_launch(a, st));
-  kry::k_norms<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.Rres.p, N, w.red1.p);
+  kry::k_norms<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.Rres.p, N, w.red1.p); lyap_count_launch();
   if (Zadj) {
-    k_dot_pair<<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.Rres.p, Zadj, w.red2.p);
-    k_grad<<<Bc * k, kry::NT, 0, st>>>(n, k, Bc, Wp, Zadj, w.vinv.p, w.red3.p);
+    k_dot_pair<<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.Rres.p, Zadj, w.red2.p); lyap_count_launch();
+    k_grad<<<Bc * k, kry::NT, 0, st>>>(n, k, Bc, Wp, Zadj, w.vinv.p, w.red3.p); lyap_count_launch();
   } else {
     // delta = P^{-1} r (block-Jacobi proxy for T^{-1} r); estimate <h, delta>
     SysOp<double2> op;
@@ -293,9 +294,9 @@ int report_chunk(lyap_seed* sd, SeedWork& w, int Bc, const double2* Wp, const do
     DevBuf<int> lst, cnt;
     LY_TRY(lst.alloc(Bc));
     LY_TRY(cnt.alloc(1));
-    kry::k_iota<<<grid_of(Bc), 256, 0, st>>>(Bc, lst.p, cnt.p);
+    kry::k_iota<<<grid_of(Bc), 256, 0, st>>>(Bc, lst.p, cnt.p); lyap_count_launch();
     LY_TRY(op.precond(lst.p, cnt.p, Bc, w.Rres.p, N, w.tmp.p, N, st));
-    kry::k_dot_h<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.tmp.p, N, sd->h.p, w.red2.p, nullptr);
+    kry::k_dot_h<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.tmp.p, N, sd->h.p, w.red2.p, nullptr); lyap_count_launch();
   }
   LY_CUDA(cudaGetLastError());
   std::vector<double> tr(Bc), rn(Bc), ee(Bc), gr((size_t)Bc * k);
@@ -338,7 +339,7 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
     const int Bc = std::min(B, nv - c0);
     LY_CUDA(cudaMemcpyAsync(vdev.p, io.v.data() + (size_t)c0 * k, sizeof(double) * Bc * k,
                             cudaMemcpyHostToDevice, st));
-    k_vinv<<<grid_of((size_t)Bc * k), 256, 0, st>>>(Bc * k, vdev.p, w.vinv.p);
+    k_vinv<<<grid_of((size_t)Bc * k), 256, 0, st>>>(Bc * k, vdev.p, w.vinv.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     if (o.precision == LYAP_FP64) {
       SysOp<double2> op;

@@ -10,6 +10,7 @@
 #include "capmv.cuh"
 #include "cplx.cuh"
 #include "lyap_internal.h"
+#include "prof.h"
 
 namespace {
 
@@ -127,7 +128,13 @@ int capmv64_launch(const CapArgs64& a, cudaStream_t st) {
     attr_set = true;
   }
   dim3 grid((a.n + TI - 1) / TI, (a.nsys + SB - 1) / SB);
+  // algorithmic work per system: the Cauchy-panel product, 8 flops per
+  // complex MAC over n^2 k^2 MACs, plus the O(n k^2) epilogue
+  const int ph = prof_begin(PK_CAPMV64, st);
   k_capmv64<<<grid, 256, smem, st>>>(a);
+  lyap_count_launch();
+  prof_end(ph, st, 8.0 * (double)a.n * a.n * kk + 16.0 * (double)a.n * kk,
+           2.0 * (double)a.n * a.k * sizeof(double2), a.count ? 0 : a.nsys, a.count);
   LY_CUDA(cudaGetLastError());
   return LYAP_OK;
 }

@@ -18,6 +18,7 @@
 //   diagonal blocks of N^T L0^{-1} M (eq. (N1M1)): Gd[:, p, t] = Lc (Ub_p o Vb_t).
 #include "cplx.cuh"
 #include "lyap_internal.h"
+#include "prof.h"
 
 #include <cmath>
 #include <vector>
@@ -172,8 +173,8 @@ int re_dot(const double2* a, const double2* b, size_t count, double* out_host, c
   DevBuf<double> part, res;
   LY_TRY(part.alloc(RED_BLOCKS));
   LY_TRY(res.alloc(1));
-  k_partial_dot_re<<<RED_BLOCKS, RED_THREADS, 0, st>>>(count, a, b, part.p);
-  k_finish_sum<<<1, RED_THREADS, 0, st>>>(RED_BLOCKS, part.p, res.p);
+  k_partial_dot_re<<<RED_BLOCKS, RED_THREADS, 0, st>>>(count, a, b, part.p); lyap_count_launch();
+  k_finish_sum<<<1, RED_THREADS, 0, st>>>(RED_BLOCKS, part.p, res.p); lyap_count_launch();
   LY_CUDA(cudaGetLastError());
   LY_CUDA(cudaMemcpyAsync(out_host, res.p, sizeof(double), cudaMemcpyDeviceToHost, st));
   LY_CUDA(cudaStreamSynchronize(st));
@@ -198,7 +199,7 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
   LY_TRY(W2.alloc(nn));
 
   // ---- eig(A_p), A_p = A0^T (complex FP64, right eigenvectors) ----------
-  k_transpose_to_complex<<<grid_for(nn), 256, 0, st>>>(n, A0, W1.p);
+  k_transpose_to_complex<<<grid_for(nn), 256, 0, st>>>(n, A0, W1.p); lyap_count_launch();
   LY_CUDA(cudaGetLastError());
   {
     cusolverDnParams_t params;
@@ -243,7 +244,7 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
   {
     DevBuf<double> stats;
     LY_TRY(stats.alloc(4));
-    k_lambda_stats<<<1, RED_THREADS, 0, st>>>(n, sd->lam.p, stats.p);
+    k_lambda_stats<<<1, RED_THREADS, 0, st>>>(n, sd->lam.p, stats.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     double hs[4];
     LY_CUDA(cudaMemcpyAsync(hs, stats.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -261,7 +262,7 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
   // ---- Qi = Qp^{-1} by LU -------------------------------------------------
   {
     LY_CUDA(cudaMemcpyAsync(W1.p, sd->Qp.p, nn * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    k_identity<<<grid_for(nn), 256, 0, st>>>(n, sd->Qi.p);
+    k_identity<<<grid_for(nn), 256, 0, st>>>(n, sd->Qi.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     int lwork = 0;
     LY_SOLVER(cusolverDnZgetrf_bufferSize(ctx->solver, n, n, reinterpret_cast<cuDoubleComplex*>(W1.p), n, &lwork));
@@ -294,9 +295,9 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
   LY_TRY(Vc.alloc((size_t)n * k));
   LY_TRY(Uc.alloc((size_t)n * k));
   LY_TRY(Gc.alloc((size_t)n * g));
-  k_real_to_complex<<<grid_for((size_t)n * k), 256, 0, st>>>((size_t)n * k, V, Vc.p);
-  k_real_to_complex<<<grid_for((size_t)n * k), 256, 0, st>>>((size_t)n * k, U, Uc.p);
-  k_real_to_complex<<<grid_for((size_t)n * g), 256, 0, st>>>((size_t)n * g, G, Gc.p);
+  k_real_to_complex<<<grid_for((size_t)n * k), 256, 0, st>>>((size_t)n * k, V, Vc.p); lyap_count_launch();
+  k_real_to_complex<<<grid_for((size_t)n * k), 256, 0, st>>>((size_t)n * k, U, Uc.p); lyap_count_launch();
+  k_real_to_complex<<<grid_for((size_t)n * g), 256, 0, st>>>((size_t)n * g, G, Gc.p); lyap_count_launch();
   LY_CUDA(cudaGetLastError());
   LY_TRY(sd->Ub.alloc((size_t)n * k));
   LY_TRY(sd->Vb.alloc((size_t)n * k));
@@ -308,7 +309,7 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
   LY_TRY(Gh.alloc((size_t)n * g));
   LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, g, n, one, sd->Qi.p, n, Gc.p, n, zero, Gh.p, n));
   LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, g, one, Gh.p, n, Gh.p, n, zero, W1.p, n));
-  k_cauchy_hadamard<<<grid_for(nn), 256, 0, st>>>(n, sd->lam.p, W1.p, -1.0);  // W1 = X0h
+  k_cauchy_hadamard<<<grid_for(nn), 256, 0, st>>>(n, sd->lam.p, W1.p, -1.0); lyap_count_launch();  // W1 = X0h
   LY_CUDA(cudaGetLastError());
   LY_TRY(sd->Ph.alloc((size_t)n * k));
   LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, n, one, W1.p, n, sd->Vb.p, n, zero, sd->Ph.p, n));
@@ -320,7 +321,7 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
 
   // ---- trace data: Eh = Qp^T sym(E) Qp, f0 = sum Eh o X0h, h = 2 (Eh o Lc) Ub ----
   if (E) {
-    k_sym_to_complex<<<grid_for(nn), 256, 0, st>>>(n, E, W2.p);
+    k_sym_to_complex<<<grid_for(nn), 256, 0, st>>>(n, E, W2.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     DevBuf<double2> W3;
     LY_TRY(W3.alloc(nn));
@@ -330,7 +331,7 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
     LY_TRY(zgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, n, n, n, one, sd->Qp.p, n, sd->Qp.p, n, zero, W2.p, n));
   }
   LY_TRY(re_dot(W2.p, W1.p, nn, &sd->f0, st));  // Eh, X0h symmetric: trace(Eh X0h) = sum Eh o X0h
-  k_cauchy_hadamard<<<grid_for(nn), 256, 0, st>>>(n, sd->lam.p, W2.p, 2.0);  // W2 = 2 Eh o Lc
+  k_cauchy_hadamard<<<grid_for(nn), 256, 0, st>>>(n, sd->lam.p, W2.p, 2.0); lyap_count_launch();  // W2 = 2 Eh o Lc
   LY_CUDA(cudaGetLastError());
   LY_TRY(sd->h.alloc((size_t)n * k));
   LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, n, one, W2.p, n, sd->Ub.p, n, zero, sd->h.p, n));
@@ -339,8 +340,8 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
   {
     DevBuf<double2> Y;
     LY_TRY(Y.alloc((size_t)n * k * k));
-    k_panel_products<<<grid_for((size_t)n * k * k), 256, 0, st>>>(n, k, sd->Ub.p, sd->Vb.p, Y.p);
-    k_fill_cauchy<<<grid_for(nn), 256, 0, st>>>(n, sd->lam.p, W1.p);
+    k_panel_products<<<grid_for((size_t)n * k * k), 256, 0, st>>>(n, k, sd->Ub.p, sd->Vb.p, Y.p); lyap_count_launch();
+    k_fill_cauchy<<<grid_for(nn), 256, 0, st>>>(n, sd->lam.p, W1.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     LY_TRY(sd->Gd.alloc((size_t)n * k * k));
     LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k * k, n, one, W1.p, n, Y.p, n, zero, sd->Gd.p, n));

@@ -20,6 +20,7 @@
 #include "cplx.cuh"
 #include "krylov.cuh"
 #include "solver.h"
+#include "prof.h"
 
 namespace {
 
@@ -217,13 +218,13 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
   const int g1 = (B + 255) / 256;
 
   // ---- initial state: x = 0, r = rhs ----------------------------------
-  kry::k_iota<<<g1, 256, 0, st>>>(B, Lchunk, cchunk);
-  k_zero<T2><<<512, 256, 0, st>>>((size_t)B * NS, ws.X.p);
-  k_bcast<T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(B, NS, rhs, rhs_ss, ws.R.p, NS);
-  kry::k_norms<T2><<<B, kry::NT, 0, st>>>(N, B, ws.R.p, NS, ws.tmpd.p);
+  kry::k_iota<<<g1, 256, 0, st>>>(B, Lchunk, cchunk); lyap_count_launch();
+  k_zero<T2><<<512, 256, 0, st>>>((size_t)B * NS, ws.X.p); lyap_count_launch();
+  k_bcast<T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(B, NS, rhs, rhs_ss, ws.R.p, NS); lyap_count_launch();
+  kry::k_norms<T2><<<B, kry::NT, 0, st>>>(N, B, ws.R.p, NS, ws.tmpd.p); lyap_count_launch();
   const bool have_rec = rec.s == s && s > 0 && rec.Ut.p != nullptr;
   k_init_sys<<<g1, 256, 0, st>>>(B, ws.tmpd.p, prm.tol, ws.tolabs.p, ws.iters.p, ws.flag.p, ws.hasrec.p,
-                                 have_rec ? 1 : 0);
+                                 have_rec ? 1 : 0); lyap_count_launch();
   LY_CUDA(cudaGetLastError());
 
   int s_cur = 0;
@@ -236,13 +237,13 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     }
     const size_t ss = (size_t)smax * NS;
     kry::k_make_AU<T2><<<dim3(gx(NS * s), B), kry::NT, 0, st>>>(n, k, s, Lchunk, cchunk, rec.Ut.p, rec.C0Ut.p,
-                                                                 op.vinv, ws.C.p, ss);
+                                                                 op.vinv, ws.C.p, ss); lyap_count_launch();
     // CholQR2: C = AU R^{-1}, U = Ut R^{-1}
     for (int pass = 0; pass < 2; ++pass) {
       auto cseg = seg2(seg(ws.C.p, ss, NS, s), seg(ws.C.p, ss, NS, 0));
-      kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lchunk, cchunk, cseg, cseg, ws.Gs.p, s, (size_t)smax * smax);
+      kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lchunk, cchunk, cseg, cseg, ws.Gs.p, s, (size_t)smax * smax); lyap_count_launch();
       kry::k_chol_rinv<<<(B * 32 + 255) / 256, 256, 0, st>>>(s, Lchunk, cchunk, ws.Gs.p, (size_t)smax * smax,
-                                                             ws.Rinv.p, ws.Racc.p, ws.Rtmp.p, pass, ws.ok.p);
+                                                             ws.Rinv.p, ws.Racc.p, ws.Rtmp.p, pass, ws.ok.p); lyap_count_launch();
       if (pass == 0) {
         // Racc = Rinv
         LY_CUDA(cudaMemcpyAsync(ws.Racc.p, ws.Rinv.p, sizeof(double2) * (size_t)B * s * s,
@@ -250,23 +251,23 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
       }
       // C := C Rinv (in place: each element column-set is read before written)
       kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lchunk, cchunk, cseg, ws.Rinv.p, s,
-                                                               (size_t)s * s, s, ws.C.p, ss, NS, 0);
+                                                               (size_t)s * s, s, ws.C.p, ss, NS, 0); lyap_count_launch();
     }
     // U = Ut Racc (shared input: system stride 0)
     auto useg = seg2(seg(rec.Ut.p, 0, NS, s), seg(rec.Ut.p, 0, NS, 0));
     kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lchunk, cchunk, useg, ws.Racc.p, s,
-                                                             (size_t)s * s, s, ws.U.p, ss, NS, 0);
+                                                             (size_t)s * s, s, ws.U.p, ss, NS, 0); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     std::vector<int> okh(B);
     LY_CUDA(cudaMemcpyAsync(okh.data(), ws.ok.p, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
     LY_CUDA(cudaStreamSynchronize(st));
     bool all_ok = std::all_of(okh.begin(), okh.end(), [](int v) { return v == 1; });
     if (all_ok) {
-      kry::k_project<T2><<<B, kry::NT, 0, st>>>(N, s, Lchunk, cchunk, ws.C.p, ws.U.p, ss, ws.X.p, ws.R.p);
+      kry::k_project<T2><<<B, kry::NT, 0, st>>>(N, s, Lchunk, cchunk, ws.C.p, ws.U.p, ss, ws.X.p, ws.R.p); lyap_count_launch();
       LY_CUDA(cudaGetLastError());
       s_cur = s;
     } else {
-      k_init_sys<<<g1, 256, 0, st>>>(B, ws.tmpd.p, prm.tol, ws.tolabs.p, ws.iters.p, ws.flag.p, ws.hasrec.p, 0);
+      k_init_sys<<<g1, 256, 0, st>>>(B, ws.tmpd.p, prm.tol, ws.tolabs.p, ws.iters.p, ws.flag.p, ws.hasrec.p, 0); lyap_count_launch();
       rec.c0_valid = false;
     }
   }
@@ -279,8 +280,8 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     LY_CUDA(cudaMemcpyAsync(Lstart, Lchunk, sizeof(int) * B, cudaMemcpyDeviceToDevice, st));
     LY_CUDA(cudaMemcpyAsync(cstart, cchunk, sizeof(int), cudaMemcpyDeviceToDevice, st));
     kry::k_cycle_start<T2><<<B, kry::NT, 0, st>>>(N, m, Lstart, cstart, ws.R.p, ws.V.p, ws.g.p, ws.tolabs.p,
-                                                  ws.flag.p, ws.jstop.p, ws.beta.p);
-    kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.flag.p, La, ca);
+                                                  ws.flag.p, ws.jstop.p, ws.beta.p); lyap_count_launch();
+    kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.flag.p, La, ca); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     int* Lcur = La;
     int* ccur = ca;
@@ -294,53 +295,62 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
                         (size_t)m * NS, st));
       LY_TRY(op.apply(Lcur, ccur, B, Zj + (size_t)j * NS, (size_t)m * NS, Vj + (size_t)(j + 1) * NS,
                       (size_t)(m + 1) * NS, st));
-      kry::k_ortho<T2><<<B, kry::NT, 0, st>>>(N, j, m, s_cur, Lcur, ccur, ws.V.p, ws.C.p, css, ws.H.p, ws.Bk.p,
-                                              smax);
+      {
+        // CGS2: two passes, each reading nb basis vectors twice (dots, update) and w twice
+        const int nb = s_cur + j + 1;
+        const int ph = prof_begin(PK_ORTHO, st);
+        kry::k_ortho<T2><<<B, kry::NT, 0, st>>>(N, j, m, s_cur, Lcur, ccur, ws.V.p, ws.C.p, css, ws.H.p, ws.Bk.p,
+                                                smax);
+        lyap_count_launch();
+        prof_end(ph, st, 2.0 * 2.0 * 8.0 * nb * N, (4.0 * nb + 6.0) * N * sizeof(T2), 0, ccur);
+      }
       kry::k_lsq<<<g1, 256, 0, st>>>(j, m, Lcur, ccur, ws.H.p, ws.H0.p, ws.cs.p, ws.sn.p, ws.g.p, ws.tolabs.p,
-                                     ws.jstop.p, ws.flag.p, ws.iters.p, maxit);
-      kry::k_compact<<<1, 1024, 0, st>>>(Lcur, ccur, ws.flag.p, Lnext, cnext);
+                                     ws.jstop.p, ws.flag.p, ws.iters.p, maxit); lyap_count_launch();
+      kry::k_compact<<<1, 1024, 0, st>>>(Lcur, ccur, ws.flag.p, Lnext, cnext); lyap_count_launch();
       LY_CUDA(cudaGetLastError());
       std::swap(Lcur, Lnext);
       std::swap(ccur, cnext);
     }
     // ---- cycle end -----------------------------------------------------
     kry::k_cycle_solve<<<g1, 256, 0, st>>>(m, smax, s_cur, Lstart, cstart, ws.H.p, ws.H0.p, ws.Bk.p, ws.g.p,
-                                           ws.beta.p, ws.jstop.p, ws.coefY.p, ws.coefR.p);
+                                           ws.beta.p, ws.jstop.p, ws.coefY.p, ws.coefR.p); lyap_count_launch();
     kry::k_update_xr<T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, m, smax, s_cur, Lstart, cstart, ws.jstop.p,
                                                               ws.coefY.p, ws.coefR.p, ws.U.p, ws.Z.p, ws.V.p,
-                                                              ws.X.p, ws.R.p);
-    k_add_iters<<<g1, 256, 0, st>>>(Lstart, cstart, ws.jstop.p, ws.iters.p);
+                                                              ws.X.p, ws.R.p); lyap_count_launch();
+    k_add_iters<<<g1, 256, 0, st>>>(Lstart, cstart, ws.jstop.p, ws.iters.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     // ---- recycle update (harmonic Ritz) ----------------------------------
     if (s > 0) {
       auto Vh = seg2(seg(ws.C.p, css, NS, s_cur), segd(ws.V.p, (size_t)(m + 1) * NS, NS, ws.jstop.p, 1));
       auto Wh = seg2(seg(ws.U.p, css, NS, s_cur), segd(ws.Z.p, (size_t)m * NS, NS, ws.jstop.p, 0));
-      kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lstart, cstart, Vh, Wh, ws.F.p, LD, (size_t)LD * LD);
+      kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lstart, cstart, Vh, Wh, ws.F.p, LD, (size_t)LD * LD); lyap_count_launch();
       if (s_cur > 0) {
         auto Us = seg2(seg(ws.U.p, css, NS, s_cur), seg(ws.U.p, css, NS, 0));
-        kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lstart, cstart, Us, Us, ws.UU.p, smax, (size_t)smax * smax);
+        kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lstart, cstart, Us, Us, ws.UU.p, smax, (size_t)smax * smax); lyap_count_launch();
       }
       kry::k_ritz<<<(B * 32 + 127) / 128, 128, 0, st>>>(m, smax, s_cur, s, Lstart, cstart, ws.jstop.p, ws.H0.p,
                                                         ws.Bk.p, ws.F.p, ws.UU.p, ws.work.p, ws.wstride, ws.Pu.p,
-                                                        ws.Qc.p, ws.ok.p);
+                                                        ws.Qc.p, ws.ok.p); lyap_count_launch();
       // systems whose update succeeded: new U = [U Z] Pu, C = [C V] Qc (in place)
       {
         // list of systems with ok = 1 (flag-like compaction on ok)
-        kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.ok.p, Lritz, critz);
+        kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.ok.p, Lritz, critz); lyap_count_launch();
         kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lritz, critz, Wh, ws.Pu.p, LD,
-                                                                 (size_t)LD * 16, s, ws.U.p, css, NS, 0);
+                                                                 (size_t)LD * 16, s, ws.U.p, css, NS, 0); lyap_count_launch();
         kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lritz, critz, Vh, ws.Qc.p, LD,
-                                                                 (size_t)LD * 16, s, ws.C.p, css, NS, 0);
-        k_mark_rec<<<g1, 256, 0, st>>>(Lstart, cstart, ws.ok.p, ws.hasrec.p);
-        if (s_cur == 0)
+                                                                 (size_t)LD * 16, s, ws.C.p, css, NS, 0); lyap_count_launch();
+        k_mark_rec<<<g1, 256, 0, st>>>(Lstart, cstart, ws.ok.p, ws.hasrec.p); lyap_count_launch();
+        if (s_cur == 0) {
           k_zero_failed<T2><<<dim3(gx(NS * s), B), kry::NT, 0, st>>>(NS, s, Lstart, cstart, ws.ok.p, ws.C.p,
                                                                      ws.U.p, css);
+          lyap_count_launch();
+        }
         LY_CUDA(cudaGetLastError());
       }
       s_cur = s;
     }
     // ---- next cycle: systems still running (flag > 0) ---------------------
-    kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.flag.p, Lchunk, cchunk);
+    kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.flag.p, Lchunk, cchunk); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     LY_CUDA(cudaMemcpyAsync(&chunk_count, cchunk, sizeof(int), cudaMemcpyDeviceToHost, st));
     LY_CUDA(cudaStreamSynchronize(st));
@@ -368,7 +378,7 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     const size_t off = (size_t)(B - 1) * css;
     LY_CUDA(cudaMemcpyAsync(rec.Ut.p, ws.U.p + off, sizeof(T2) * s * NS, cudaMemcpyDeviceToDevice, st));
     k_c0_from_relation<T2><<<gx(NS * s), kry::NT, 0, st>>>(n, k, s, ws.U.p + off, ws.C.p + off,
-                                                            op.vinv + (size_t)(B - 1) * k, rec.C0Ut.p);
+                                                            op.vinv + (size_t)(B - 1) * k, rec.C0Ut.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     rec.s = s;
     rec.c0_valid = true;
@@ -433,7 +443,7 @@ int SysOp<double2>::precond(const int* list, const int* count, int B, const doub
                             double2* Out, size_t out_ss, cudaStream_t st) const {
   dim3 grid((sd->n + kry::NT - 1) / kry::NT, B);
   kry::k_precond_bj<double2><<<grid, kry::NT, 0, st>>>(sd->n, sd->k, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv,
-                                                      In, in_ss, Out, out_ss);
+                                                      In, in_ss, Out, out_ss); lyap_count_launch();
   LY_CUDA(cudaGetLastError());
   return LYAP_OK;
 }
