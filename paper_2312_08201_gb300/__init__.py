@@ -1,7 +1,7 @@
 """Python binding of liblyap (argument marshalling only).
 
 Every computation runs in the CUDA library ``liblyap.so`` (built in-tree by
-``paper_2312_08201_gb300.build``); this module converts NumPy arrays or
+``paper_2312_08201_gb300.builder``); this module converts NumPy arrays or
 torch tensors to pointers, sizes and streams and back. There is no CPU
 fallback: without the compiled library (or without a GPU) calls raise.
 
@@ -165,7 +165,7 @@ def load(path: str = LIB_PATH):
     if _LIB is not None:
         return _LIB
     if not os.path.exists(path):
-        raise ImportError(f"{path} not built; run paper_2312_08201_gb300.build.build()")
+        raise ImportError(f"{path} not built; run paper_2312_08201_gb300.build()")
     lib = ctypes.CDLL(path)
     for name, (res, args) in _SIGS.items():
         fn = getattr(lib, name)
@@ -176,7 +176,7 @@ def load(path: str = LIB_PATH):
 
 
 def build(verbose: bool = False) -> str:
-    from .build import build as _b
+    from .builder import build as _b
 
     return _b(verbose=verbose)
 
