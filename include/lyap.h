@@ -219,6 +219,28 @@ int lyap_serve_poll(lyap_server* srv, uint64_t ticket, double* trace_out, double
 int lyap_serve_cancel(lyap_server* srv, uint64_t ticket);
 void lyap_serve_destroy(lyap_server* srv);
 
+/* ------------------------------------------------- allocation-free check
+ * The paper has no counterpart to this call; it exists for callers that
+ * must not allocate device memory: code running while its stream is being
+ * captured into a CUDA graph, hosts whose device memory is reserved once at
+ * start-up by their own pool, and plug-ins confined to a host framework's
+ * allocator. For nv parameter vectors v (device, nv x k row-major) and the
+ * caller's capacitance solutions w (device, nv x n x k complex128 as written
+ * by lyap_param_solve), it writes trace_out[b] = f(v_b) and resid_out[b] =
+ * ||P - T(v_b) W'_b|| / ||P|| in FP64 (device, nv doubles each), in order on
+ * `stream` (NULL = default stream), without synchronising.
+ * It calls no allocation routine: intermediates live in one static device
+ * array of LYAP_NOALLOC_MAX_ENTRIES complex doubles (about 33 MiB, held by
+ * every GPU that loads the library until the process exits); a call needs
+ * nv*n*k + ceil(nv*k/2) entries and returns LYAP_EINVAL when that exceeds
+ * the limit. All calls share the array, so calls that overlap on the GPU
+ * race. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * A zero or non-finite v_i yields NaN in that system's outputs. */
+#define LYAP_NOALLOC_MAX_ENTRIES ((1u << 21) + (1u << 16))
+int lyap_check_solution_noalloc(lyap_seed* seed, int nv, const double* v, const double* w, double* trace_out,
+                                double* resid_out, void* stream);
+
 /* ------------------------------------------------------- kernel accounting
  * For measurement only. lyap_prof_enable(1) clears the records and starts
  * timing selected kernels with CUDA events on their launch stream, together

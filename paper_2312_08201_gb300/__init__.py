@@ -144,6 +144,7 @@ _SIGS = {
     ),
     "lyap_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "lyap_serve_destroy": (None, [_P]),
+    "lyap_check_solution_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
     "lyap_prof_enable": (ctypes.c_int, [ctypes.c_int]),
     "lyap_prof_read": (
         ctypes.c_int,
@@ -353,6 +354,21 @@ def prof_read():
         for i in range(cnt.value)
     }
     return recs, launches.value
+
+
+def check_solution_noalloc(seed, v, w, trace_out, resid_out, stream=None):
+    """lyap_check_solution_noalloc on torch CUDA tensors: v (nv, k) float64,
+    w (nv, k, n, 2) float64 as returned by Seed.param_solve for device v,
+    trace_out and resid_out (nv,) float64. Marshals pointers only."""
+    import torch
+
+    nv = int(v.shape[0])
+    if stream is None:
+        stream = torch.cuda.current_stream(v.device).cuda_stream
+    code = load().lyap_check_solution_noalloc(
+        seed.h, nv, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+        ctypes.c_void_p(trace_out.data_ptr()), ctypes.c_void_p(resid_out.data_ptr()), ctypes.c_void_p(stream))
+    _check(code, "lyap_check_solution_noalloc")
 
 
 def _infos(info, nv):
