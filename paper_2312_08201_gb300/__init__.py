@@ -19,6 +19,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblyap.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "lyap.h")
+TESTING_HEADER = os.path.join(os.path.dirname(HERE), "include", "lyap_testing.h")
 
 OK = 0
 PENDING = 1
@@ -145,6 +146,8 @@ _SIGS = {
     "lyap_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "lyap_serve_destroy": (None, [_P]),
     "lyap_check_solution_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "lyap_test_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
+    "lyap_test_tc_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "lyap_prof_enable": (ctypes.c_int, [ctypes.c_int]),
     "lyap_prof_read": (
         ctypes.c_int,
@@ -153,8 +156,10 @@ _SIGS = {
 }
 
 
-def header_functions(path: str = HEADER):
-    """Names of the functions declared in include/lyap.h."""
+def header_functions(path: str | None = None):
+    """Names of the functions declared in include/lyap.h and lyap_testing.h."""
+    if path is None:
+        return sorted(set(header_functions(HEADER)) | set(header_functions(TESTING_HEADER)))
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(lyap_[a-zA-Z0-9_]+)\s*\(", text)))
@@ -369,6 +374,31 @@ def check_solution_noalloc(seed, v, w, trace_out, resid_out, stream=None):
         seed.h, nv, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(w.data_ptr()),
         ctypes.c_void_p(trace_out.data_ptr()), ctypes.c_void_p(resid_out.data_ptr()), ctypes.c_void_p(stream))
     _check(code, "lyap_check_solution_noalloc")
+
+
+def test_apply(seed, v, w, precision=FP64, adjoint=False):
+    """lyap_test_apply on torch CUDA tensors (v: (nsys, k), w: (nsys, k, n, 2))."""
+    import torch
+
+    out = torch.empty_like(w)
+    code = load().lyap_test_apply(seed.h, int(v.shape[0]), ctypes.c_void_p(v.data_ptr()),
+                                  ctypes.c_void_p(w.data_ptr()), precision, 1 if adjoint else 0,
+                                  ctypes.c_void_p(out.data_ptr()))
+    _check(code, "lyap_test_apply")
+    return out
+
+
+def test_tc_gemm(A, B):
+    """lyap_test_tc_gemm on torch CUDA float32 tensors: returns B @ A^T (N x M)."""
+    import torch
+
+    A = A.contiguous()
+    B = B.contiguous()
+    D = torch.empty((B.shape[0], A.shape[0]), dtype=torch.float32, device=A.device)
+    code = load().lyap_test_tc_gemm(int(A.shape[0]), int(B.shape[0]), int(A.shape[1]), ctypes.c_void_p(A.data_ptr()),
+                                    ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(D.data_ptr()))
+    _check(code, "lyap_test_tc_gemm")
+    return D
 
 
 def _infos(info, nv):

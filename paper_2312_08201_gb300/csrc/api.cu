@@ -214,6 +214,7 @@ extern "C" int lyap_seed_free(lyap_seed* sd) {
   if (!sd) return LYAP_EINVAL;
   cudaSetDevice(sd->ctx->device);
   delete sd->work;
+  lyap_mixed_free(sd);
   delete sd;
   return LYAP_OK;
 }

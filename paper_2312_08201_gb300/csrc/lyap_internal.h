@@ -131,6 +131,8 @@ struct lyap_seed {
   size_t resident_bytes = 0;
   // Solver workspaces cached across calls (owned; freed with the seed).
   struct SeedWork* work = nullptr;
+  // Mixed-path operands and buffers (owned; freed with the seed).
+  struct MixedState* mixed = nullptr;
 };
 
 // ------------------------------------------------------------------ helpers

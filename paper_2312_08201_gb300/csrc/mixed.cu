@@ -1,23 +1,492 @@
-// Mixed-precision path (placeholder until the tensor-core operator lands).
+// Mixed-precision path (spec addition 1, built on paper §2.1):
+//  * inner operator T~(v) in FP32 with the Cauchy-panel product on tcgen05
+//    tensor cores. The complex product Lc Z is one real GEMM with
+//      A[2i][2j] = Re Lc_ij, A[2i][2j+1] = -Im Lc_ij,
+//      A[2i+1][2j] = Im Lc_ij, A[2i+1][2j+1] = Re Lc_ij,
+//      B[col][2j] = Re Z_j,  B[col][2j+1] = Im Z_j,
+//    so D[col][2i], D[col][2i+1] are the real and imaginary parts of (Lc Z)_i.
+//    A and B are split into two BF16 terms each (x = hi + lo) and the GEMM
+//    accumulates hi*hi + hi*lo + lo*hi in FP32 (about 16 significant bits);
+//  * FP32 recycled Krylov inner solves (same batched GCRO-DR, float vectors,
+//    FP64 small matrices);
+//  * iterative refinement on the FP64 capacitance residual
+//    r = P - T(v) W (FP64 kernel), W += ||r|| * solve(T~, r/||r||), until
+//    ||r|| <= refine_tol ||P||. The trace and the update stay in FP64.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <memory>
+
+#include "cplx.cuh"
+#include "krylov.cuh"
 #include "mixed.h"
+#include "prof.h"
+#include "tc_gemm.cuh"
 
-int lyap_mixed_prepare(lyap_seed*, cudaStream_t) { return LYAP_OK; }
+struct MixedState {
+  int mpad = 0, kpad = 0;
+  DevBuf<__nv_bfloat16> Ahi, Alo;  // mpad x kpad
+  DevBuf<float2> Ub32, Vb32, Gd32;
+  int ncap = 0;
+  DevBuf<__nv_bfloat16> Bhi, Blo;  // ncap x kpad
+  DevBuf<float> D;                 // ncap x mpad
+  tc::Maps maps;
+  DevBuf<int> err;
+  // refinement work
+  int bcap = 0;
+  DevBuf<double2> R64;
+  DevBuf<float2> R32;
+  DevBuf<double> norms, vinv_c;
+  DevBuf<int> act, cnt;
+};
 
-int lyap_mixed_chunk(lyap_seed*, int, const double*, const lyap_opts&, const SolveParams&, cudaStream_t,
-                     KrylovWS<float2>&, KrylovWS<float2>&, double2*, double2*, std::vector<int>&,
-                     std::vector<int>&, std::vector<int>&) {
-  lyap_set_last_error("mixed precision path not available");
-  return LYAP_EINVAL;
+namespace {
+
+__global__ void k_build_A(int n, const double2* __restrict__ lam, int mpad, int kpad, __nv_bfloat16* __restrict__ Ah,
+                          __nv_bfloat16* __restrict__ Al) {
+  const size_t total = (size_t)mpad * kpad;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / kpad), c = (int)(idx % kpad);
+    const int i = r >> 1, j = c >> 1;
+    double v = 0.0;
+    if (i < n && j < n) {
+      double2 L = crcp(cadd(lam[i], lam[j]));
+      if ((r & 1) == 0) v = (c & 1) == 0 ? L.x : -L.y;
+      else v = (c & 1) == 0 ? L.y : L.x;
+    }
+    __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
+    __nv_bfloat16 lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
+    Ah[idx] = hi;
+    Al[idx] = lo;
+  }
 }
 
+__global__ void k_to_f32(size_t count, const double2* __restrict__ in, float2* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+// Panel columns col = slot*k^2 + p*k + t: Z[j] = W_slot[j, p] * P2[j, t],
+// stored split (hi, lo) and real-split along K (2j, 2j+1).
+template <typename T2>
+__global__ void k_panel(int n, int k, const int* __restrict__ list, const int* __restrict__ count, int nsys,
+                        const T2* __restrict__ In, size_t in_ss, const float2* __restrict__ P2, int kpad,
+                        __nv_bfloat16* __restrict__ Bh, __nv_bfloat16* __restrict__ Bl) {
+  const int slot = blockIdx.y;
+  const int ns = count ? *count : nsys;
+  if (slot >= ns) return;
+  const int b = list ? list[slot] : slot;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int kk = k * k;
+  for (int p = 0; p < k; ++p) {
+    const double2 w = to_d2(In[(size_t)b * in_ss + (size_t)p * n + j]);
+    const float2 wf = make_float2((float)w.x, (float)w.y);
+    for (int t = 0; t < k; ++t) {
+      const float2 z = cmul(wf, P2[(size_t)t * n + j]);
+      const size_t o = (size_t)(slot * kk + p * k + t) * kpad + 2 * j;
+      const __nv_bfloat16 hr = __float2bfloat16_rn(z.x), hi = __float2bfloat16_rn(z.y);
+      Bh[o] = hr;
+      Bh[o + 1] = hi;
+      Bl[o] = __float2bfloat16_rn(z.x - __bfloat162float(hr));
+      Bl[o + 1] = __float2bfloat16_rn(z.y - __bfloat162float(hi));
+    }
+  }
+}
+
+// out[i, t] = sum_p P1[i,p] (Lc Z)[i, (slot,p,t)] + sum_p W[i,p] Gd(i,p,t); then T or C0.
+template <typename T2>
+__global__ void k_epi(int n, int k, const int* __restrict__ list, const int* __restrict__ count, int nsys,
+                      const float* __restrict__ D, int ldd, const T2* __restrict__ In, size_t in_ss,
+                      const float2* __restrict__ P1, const float2* __restrict__ Gd, int gT,
+                      const double* __restrict__ vinv, int mode, T2* __restrict__ Out, size_t out_ss) {
+  const int slot = blockIdx.y;
+  const int ns = count ? *count : nsys;
+  if (slot >= ns) return;
+  const int b = list ? list[slot] : slot;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int kk = k * k;
+  const float2* D2 = reinterpret_cast<const float2*>(D);
+  const int ld2 = ldd / 2;
+  float2 w[8];
+  for (int p = 0; p < k; ++p) {
+    const double2 x = to_d2(In[(size_t)b * in_ss + (size_t)p * n + i]);
+    w[p] = make_float2((float)x.x, (float)x.y);
+  }
+  for (int t = 0; t < k; ++t) {
+    float2 o = make_float2(0.f, 0.f);
+    for (int p = 0; p < k; ++p) {
+      o = cfma(P1[(size_t)p * n + i], D2[(size_t)(slot * kk + p * k + t) * ld2 + i], o);
+      const size_t g = gT ? ((size_t)(t * k + p) * n + i) : ((size_t)(p * k + t) * n + i);
+      o = cfma(w[p], Gd[g], o);
+    }
+    float2 y = o;
+    if (mode == CAP_T) y = csub(cscale(w[t], (float)vinv[(size_t)b * k + t]), o);
+    Out[(size_t)b * out_ss + (size_t)t * n + i] = from_d2<T2>(to_d2(y));
+  }
+}
+
+__global__ void k_gather_r32(int N, int k, const int* __restrict__ act, int nact, const double2* __restrict__ R64,
+                             const double* __restrict__ norms, const double* __restrict__ vinv, float2* __restrict__ R32,
+                             double* __restrict__ vinv_c) {
+  const int c = blockIdx.y;
+  if (c >= nact) return;
+  const int b = act[c];
+  const double s = norms[b] > 0 ? 1.0 / norms[b] : 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+    const double2 r = R64[(size_t)b * N + e];
+    R32[(size_t)c * N + e] = make_float2((float)(r.x * s), (float)(r.y * s));
+  }
+  if (blockIdx.x == 0 && threadIdx.x < k) vinv_c[(size_t)c * k + threadIdx.x] = vinv[(size_t)b * k + threadIdx.x];
+}
+
+__global__ void k_scatter_add(int N, const int* __restrict__ act, int nact, const float2* __restrict__ X32,
+                              const double* __restrict__ norms, double2* __restrict__ W) {
+  const int c = blockIdx.y;
+  if (c >= nact) return;
+  const int b = act[c];
+  const double s = norms[b];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+    const float2 x = X32[(size_t)c * N + e];
+    double2 w = W[(size_t)b * N + e];
+    w.x += s * (double)x.x;
+    w.y += s * (double)x.y;
+    W[(size_t)b * N + e] = w;
+  }
+}
+
+template <typename T2>
+__global__ void k_fill_shared(int nsys, size_t N, const double2* __restrict__ src, T2* __restrict__ dst) {
+  const int b = blockIdx.y;
+  if (b >= nsys) return;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x)
+    dst[(size_t)b * N + e] = from_d2<T2>(src[e]);
+}
+
+int gx(size_t N) { return (int)std::max<size_t>(1, std::min<size_t>((N + 255) / 256, 64)); }
+
+int ensure_cols(lyap_seed* sd, int ncols) {
+  MixedState& ms = *sd->mixed;
+  if (ncols <= ms.ncap) return LYAP_OK;
+  const int cap = ((ncols + tc::BN - 1) / tc::BN) * tc::BN;
+  LY_TRY(ms.Bhi.alloc((size_t)cap * ms.kpad));
+  LY_TRY(ms.Blo.alloc((size_t)cap * ms.kpad));
+  LY_TRY(ms.D.alloc((size_t)cap * ms.mpad));
+  LY_CUDA(cudaMemset(ms.Bhi.p, 0, ms.Bhi.bytes()));  // K padding stays zero
+  LY_CUDA(cudaMemset(ms.Blo.p, 0, ms.Blo.bytes()));
+  LY_TRY(tc::make_map(&ms.maps.b_hi, ms.Bhi.p, cap, ms.kpad, tc::BN));
+  LY_TRY(tc::make_map(&ms.maps.b_lo, ms.Blo.p, cap, ms.kpad, tc::BN));
+  ms.ncap = cap;
+  return LYAP_OK;
+}
+
+template <typename T2>
+int mixed_apply(lyap_seed* sd, bool adjoint, const double* vinv, const int* list, const int* count, int nsys,
+                const T2* In, size_t in_ss, T2* Out, size_t out_ss, int mode, cudaStream_t st) {
+  MixedState& ms = *sd->mixed;
+  const int n = sd->n, k = sd->k, kk = k * k;
+  LY_TRY(ensure_cols(sd, nsys * kk));
+  const float2* P1 = adjoint ? ms.Vb32.p : ms.Ub32.p;
+  const float2* P2 = adjoint ? ms.Ub32.p : ms.Vb32.p;
+  dim3 g((n + 255) / 256, nsys);
+  k_panel<T2><<<g, 256, 0, st>>>(n, k, list, count, nsys, In, in_ss, P2, ms.kpad, ms.Bhi.p, ms.Blo.p);
+  lyap_count_launch();
+  LY_CUDA(cudaGetLastError());
+  // algorithmic work per system: 2 (real) x (2n)^2 x k^2 MACs per product, three products
+  const int ph = prof_begin(PK_TCGEMM, st);
+  LY_TRY(tc::launch(ms.maps, ms.D.p, ms.mpad, 2 * n, ms.mpad, ms.kpad, count, kk, nsys * kk, nsys * kk, ms.err.p, st));
+  prof_end(ph, st, 3.0 * 2.0 * (2.0 * n) * (2.0 * n) * kk, 0.0, count ? 0 : nsys, count);
+  const int pe = prof_begin(PK_EPI32, st);
+  k_epi<T2><<<g, 256, 0, st>>>(n, k, list, count, nsys, ms.D.p, ms.mpad, In, in_ss, P1, ms.Gd32.p, adjoint ? 1 : 0,
+                               vinv, mode, Out, out_ss);
+  lyap_count_launch();
+  prof_end(pe, st, 0.0, (double)kk * n * 8.0 + 4.0 * n * k * sizeof(T2), count ? 0 : nsys, count);
+  LY_CUDA(cudaGetLastError());
+  return LYAP_OK;
+}
+
+int ensure_refine(lyap_seed* sd, int Bc) {
+  MixedState& ms = *sd->mixed;
+  if (Bc <= ms.bcap) return LYAP_OK;
+  const size_t N = (size_t)sd->n * sd->k;
+  LY_TRY(ms.R64.alloc((size_t)Bc * N));
+  LY_TRY(ms.R32.alloc((size_t)Bc * N));
+  LY_TRY(ms.norms.alloc(Bc));
+  LY_TRY(ms.vinv_c.alloc((size_t)Bc * sd->k));
+  LY_TRY(ms.act.alloc(Bc));
+  LY_TRY(ms.cnt.alloc(1));
+  ms.bcap = Bc;
+  return LYAP_OK;
+}
+
+// Refinement for one right-hand side (shared by all systems): W (Bc x N FP64).
+int refine(lyap_seed* sd, int Bc, const double* vinv, const double2* rhs, double rhs_norm, bool adjoint,
+           Recycle<float2>& rec, const lyap_opts& o, const SolveParams& prm, cudaStream_t st, KrylovWS<float2>& ws,
+           double2* W, std::vector<int>& iters, std::vector<int>& status, std::vector<int>& rsteps) {
+  MixedState& ms = *sd->mixed;
+  const int n = sd->n, k = sd->k;
+  const int N = n * k;
+  LY_TRY(ensure_refine(sd, Bc));
+  LY_CUDA(cudaMemsetAsync(W, 0, sizeof(double2) * (size_t)Bc * N, st));
+  std::vector<int> act(Bc);
+  for (int b = 0; b < Bc; ++b) act[b] = b;
+  std::vector<double> nrm(Bc, rhs_norm);
+  SolveParams pin = prm;
+  pin.tol = o.inner_tol;
+  const int max_refine = std::max(1, o.max_refine);
+  std::vector<int> it, stt;
+  for (int step = 0;; ++step) {
+    const int nact = (int)act.size();
+    LY_CUDA(cudaMemcpyAsync(ms.act.p, act.data(), sizeof(int) * nact, cudaMemcpyHostToDevice, st));
+    LY_CUDA(cudaMemcpyAsync(ms.cnt.p, &nact, sizeof(int), cudaMemcpyHostToDevice, st));
+    if (step == 0) {
+      k_fill_shared<double2><<<dim3(gx(N), Bc), 256, 0, st>>>(Bc, N, rhs, ms.R64.p);
+      lyap_count_launch();
+      LY_CUDA(cudaMemcpyAsync(ms.norms.p, nrm.data(), sizeof(double) * Bc, cudaMemcpyHostToDevice, st));
+    } else {
+      CapArgs64 a{};
+      a.n = n;
+      a.k = k;
+      a.lam = sd->lam.p;
+      a.P1 = adjoint ? sd->Vb.p : sd->Ub.p;
+      a.P2 = adjoint ? sd->Ub.p : sd->Vb.p;
+      a.Gd = sd->Gd.p;
+      a.gT = adjoint ? 1 : 0;
+      a.W = W;
+      a.ldw = N;
+      a.vinv = vinv;
+      a.rhs = rhs;
+      a.ldr = 0;
+      a.out = ms.R64.p;
+      a.ldo = N;
+      a.mode = CAP_RESID;
+      a.list = ms.act.p;
+      a.count = ms.cnt.p;
+      a.nsys = nact;
+      LY_TRY(capmv64_launch(a, st));
+      kry::k_norms<double2><<<Bc, kry::NT, 0, st>>>(N, Bc, ms.R64.p, N, ms.norms.p);
+      lyap_count_launch();
+      LY_CUDA(cudaGetLastError());
+      LY_CUDA(cudaMemcpyAsync(nrm.data(), ms.norms.p, sizeof(double) * Bc, cudaMemcpyDeviceToHost, st));
+      LY_CUDA(cudaStreamSynchronize(st));
+      std::vector<int> keep;
+      for (int b : act) {
+        rsteps[b] = step;
+        const double rel = rhs_norm > 0 ? nrm[b] / rhs_norm : nrm[b];
+        if (!std::isfinite(rel)) status[b] = LYAP_ENONFINITE;
+        else if (rel <= o.refine_tol) status[b] = LYAP_OK;
+        else if (step >= max_refine) status[b] = LYAP_ENOCONV;
+        else keep.push_back(b);
+      }
+      act.swap(keep);
+      if (act.empty()) break;
+      const int na = (int)act.size();
+      LY_CUDA(cudaMemcpyAsync(ms.act.p, act.data(), sizeof(int) * na, cudaMemcpyHostToDevice, st));
+    }
+    const int na = (int)act.size();
+    k_gather_r32<<<dim3(gx(N), na), 256, 0, st>>>(N, k, ms.act.p, na, ms.R64.p, ms.norms.p, vinv, ms.R32.p,
+                                                  ms.vinv_c.p);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    SysOp<float2> op;
+    op.sd = sd;
+    op.adjoint = adjoint;
+    op.vinv = ms.vinv_c.p;
+    LY_TRY(gcrodr_chunk<float2>(op, na, ms.R32.p, (size_t)N, rec, pin, ws, it, stt, st));
+    k_scatter_add<<<dim3(gx(N), na), 256, 0, st>>>(N, ms.act.p, na, ws.X.p, ms.norms.p, W);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    for (int c = 0; c < na; ++c) iters[act[c]] += it[c];
+  }
+  int herr = 0;
+  LY_CUDA(cudaMemcpyAsync(&herr, ms.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LY_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    lyap_set_last_error("tensor-core GEMM wait timed out (code " + std::to_string(herr) + ")");
+    LY_CUDA(cudaMemsetAsync(ms.err.p, 0, sizeof(int), st));
+    return LYAP_EDEVICE_TIMEOUT;
+  }
+  return LYAP_OK;
+}
+
+}  // namespace
+
+void lyap_mixed_free(lyap_seed* sd) {
+  delete sd->mixed;
+  sd->mixed = nullptr;
+}
+
+int lyap_mixed_prepare(lyap_seed* sd, cudaStream_t st) {
+  std::unique_ptr<MixedState> ms(new MixedState());
+  const int n = sd->n, k = sd->k;
+  ms->mpad = ((2 * n + tc::BM - 1) / tc::BM) * tc::BM;
+  ms->kpad = ((2 * n + tc::BK - 1) / tc::BK) * tc::BK;
+  LY_TRY(ms->Ahi.alloc((size_t)ms->mpad * ms->kpad));
+  LY_TRY(ms->Alo.alloc((size_t)ms->mpad * ms->kpad));
+  k_build_A<<<gx((size_t)ms->mpad * ms->kpad) * 16, 256, 0, st>>>(n, sd->lam.p, ms->mpad, ms->kpad, ms->Ahi.p,
+                                                                  ms->Alo.p);
+  lyap_count_launch();
+  LY_CUDA(cudaGetLastError());
+  LY_TRY(ms->Ub32.alloc((size_t)n * k));
+  LY_TRY(ms->Vb32.alloc((size_t)n * k));
+  LY_TRY(ms->Gd32.alloc((size_t)n * k * k));
+  k_to_f32<<<gx((size_t)n * k), 256, 0, st>>>((size_t)n * k, sd->Ub.p, ms->Ub32.p);
+  k_to_f32<<<gx((size_t)n * k), 256, 0, st>>>((size_t)n * k, sd->Vb.p, ms->Vb32.p);
+  k_to_f32<<<gx((size_t)n * k * k), 256, 0, st>>>((size_t)n * k * k, sd->Gd.p, ms->Gd32.p);
+  lyap_count_launch(3);
+  LY_CUDA(cudaGetLastError());
+  LY_TRY(tc::make_map(&ms->maps.a_hi, ms->Ahi.p, ms->mpad, ms->kpad, tc::BM));
+  LY_TRY(tc::make_map(&ms->maps.a_lo, ms->Alo.p, ms->mpad, ms->kpad, tc::BM));
+  LY_TRY(ms->err.alloc(1));
+  LY_CUDA(cudaMemsetAsync(ms->err.p, 0, sizeof(int), st));
+  LY_CUDA(cudaStreamSynchronize(st));
+  sd->resident_bytes += ms->Ahi.bytes() + ms->Alo.bytes() + ms->Ub32.bytes() + ms->Vb32.bytes() + ms->Gd32.bytes();
+  sd->mixed = ms.release();
+  return LYAP_OK;
+}
+
+int lyap_mixed_chunk(lyap_seed* sd, int Bc, const double* vinv, const lyap_opts& o, const SolveParams& prm,
+                     cudaStream_t st, KrylovWS<float2>& ws, KrylovWS<float2>& wsadj, double2* Wp_out,
+                     double2* Zadj_out, std::vector<int>& iters, std::vector<int>& status,
+                     std::vector<int>& rsteps) {
+  if (!sd->mixed) return LYAP_EINVAL;
+  iters.assign(Bc, 0);
+  status.assign(Bc, LYAP_OK);
+  rsteps.assign(Bc, 0);
+  LY_TRY(refine(sd, Bc, vinv, sd->Ph.p, sd->ph_norm, false, sd->rec32, o, prm, st, ws, Wp_out, iters, status, rsteps));
+  if (Zadj_out) {
+    double hn = 0;
+    {
+      DevBuf<double> t;
+      LY_TRY(t.alloc(1));
+      kry::k_norms<double2><<<1, kry::NT, 0, st>>>(sd->n * sd->k, 1, sd->h.p, 0, t.p);
+      lyap_count_launch();
+      LY_CUDA(cudaMemcpyAsync(&hn, t.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+      LY_CUDA(cudaStreamSynchronize(st));
+    }
+    std::vector<int> ita(Bc, 0), sta(Bc, LYAP_OK), rsa(Bc, 0);
+    LY_TRY(refine(sd, Bc, vinv, sd->h.p, hn, true, sd->rec32_adj, o, prm, st, wsadj, Zadj_out, ita, sta, rsa));
+    for (int b = 0; b < Bc; ++b) {
+      iters[b] += ita[b];
+      rsteps[b] += rsa[b];
+      if (status[b] == LYAP_OK) status[b] = sta[b];
+    }
+  }
+  return LYAP_OK;
+}
+
+// ------------------------------------------------------------ SysOp<float2>
 template <>
-int SysOp<float2>::apply(const int*, const int*, int, const float2*, size_t, float2*, size_t, cudaStream_t) const {
-  return LYAP_EINVAL;
+int SysOp<float2>::apply(const int* list, const int* count, int B, const float2* In, size_t in_ss, float2* Out,
+                         size_t out_ss, cudaStream_t st) const {
+  return mixed_apply<float2>(sd, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, CAP_T, st);
 }
 template <>
-int SysOp<float2>::apply_c0(int, const float2*, float2*, cudaStream_t) const { return LYAP_EINVAL; }
+int SysOp<float2>::apply_c0(int nvec, const float2* In, float2* Out, cudaStream_t st) const {
+  const size_t N = (size_t)sd->n * sd->k;
+  return mixed_apply<float2>(sd, adjoint, nullptr, nullptr, nullptr, nvec, In, N, Out, N, CAP_C0, st);
+}
 template <>
-int SysOp<float2>::precond(const int*, const int*, int, const float2*, size_t, float2*, size_t,
-                           cudaStream_t) const {
-  return LYAP_EINVAL;
+int SysOp<float2>::precond(const int* list, const int* count, int B, const float2* In, size_t in_ss, float2* Out,
+                           size_t out_ss, cudaStream_t st) const {
+  dim3 grid((sd->n + kry::NT - 1) / kry::NT, B);
+  kry::k_precond_bj<float2><<<grid, kry::NT, 0, st>>>(sd->n, sd->k, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv, In,
+                                                     in_ss, Out, out_ss);
+  lyap_count_launch();
+  LY_CUDA(cudaGetLastError());
+  return LYAP_OK;
+}
+
+// ------------------------------------------------------------ testing hooks
+extern "C" int lyap_test_apply(lyap_seed* sd, int nsys, const double* v, const double* w, int precision, int adjoint,
+                               double* out) {
+  if (!sd || nsys <= 0 || !v || !w || !out) return LYAP_EINVAL;
+  LY_CUDA(cudaSetDevice(sd->ctx->device));
+  cudaStream_t st = sd->ctx->stream;
+  const int k = sd->k;
+  const size_t N = (size_t)sd->n * k;
+  DevBuf<double> vinv;
+  LY_TRY(vinv.alloc((size_t)nsys * k));
+  std::vector<double> hv((size_t)nsys * k);
+  LY_CUDA(cudaMemcpyAsync(hv.data(), v, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
+  LY_CUDA(cudaStreamSynchronize(st));
+  for (double& x : hv) x = 1.0 / x;
+  LY_CUDA(cudaMemcpyAsync(vinv.p, hv.data(), sizeof(double) * hv.size(), cudaMemcpyHostToDevice, st));
+  if (precision == LYAP_FP64) {
+    CapArgs64 a{};
+    a.n = sd->n;
+    a.k = k;
+    a.lam = sd->lam.p;
+    a.P1 = adjoint ? sd->Vb.p : sd->Ub.p;
+    a.P2 = adjoint ? sd->Ub.p : sd->Vb.p;
+    a.Gd = sd->Gd.p;
+    a.gT = adjoint ? 1 : 0;
+    a.W = reinterpret_cast<const double2*>(w);
+    a.ldw = N;
+    a.vinv = vinv.p;
+    a.out = reinterpret_cast<double2*>(out);
+    a.ldo = N;
+    a.mode = CAP_T;
+    a.nsys = nsys;
+    LY_TRY(capmv64_launch(a, st));
+  } else {
+    LY_TRY(mixed_apply<double2>(sd, adjoint != 0, vinv.p, nullptr, nullptr, nsys, reinterpret_cast<const double2*>(w),
+                                N, reinterpret_cast<double2*>(out), N, CAP_T, st));
+  }
+  LY_CUDA(cudaStreamSynchronize(st));
+  int herr = 0;
+  if (sd->mixed) LY_CUDA(cudaMemcpy(&herr, sd->mixed->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  return herr ? LYAP_EDEVICE_TIMEOUT : LYAP_OK;
+}
+
+namespace {
+__global__ void k_split_rows(int rows, int cols, int kpad, const float* __restrict__ X, __nv_bfloat16* __restrict__ H,
+                             __nv_bfloat16* __restrict__ L) {
+  const size_t total = (size_t)rows * kpad;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / kpad), c = (int)(idx % kpad);
+    const float x = c < cols ? X[(size_t)r * cols + c] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    H[idx] = h;
+    L[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+}  // namespace
+
+extern "C" int lyap_test_tc_gemm(int M, int N, int K, const float* A, const float* B, float* D) {
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !D) return LYAP_EINVAL;
+  const int mpad = ((M + tc::BM - 1) / tc::BM) * tc::BM;
+  const int kpad = ((K + tc::BK - 1) / tc::BK) * tc::BK;
+  const int ncap = ((N + tc::BN - 1) / tc::BN) * tc::BN;
+  DevBuf<__nv_bfloat16> ah, al, bh, bl;
+  DevBuf<float> Dp;
+  DevBuf<int> err;
+  LY_TRY(ah.alloc((size_t)mpad * kpad));
+  LY_TRY(al.alloc((size_t)mpad * kpad));
+  LY_TRY(bh.alloc((size_t)ncap * kpad));
+  LY_TRY(bl.alloc((size_t)ncap * kpad));
+  LY_TRY(Dp.alloc((size_t)ncap * mpad));
+  LY_TRY(err.alloc(1));
+  LY_CUDA(cudaMemset(ah.p, 0, ah.bytes()));
+  LY_CUDA(cudaMemset(al.p, 0, al.bytes()));
+  LY_CUDA(cudaMemset(bh.p, 0, bh.bytes()));
+  LY_CUDA(cudaMemset(bl.p, 0, bl.bytes()));
+  LY_CUDA(cudaMemset(err.p, 0, sizeof(int)));
+  k_split_rows<<<1024, 256>>>(M, K, kpad, A, ah.p, al.p);
+  k_split_rows<<<1024, 256>>>(N, K, kpad, B, bh.p, bl.p);
+  lyap_count_launch(2);
+  LY_CUDA(cudaGetLastError());
+  tc::Maps m;
+  LY_TRY(tc::make_map(&m.a_hi, ah.p, mpad, kpad, tc::BM));
+  LY_TRY(tc::make_map(&m.a_lo, al.p, mpad, kpad, tc::BM));
+  LY_TRY(tc::make_map(&m.b_hi, bh.p, ncap, kpad, tc::BN));
+  LY_TRY(tc::make_map(&m.b_lo, bl.p, ncap, kpad, tc::BN));
+  LY_TRY(tc::launch(m, Dp.p, mpad, M, mpad, kpad, nullptr, 1, N, N, err.p, 0));
+  LY_CUDA(cudaDeviceSynchronize());
+  int herr = 0;
+  LY_CUDA(cudaMemcpy(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  LY_CUDA(cudaMemcpy2D(D, sizeof(float) * M, Dp.p, sizeof(float) * mpad, sizeof(float) * M, N, cudaMemcpyDeviceToDevice));
+  return herr ? LYAP_EDEVICE_TIMEOUT : LYAP_OK;
 }

@@ -6,6 +6,7 @@
 
 // Build the low-precision Cauchy operands of a seed (called by the factor).
 int lyap_mixed_prepare(lyap_seed* sd, cudaStream_t st);
+void lyap_mixed_free(lyap_seed* sd);
 
 // Solve the chunk's Bc systems (vinv already in the seed work area) to the
 // FP64 residual tolerance; W' (and the adjoint Z when Zadj_out != nullptr)

@@ -1,0 +1,114 @@
+"""Mixed-precision path: the tcgen05 GEMM, the tensor-core operator, and the
+refined traces and gradients against the CPU oracle.
+
+Tolerances:
+  * GEMM: |D - A B^T| <= 2^-13 |A| |B|^T elementwise (two-term BF16 split,
+    FP32 accumulation: about 16 significant bits per product);
+  * operator: ||T~ w - T w|| <= 1e-4 ||T w|| per system;
+  * traces after refinement: 1e-8 relative to the oracle;
+  * gradients after refinement: 1e-6 relative to the largest component.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2312_08201_gb300 as ly
+from tests.gpu_common import rel_err
+from workloads import workload_precision, workload_small_fp64
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-8
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    ly.build()
+    return ly.Context(0)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (200, 300, 150), (1600, 260, 1600)])
+def test_tc_gemm_against_fp64(M, N, K):
+    import torch
+
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g, dtype=torch.float32)
+    B = torch.randn(N, K, device="cuda", generator=g, dtype=torch.float32)
+    D = ly.test_tc_gemm(A, B).double()
+    ref = B.double() @ A.double().T
+    bound = (B.double().abs() @ A.double().abs().T) * 2.0**-13
+    assert torch.all((D - ref).abs() <= bound), float(((D - ref).abs() / bound).max())
+
+
+def random_problem(seed, n, k, g, margin=1.0):
+    rng = np.random.default_rng(seed)
+    R = rng.standard_normal((n, n)) / math.sqrt(n)
+    A0 = R - (np.linalg.eigvals(R).real.max() + margin) * np.eye(n)
+    U = rng.standard_normal((n, k)) * 0.3
+    V = rng.standard_normal((n, k)) * 0.3
+    G = rng.standard_normal((n, g))
+    E = rng.standard_normal((n, n))
+    E = E @ E.T / n
+    vs = rng.uniform(0.2, 2.0, (12, k))
+    return A0, U, V, G, E, vs
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_tensor_core_operator_matches_fp64_operator(ctx, adjoint):
+    import torch
+
+    p, vs = workload_small_fp64()
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    rng = np.random.default_rng(1)
+    w = rng.standard_normal((7, p.k, p.n, 2))
+    v = torch.tensor(vs[:7], dtype=torch.float64, device="cuda")
+    wt = torch.tensor(w, dtype=torch.float64, device="cuda")
+    y64 = ly.test_apply(seed, v, wt, ly.FP64, adjoint).cpu().numpy()
+    y16 = ly.test_apply(seed, v, wt, ly.BF16_IR, adjoint).cpu().numpy()
+    for b in range(7):
+        assert np.linalg.norm(y16[b] - y64[b]) <= 1e-4 * np.linalg.norm(y64[b])
+
+
+def test_mixed_small_chain_full_sweep(ctx):
+    p, vs = workload_small_fp64()
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    f, info = seed.trace_EX(vs, return_info=True, precision=ly.BF16_IR)
+    ref = oracle.sweep(p, vs)
+    assert rel_err(f, ref).max() <= TOL_MIXED
+    assert all(i["status"] == 0 for i in info)
+    assert all(i["refine_steps"] >= 1 for i in info)
+
+
+@pytest.mark.parametrize("n,k", [(37, 3), (70, 8), (9, 1)])
+def test_mixed_general_problems(ctx, n, k):
+    A0, U, V, G, E, vs = random_problem(20 + n, n, k, 4)
+    seed = ly.Seed(ctx, A0, U, V, G, E)
+    f = seed.trace_EX(vs, precision=ly.BF16_IR)
+    ref = np.array([oracle.trace_EX(A0, U, V, G, E, v) for v in vs])
+    assert rel_err(f, ref).max() <= TOL_MIXED
+
+
+def test_mixed_gradient(ctx):
+    A0, U, V, G, E, vs = random_problem(33, 37, 3, 5)
+    seed = ly.Seed(ctx, A0, U, V, G, E)
+    f, g, info = seed.grad(vs[:4], return_info=True, precision=ly.BF16_IR)
+    for i, v in enumerate(vs[:4]):
+        fo, go = oracle.gradient(A0, U, V, G, E, v)
+        assert rel_err(f[i], fo) <= TOL_MIXED
+        assert np.abs(g[i] - go).max() <= 1e-6 * np.abs(go).max()
+
+
+def test_mixed_full_size_precision_workload_sampled(ctx):
+    """800-state chain, all 1000 parameter pairs in the bench configuration;
+    sampled outputs against the oracle, all outputs against the FP64 path."""
+    p, vs = workload_precision()
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    f16, info = seed.trace_EX(vs, return_info=True, precision=ly.BF16_IR)
+    f64 = seed.trace_EX(vs, precision=ly.FP64)
+    assert all(i["status"] == 0 for i in info)
+    assert rel_err(f16, f64).max() <= TOL_MIXED
+    idx = [0, 500, 999]
+    ref = np.array([oracle.trace_EX(p.A0, p.U, p.V, p.G, p.E, vs[i]) for i in idx])
+    assert rel_err(f16[idx], ref).max() <= TOL_MIXED
