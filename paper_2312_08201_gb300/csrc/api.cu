@@ -328,7 +328,17 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
   LY_TRY(lyap_params_from_opts(o, prm));
   if (o.precision != LYAP_FP64 && o.precision != LYAP_BF16_IR) return LYAP_EINVAL;
   SeedWork& w = *sd->work;
-  int B = o.batch > 0 ? o.batch : 256;
+  // Default batch: the whole sweep in lockstep (one recycle chain per call),
+  // capped so the Krylov workspaces use at most a quarter of free memory.
+  int B = o.batch;
+  if (B <= 0) {
+    size_t freeb = 0, totalb = 0;
+    cudaMemGetInfo(&freeb, &totalb);
+    const size_t per_sys = (size_t)(2 * o.m + 2 * o.s + 6) * N * (o.precision == LYAP_FP64 ? 16 : 8) +
+                           (size_t)((o.m + o.s + 1) * (o.m + o.s + 1) * 8) * 16;
+    const size_t cap = std::max<size_t>(1, (freeb / 4) / std::max<size_t>(per_sys, 1));
+    B = (int)std::min<size_t>(std::min<size_t>(4096, cap), (size_t)std::max(nv, 1));
+  }
   B = std::min(B, std::max(nv, 1));
   LY_TRY(w.vinv.alloc(std::max<size_t>(w.vinv.count, (size_t)B * k)));
   LY_TRY(w.Wp.alloc(std::max<size_t>(w.Wp.count, (size_t)B * N)));

@@ -2,6 +2,17 @@
 #pragma once
 #include <cuda_runtime.h>
 
+template <typename T2>
+struct RealOf;
+template <>
+struct RealOf<double2> {
+  using T = double;
+};
+template <>
+struct RealOf<float2> {
+  using T = float;
+};
+
 template <typename R>
 struct Cplx;
 template <>
@@ -51,6 +62,11 @@ __host__ __device__ __forceinline__ double2 crcp(double2 z) {
   return make_double2(z.x * d, -z.y * d);
 }
 __host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) { return cmul(a, crcp(b)); }
+__host__ __device__ __forceinline__ float2 crcp(float2 z) {
+  float d = 1.0f / (z.x * z.x + z.y * z.y);
+  return make_float2(z.x * d, -z.y * d);
+}
+__host__ __device__ __forceinline__ float2 cdiv(float2 a, float2 b) { return cmul(a, crcp(b)); }
 
 __host__ __device__ __forceinline__ double2 to_d2(double2 a) { return a; }
 __host__ __device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
@@ -60,3 +76,9 @@ template <>
 __host__ __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
 template <>
 __host__ __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+// Convert a double2 coefficient to the vector type T2.
+template <typename T2>
+__host__ __device__ __forceinline__ T2 cvt(double2 a) {
+  return from_d2<T2>(a);
+}

@@ -57,7 +57,7 @@ __global__ void k_lsq(int j, int m, const int* __restrict__ list, const int* __r
   }
   double cj;
   double2 sj;
-  sd::givens(h[j], h[j + 1], cj, sj);
+  sd::givens<double2, double>(h[j], h[j + 1], cj, sj);
   double2 rho = cadd(cscale(h[j], cj), cmul(sj, h[j + 1]));
   const double sub = h0[j + 1].x;
   h[j] = rho;
@@ -117,14 +117,23 @@ __global__ void k_cycle_solve(int m, int smax, int s_cur, const int* __restrict_
   }
 }
 
-__global__ void k_ritz(int m, int smax, int s_cur, int s_new, const int* __restrict__ list,
-                       const int* __restrict__ count, const int* __restrict__ jstop, const double2* __restrict__ H0,
-                       const double2* __restrict__ Bk, const double2* __restrict__ F, const double2* __restrict__ UU,
-                       double2* __restrict__ work, size_t wstride, double2* __restrict__ Pu,
-                       double2* __restrict__ Qc, int* __restrict__ ok) {
-  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp_global >= *count) return;
-  const int b = list[warp_global];
+// One warp (one CTA of 32 threads) per system. The generalized problem
+// Ghat^H Ghat z = theta Ghat^H Fhat z is reduced through a Householder QR
+// Ghat = Qg Rg (no normal equations): Rg z = theta (Qg^H Fhat) z, i.e.
+// K z = mu z with K = Rg^{-1} (Qg^H Fhat) and mu = 1/theta; the s largest |mu|
+// (smallest |theta|) are kept. The eigen-decomposition runs in FP32 in
+// shared memory; it only selects the recycle subspace. The part that keeps
+// the relation T U = C exact (Y = Ghat P, Y = Qc R, Pu = diag(D, I) P R^{-1})
+// runs in FP64.
+__global__ void __launch_bounds__(32) k_ritz(int m, int smax, int s_cur, int s_new, const int* __restrict__ list,
+                                           const int* __restrict__ count, const int* __restrict__ jstop,
+                                           const double2* __restrict__ H0, const double2* __restrict__ Bk,
+                                           const double2* __restrict__ F, const double2* __restrict__ UU,
+                                           double2* __restrict__ work, size_t wstride, double2* __restrict__ Pu,
+                                           double2* __restrict__ Qc, int* __restrict__ ok) {
+  const int slot = blockIdx.x;
+  if (slot >= *count) return;
+  const int b = list[slot];
   const int js = jstop[b];
   const int me = s_cur + js, re = me + 1;
   const int LD = m + smax + 1;
@@ -132,69 +141,76 @@ __global__ void k_ritz(int m, int smax, int s_cur, int s_new, const int* __restr
     if (sd::lane() == 0) ok[b] = 0;
     return;
   }
+  extern __shared__ float2 smf[];
+  float2* Gf = smf;                          // LD x LD
+  float2* Ff = Gf + (size_t)LD * LD;         // LD x LD -> Qg^H Fhat
+  float2* K = Ff + (size_t)LD * LD;          // LD x LD
+  float2* Q = K + (size_t)LD * LD;           // LD x LD
+  float2* vt = Q + (size_t)LD * LD;          // LD
+  float2* Yz = vt + LD;                      // LD x 16
+  float2* Xf = Yz + (size_t)LD * 16;         // LD x 16
+  int* sel = reinterpret_cast<int*>(Xf + (size_t)LD * 16);  // 16
   double2* w = work + (size_t)b * wstride;
-  double2* Gh = w;                       // LD x LD
-  double2* A = Gh + (size_t)LD * LD;     // LD x LD
-  double2* K = A + (size_t)LD * LD;      // LD x LD
-  double2* Q = K + (size_t)LD * LD;      // LD x LD
-  double2* Fh = Q + (size_t)LD * LD;     // LD x LD
-  double2* X = Fh + (size_t)LD * LD;     // LD x 16
-  double2* P = X + (size_t)LD * 16;      // LD x 16
-  double2* Yq = P + (size_t)LD * 16;     // LD x 16
-  double2* R = Yq + (size_t)LD * 16;     // 16 x 16
-  double2* vt = R + 256;                 // LD
-  double2* coef = vt + LD;               // LD
-  int* sel = reinterpret_cast<int*>(coef + LD);  // 16 ints
+  double2* Gh = w;                           // LD x LD (FP64)
+  double2* P = Gh + (size_t)LD * LD;         // LD x 16
+  double2* Y = P + (size_t)LD * 16;          // LD x 16
+  double2* Yq = Y + (size_t)LD * 16;         // LD x 16
+  double2* R = Yq + (size_t)LD * 16;         // 16 x 16
+  double2* coef = R + 256;                   // LD
   double D[16];
   const double2* UUb = UU + (size_t)b * smax * smax;
   for (int q = 0; q < s_cur; ++q) {
-    double nn = UUb[q + (size_t)q * smax].x;
+    const double nn = UUb[q + (size_t)q * smax].x;
     D[q] = nn > 0 ? 1.0 / sqrt(nn) : 1.0;
   }
   const double2* H0b = H0 + (size_t)b * (m + 1) * m;
   const double2* Bb = Bk + (size_t)b * smax * m;
   const double2* Fb = F + (size_t)b * LD * LD;
-  // Ghat (re x me) and Fhat (re x me)
   for (int e = sd::lane(); e < re * me; e += 32) {
-    int i = e % re, c = e / re;
+    const int i = e % re, c = e / re;
     double2 v = make_double2(0.0, 0.0);
     if (i < s_cur && c < s_cur) {
       if (i == c) v = make_double2(D[i], 0.0);
     } else if (i < s_cur) {
       v = Bb[i + (size_t)(c - s_cur) * smax];
     } else if (c >= s_cur) {
-      int ii = i - s_cur, cc = c - s_cur;
+      const int ii = i - s_cur, cc = c - s_cur;
       if (ii <= cc + 1) v = H0b[ii + (size_t)cc * (m + 1)];
     }
     Gh[i + (size_t)c * LD] = v;
+    Gf[i + (size_t)c * LD] = make_float2((float)v.x, (float)v.y);
     double2 f = Fb[i + (size_t)c * LD];
     if (c < s_cur) f = cscale(f, D[c]);
-    Fh[i + (size_t)c * LD] = f;
+    Ff[i + (size_t)c * LD] = make_float2((float)f.x, (float)f.y);
   }
   sd::wsync();
-  sd::gemm_hn(me, me, re, Gh, LD, Gh, LD, A, LD);
-  sd::gemm_hn(me, me, re, Gh, LD, Fh, LD, K, LD);
-  if (sd::cholesky(me, A, LD)) {
+  sd::householder_qr_apply<float2>(re, me, Gf, LD, Ff, LD, me, vt);
+  for (int e = sd::lane(); e < me * me; e += 32) K[(e % me) + (size_t)(e / me) * LD] = Ff[(e % me) + (size_t)(e / me) * LD];
+  sd::wsync();
+  sd::trsm_upper_left<float2>(me, me, Gf, LD, K, LD);
+  bool fin = true;
+  for (int e = sd::lane(); e < me * me; e += 32) {
+    const float2 v = K[(e % me) + (size_t)(e / me) * LD];
+    fin &= isfinite(v.x) && isfinite(v.y);
+  }
+  if (!__all_sync(0xffffffffu, fin)) {
     if (sd::lane() == 0) ok[b] = 0;
     return;
   }
-  sd::trsm_lower_left(me, me, A, LD, K, LD);
-  sd::trsm_right_lower_h(me, me, A, LD, K, LD);
-  sd::hessenberg(me, K, LD, Q, LD, vt);
-  if (sd::hqr(me, K, LD, Q, LD, 60 * me)) {
+  sd::hessenberg<float2>(me, K, LD, Q, LD, vt);
+  if (sd::hqr<float2>(me, K, LD, Q, LD, 60 * me)) {
     if (sd::lane() == 0) ok[b] = 0;
     return;
   }
-  // select s_new eigenvalues of largest |mu| (ties: lower index)
   if (sd::lane() == 0) {
     for (int c = 0; c < s_new; ++c) {
       int best = -1;
-      double bv = -1.0;
+      float bv = -1.f;
       for (int i = 0; i < me; ++i) {
         bool used = false;
         for (int q = 0; q < c; ++q) used |= sel[q] == i;
         if (used) continue;
-        double a = cabs2(K[i + (size_t)i * LD]);
+        const float a = cabs2(K[i + (size_t)i * LD]);
         if (a > bv) {
           bv = a;
           best = i;
@@ -204,39 +220,44 @@ __global__ void k_ritz(int m, int smax, int s_cur, int s_new, const int* __restr
     }
   }
   sd::wsync();
-  // Y buffer for the triangular eigenvectors: reuse Fh
-  sd::schur_vectors(me, K, LD, Q, LD, sel, s_new, Fh, LD, X, LD);
-  // P = L^{-H} X
-  for (int e = sd::lane(); e < me * s_new; e += 32) P[(e % me) + (size_t)(e / me) * LD] = X[(e % me) + (size_t)(e / me) * LD];
+  sd::schur_vectors<float2>(me, K, LD, Q, LD, sel, s_new, Yz, LD, Xf, LD);
+  for (int e = sd::lane(); e < me * s_new; e += 32) {
+    const float2 x = Xf[(e % me) + (size_t)(e / me) * LD];
+    P[(e % me) + (size_t)(e / me) * LD] = make_double2(x.x, x.y);
+  }
   sd::wsync();
-  sd::trsm_lower_h_left(me, s_new, A, LD, P, LD);
-  // Yq = Ghat P, QR
-  sd::gemm_nn(re, s_new, me, Gh, LD, P, LD, X, LD);
-  if (sd::qr_cgs2(re, s_new, X, LD, Yq, LD, R, 16, coef)) {
+  sd::gemm_nn(re, s_new, me, Gh, LD, P, LD, Y, LD);
+  if (sd::qr_cgs2(re, s_new, Y, LD, Yq, LD, R, 16, coef)) {
     if (sd::lane() == 0) ok[b] = 0;
     return;
   }
   for (int e = sd::lane(); e < s_cur * s_new; e += 32) {
-    int i = e % s_cur, c = e / s_cur;
+    const int i = e % s_cur, c = e / s_cur;
     P[i + (size_t)c * LD] = cscale(P[i + (size_t)c * LD], D[i]);
   }
   sd::wsync();
   sd::trsm_right_upper(me, s_new, R, 16, P, LD);
   bool finite = true;
   for (int e = sd::lane(); e < me * s_new; e += 32) {
-    double2 v = P[(e % me) + (size_t)(e / me) * LD];
+    const double2 v = P[(e % me) + (size_t)(e / me) * LD];
     finite &= isfinite(v.x) && isfinite(v.y);
   }
-  finite = __all_sync(0xffffffffu, finite);
-  if (!finite) {
+  if (!__all_sync(0xffffffffu, finite)) {
     if (sd::lane() == 0) ok[b] = 0;
     return;
   }
   double2* Pub = Pu + (size_t)b * LD * 16;
   double2* Qcb = Qc + (size_t)b * LD * 16;
-  for (int e = sd::lane(); e < me * s_new; e += 32) Pub[(e % me) + (size_t)(e / me) * LD] = P[(e % me) + (size_t)(e / me) * LD];
-  for (int e = sd::lane(); e < re * s_new; e += 32) Qcb[(e % re) + (size_t)(e / re) * LD] = Yq[(e % re) + (size_t)(e / re) * LD];
+  for (int e = sd::lane(); e < me * s_new; e += 32)
+    Pub[(e % me) + (size_t)(e / me) * LD] = P[(e % me) + (size_t)(e / me) * LD];
+  for (int e = sd::lane(); e < re * s_new; e += 32)
+    Qcb[(e % re) + (size_t)(e / re) * LD] = Yq[(e % re) + (size_t)(e / re) * LD];
   if (sd::lane() == 0) ok[b] = 1;
+}
+
+size_t ritz_smem_bytes(int m, int smax) {
+  const int LD = m + smax + 1;
+  return sizeof(float2) * ((size_t)4 * LD * LD + LD + (size_t)2 * LD * 16) + 16 * sizeof(int);
 }
 
 __global__ void k_chol_rinv(int s, const int* __restrict__ list, const int* __restrict__ count,

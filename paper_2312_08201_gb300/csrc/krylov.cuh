@@ -17,8 +17,8 @@ namespace kry {
 constexpr int NT = 256;  // threads per CTA for vector kernels
 
 // Sum NV doubles over the CTA (fixed shuffle tree, fixed cross-warp order).
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* red /* NV*32 */) {
+template <int NV, typename R = double>
+__device__ __forceinline__ void block_sum(R (&v)[NV], R* red /* NV*32 */) {
 #pragma unroll
   for (int i = 0; i < NV; ++i)
 #pragma unroll
@@ -32,7 +32,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red /* NV*32 
   if (warp == 0) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
-      double x = ln < nw ? red[i * 32 + ln] : 0.0;
+      R x = ln < nw ? red[i * 32 + ln] : R(0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
       if (ln == 0) red[i * 32] = x;
@@ -82,8 +82,9 @@ __global__ void __launch_bounds__(NT) k_ortho(int N, int j, int m, int s_cur, co
                                              const int* __restrict__ count, T2* __restrict__ V,
                                              const T2* __restrict__ C, size_t c_ss, double2* __restrict__ H,
                                              double2* __restrict__ Bk, int smax) {
-  __shared__ double red[16 * 32];
-  __shared__ double2 coef[128];
+  using R = typename RealOf<T2>::T;
+  __shared__ R red[32 * 32];
+  __shared__ T2 coef[128];
   const int slot = blockIdx.x;
   if (slot >= *count) return;
   const int b = list[slot];
@@ -95,50 +96,54 @@ __global__ void __launch_bounds__(NT) k_ortho(int N, int j, int m, int s_cur, co
   double2* Hc = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
   double2* Bc = Bk + (size_t)b * smax * m + (size_t)j * smax;
   for (int pass = 0; pass < 2; ++pass) {
-    for (int q0 = 0; q0 < nb; q0 += 8) {
-      double acc[16];
+    for (int q0 = 0; q0 < nb; q0 += 16) {
+      R acc[32];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) acc[u] = 0.0;
+      for (int u = 0; u < 32; ++u) acc[u] = R(0);
       for (int e = threadIdx.x; e < N; e += NT) {
-        double2 we = to_d2(w[e]);
+        const T2 we = w[e];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 16; ++u) {
           if (q0 + u < nb) {
-            double2 qe = to_d2(basis(q0 + u)[e]);
+            const T2 qe = basis(q0 + u)[e];
             acc[2 * u] += qe.x * we.x + qe.y * we.y;
             acc[2 * u + 1] += qe.x * we.y - qe.y * we.x;
           }
         }
       }
-      block_sum<16>(acc, red);
-      if (threadIdx.x < 8 && q0 + threadIdx.x < nb)
-        coef[q0 + threadIdx.x] = make_double2(acc[2 * threadIdx.x], acc[2 * threadIdx.x + 1]);
+      block_sum<32, R>(acc, red);
+      if (threadIdx.x < 16 && q0 + threadIdx.x < nb) {
+        T2 c;
+        c.x = acc[2 * threadIdx.x];
+        c.y = acc[2 * threadIdx.x + 1];
+        coef[q0 + threadIdx.x] = c;
+      }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < N; e += NT) {
-      double2 we = to_d2(w[e]);
-      for (int q = 0; q < nb; ++q) we = csub(we, cmul(to_d2(basis(q)[e]), coef[q]));
-      w[e] = from_d2<T2>(we);
+      T2 we = w[e];
+      for (int q = 0; q < nb; ++q) we = csub(we, cmul(basis(q)[e], coef[q]));
+      w[e] = we;
     }
     if (threadIdx.x < nb) {
-      int q = threadIdx.x;
-      double2 cval = coef[q];
+      const int q = threadIdx.x;
+      const double2 cval = to_d2(coef[q]);
       if (q < s_cur) {
         Bc[q] = pass == 0 ? cval : cadd(Bc[q], cval);
       } else {
-        int r = q - s_cur;
+        const int r = q - s_cur;
         Hc[r] = pass == 0 ? cval : cadd(Hc[r], cval);
       }
     }
     __syncthreads();
   }
-  double nr[1] = {0.0};
-  for (int e = threadIdx.x; e < N; e += NT) nr[0] += cabs2(to_d2(w[e]));
-  block_sum<1>(nr, red);
-  double nrm = sqrt(nr[0]);
+  R nr[1] = {R(0)};
+  for (int e = threadIdx.x; e < N; e += NT) nr[0] += cabs2(w[e]);
+  block_sum<1, R>(nr, red);
+  const double nrm = sqrt((double)nr[0]);
   if (threadIdx.x == 0) Hc[j + 1] = make_double2(nrm, 0.0);
-  double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-  for (int e = threadIdx.x; e < N; e += NT) w[e] = from_d2<T2>(cscale(to_d2(w[e]), inv));
+  const R inv = nrm > 0.0 ? (R)(1.0 / nrm) : R(0);
+  for (int e = threadIdx.x; e < N; e += NT) w[e] = cscale(w[e], inv);
 }
 
 // ------------------------------------------------------ Givens least squares
@@ -161,18 +166,19 @@ __global__ void __launch_bounds__(NT) k_cycle_start(int N, int m, const int* __r
                                                    T2* __restrict__ V, double2* __restrict__ g,
                                                    const double* __restrict__ tolabs, int* __restrict__ flag,
                                                    int* __restrict__ jstop, double* __restrict__ beta_out) {
-  __shared__ double red[32];
+  using RT = typename RealOf<T2>::T;
+  __shared__ RT red[32];
   const int slot = blockIdx.x;
   if (slot >= *count) return;
   const int b = list[slot];
   const T2* r = R + (size_t)b * N;
-  double s[1] = {0.0};
-  for (int e = threadIdx.x; e < N; e += NT) s[0] += cabs2(to_d2(r[e]));
-  block_sum<1>(s, red);
-  double beta = sqrt(s[0]);
+  RT s[1] = {RT(0)};
+  for (int e = threadIdx.x; e < N; e += NT) s[0] += cabs2(r[e]);
+  block_sum<1, RT>(s, red);
+  double beta = sqrt((double)s[0]);
   T2* v0 = V + (size_t)b * (m + 1) * N;
-  double inv = beta > 0 ? 1.0 / beta : 0.0;
-  for (int e = threadIdx.x; e < N; e += NT) v0[e] = from_d2<T2>(cscale(to_d2(r[e]), inv));
+  const RT inv = beta > 0 ? (RT)(1.0 / beta) : RT(0);
+  for (int e = threadIdx.x; e < N; e += NT) v0[e] = cscale(r[e], inv);
   if (threadIdx.x == 0) {
     double2* gb = g + (size_t)b * (m + 1);
     gb[0] = make_double2(beta, 0.0);
@@ -202,26 +208,26 @@ __global__ void __launch_bounds__(NT) k_update_xr(int N, int m, int smax, int s_
                                                  const double2* __restrict__ coefR, const T2* __restrict__ U,
                                                  const T2* __restrict__ Z, const T2* __restrict__ V,
                                                  T2* __restrict__ X, T2* __restrict__ R) {
-  __shared__ double2 cy[128], cr[128];
+  __shared__ T2 cy[128], cr[128];
   const int slot = blockIdx.y;
   if (slot >= *count) return;
   const int b = list[slot];
   const int js = jstop[b];
   if (js <= 0) return;
-  for (int q = threadIdx.x; q < s_cur + js; q += NT) cy[q] = coefY[(size_t)b * (m + smax + 1) + q];
-  for (int q = threadIdx.x; q <= js; q += NT) cr[q] = coefR[(size_t)b * (m + 1) + q];
+  for (int q = threadIdx.x; q < s_cur + js; q += NT) cy[q] = cvt<T2>(coefY[(size_t)b * (m + smax + 1) + q]);
+  for (int q = threadIdx.x; q <= js; q += NT) cr[q] = cvt<T2>(coefR[(size_t)b * (m + 1) + q]);
   __syncthreads();
   const T2* Ub = U + (size_t)b * smax * N;
   const T2* Zb = Z + (size_t)b * m * N;
   const T2* Vb = V + (size_t)b * (m + 1) * N;
   for (int e = blockIdx.x * NT + threadIdx.x; e < N; e += gridDim.x * NT) {
-    double2 x = to_d2(X[(size_t)b * N + e]);
-    for (int q = 0; q < s_cur; ++q) x = cfma(to_d2(Ub[(size_t)q * N + e]), cy[q], x);
-    for (int q = 0; q < js; ++q) x = cfma(to_d2(Zb[(size_t)q * N + e]), cy[s_cur + q], x);
-    X[(size_t)b * N + e] = from_d2<T2>(x);
-    double2 r = make_double2(0.0, 0.0);
-    for (int q = 0; q <= js; ++q) r = cfma(to_d2(Vb[(size_t)q * N + e]), cr[q], r);
-    R[(size_t)b * N + e] = from_d2<T2>(r);
+    T2 x = X[(size_t)b * N + e];
+    for (int q = 0; q < s_cur; ++q) x = cfma(Ub[(size_t)q * N + e], cy[q], x);
+    for (int q = 0; q < js; ++q) x = cfma(Zb[(size_t)q * N + e], cy[s_cur + q], x);
+    X[(size_t)b * N + e] = x;
+    T2 r = cvt<T2>(make_double2(0.0, 0.0));
+    for (int q = 0; q <= js; ++q) r = cfma(Vb[(size_t)q * N + e], cr[q], r);
+    R[(size_t)b * N + e] = r;
   }
 }
 
@@ -232,7 +238,7 @@ __global__ void __launch_bounds__(NT) k_gram(int N, const int* __restrict__ list
                                             Seg2<T2> A, Seg2<T2> Bm, double2* __restrict__ out, int ldo,
                                             size_t os) {
   constexpr int TK = 16, MAXC = 64;
-  __shared__ double2 sa[TK][MAXC + 1], sb[TK][MAXC + 1];
+  __shared__ T2 sa[TK][MAXC + 1], sb[TK][MAXC + 1];
   const int slot = blockIdx.x;
   if (slot >= *count) return;
   const int b = list[slot];
@@ -245,8 +251,9 @@ __global__ void __launch_bounds__(NT) k_gram(int N, const int* __restrict__ list
     for (int q = threadIdx.x; q < TK * MAXC; q += NT) {
       int l = q / MAXC, c = q % MAXC;
       int e = e0 + l;
-      sa[l][c] = (c < na && e < N) ? to_d2(A.vec(b, c)[e]) : make_double2(0.0, 0.0);
-      sb[l][c] = (c < nbb && e < N) ? to_d2(Bm.vec(b, c)[e]) : make_double2(0.0, 0.0);
+      const T2 z = cvt<T2>(make_double2(0.0, 0.0));
+      sa[l][c] = (c < na && e < N) ? A.vec(b, c)[e] : z;
+      sb[l][c] = (c < nbb && e < N) ? Bm.vec(b, c)[e] : z;
     }
     __syncthreads();
 #pragma unroll
@@ -254,10 +261,10 @@ __global__ void __launch_bounds__(NT) k_gram(int N, const int* __restrict__ list
       int o = threadIdx.x + u * NT;
       if (o < nout) {
         int i = o % na, jj = o / na;
-        double2 a2 = acc[u];
+        T2 t = cvt<T2>(make_double2(0.0, 0.0));
 #pragma unroll
-        for (int l = 0; l < TK; ++l) a2 = cadd(a2, cjmul(sa[l][i], sb[l][jj]));
-        acc[u] = a2;
+        for (int l = 0; l < TK; ++l) t = cadd(t, cjmul(sa[l][i], sb[l][jj]));
+        acc[u] = cadd(acc[u], to_d2(t));
       }
     }
     __syncthreads();
@@ -280,22 +287,22 @@ __global__ void __launch_bounds__(NT) k_tsmm(int N, const int* __restrict__ list
                                             Seg2<T2> In, const double2* __restrict__ Msmall, int ldm, size_t ms,
                                             int ncols, TO2* __restrict__ Out, size_t o_ss, size_t o_vs,
                                             int accumulate) {
-  __shared__ double2 sm[64 * 16];
+  __shared__ T2 sm[64 * 16];
   const int slot = blockIdx.y;
   if (slot >= *count) return;
   const int b = list[slot];
   const int ni = In.cnt(b);
   for (int q = threadIdx.x; q < ni * ncols; q += NT) {
     int i = q % ni, c = q / ni;
-    sm[i * 16 + c] = Msmall[(size_t)b * ms + i + (size_t)c * ldm];
+    sm[i * 16 + c] = cvt<T2>(Msmall[(size_t)b * ms + i + (size_t)c * ldm]);
   }
   __syncthreads();
   for (int e = blockIdx.x * NT + threadIdx.x; e < N; e += gridDim.x * NT) {
-    double2 acc[16];
+    T2 acc[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < 16; ++c) acc[c] = cvt<T2>(make_double2(0.0, 0.0));
     for (int i = 0; i < ni; ++i) {
-      double2 x = to_d2(In.vec(b, i)[e]);
+      const T2 x = In.vec(b, i)[e];
 #pragma unroll
       for (int c = 0; c < 16; ++c)
         if (c < ncols) acc[c] = cfma(x, sm[i * 16 + c], acc[c]);
@@ -304,7 +311,7 @@ __global__ void __launch_bounds__(NT) k_tsmm(int N, const int* __restrict__ list
     for (int c = 0; c < 16; ++c) {
       if (c < ncols) {
         TO2* o = Out + (size_t)b * o_ss + (size_t)c * o_vs + e;
-        double2 v = acc[c];
+        double2 v = to_d2(acc[c]);
         if (accumulate) v = cadd(to_d2(*o), v);
         *o = from_d2<TO2>(v);
       }
@@ -325,6 +332,8 @@ __global__ void k_ritz(int m, int smax, int s_cur, int s_new, const int* __restr
                        const double2* __restrict__ Bk, const double2* __restrict__ F, const double2* __restrict__ UU,
                        double2* __restrict__ work, size_t wstride, double2* __restrict__ Pu,
                        double2* __restrict__ Qc, int* __restrict__ ok);
+// Dynamic shared memory of k_ritz (launched with 32 threads per CTA, one CTA per system).
+size_t ritz_smem_bytes(int m, int smax);
 
 // ------------------------------------------------------- recycle start (CholQR2)
 // Given Gram G (s x s) of the current C block, Rinv = L^{-H} (upper), with
@@ -358,8 +367,9 @@ __global__ void __launch_bounds__(NT) k_project(int N, int s, const int* __restr
                                                const int* __restrict__ count, const T2* __restrict__ C,
                                                const T2* __restrict__ U, size_t ss, T2* __restrict__ X,
                                                T2* __restrict__ R) {
-  __shared__ double red[32 * 32];
-  __shared__ double2 coef[16];
+  using RT = typename RealOf<T2>::T;
+  __shared__ RT red[32 * 32];
+  __shared__ T2 coef[16];
   const int slot = blockIdx.x;
   if (slot >= *count) return;
   const int b = list[slot];
@@ -367,31 +377,36 @@ __global__ void __launch_bounds__(NT) k_project(int N, int s, const int* __restr
   const T2* Ub = U + (size_t)b * ss;
   T2* x = X + (size_t)b * N;
   T2* r = R + (size_t)b * N;
-  double acc[32];
+  RT acc[32];
 #pragma unroll
-  for (int u = 0; u < 32; ++u) acc[u] = 0.0;
+  for (int u = 0; u < 32; ++u) acc[u] = RT(0);
   for (int e = threadIdx.x; e < N; e += NT) {
-    double2 re = to_d2(r[e]);
+    const T2 re = r[e];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       if (q < s) {
-        double2 ce = to_d2(Cb[(size_t)q * N + e]);
+        const T2 ce = Cb[(size_t)q * N + e];
         acc[2 * q] += ce.x * re.x + ce.y * re.y;
         acc[2 * q + 1] += ce.x * re.y - ce.y * re.x;
       }
     }
   }
-  block_sum<32>(acc, red);
-  if (threadIdx.x < 16) coef[threadIdx.x] = make_double2(acc[2 * threadIdx.x], acc[2 * threadIdx.x + 1]);
+  block_sum<32, RT>(acc, red);
+  if (threadIdx.x < 16) {
+    T2 c;
+    c.x = acc[2 * threadIdx.x];
+    c.y = acc[2 * threadIdx.x + 1];
+    coef[threadIdx.x] = c;
+  }
   __syncthreads();
   for (int e = threadIdx.x; e < N; e += NT) {
-    double2 xe = to_d2(x[e]), re = to_d2(r[e]);
+    T2 xe = x[e], re = r[e];
     for (int q = 0; q < s; ++q) {
-      xe = cfma(to_d2(Ub[(size_t)q * N + e]), coef[q], xe);
-      re = csub(re, cmul(to_d2(Cb[(size_t)q * N + e]), coef[q]));
+      xe = cfma(Ub[(size_t)q * N + e], coef[q], xe);
+      re = csub(re, cmul(Cb[(size_t)q * N + e], coef[q]));
     }
-    x[e] = from_d2<T2>(xe);
-    r[e] = from_d2<T2>(re);
+    x[e] = xe;
+    r[e] = re;
   }
 }
 
@@ -410,21 +425,22 @@ __global__ void __launch_bounds__(NT) k_precond_bj(int n, int k, const int* __re
   const int b = list[slot];
   const int i = blockIdx.x * NT + threadIdx.x;
   if (i >= n) return;
-  double2 K[8][9];
+  using RT = typename RealOf<T2>::T;
+  T2 K[8][9];
   for (int t = 0; t < k; ++t) {
     for (int p = 0; p < k; ++p) {
       size_t gi = gT ? ((size_t)(t * k + p) * n + i) : ((size_t)(p * k + t) * n + i);
       double2 v = cscale(Gd[gi], -1.0);
       if (t == p) v.x += vinv[(size_t)b * k + t];
-      K[t][p] = v;
+      K[t][p] = cvt<T2>(v);
     }
-    K[t][k] = to_d2(In[(size_t)b * in_ss + (size_t)t * n + i]);
+    K[t][k] = In[(size_t)b * in_ss + (size_t)t * n + i];
   }
   for (int c = 0; c < k; ++c) {
     int piv = c;
-    double best = cabs2(K[c][c]);
+    RT best = cabs2(K[c][c]);
     for (int r = c + 1; r < k; ++r) {
-      double a = cabs2(K[r][c]);
+      RT a = cabs2(K[r][c]);
       if (a > best) {
         best = a;
         piv = r;
@@ -432,23 +448,25 @@ __global__ void __launch_bounds__(NT) k_precond_bj(int n, int k, const int* __re
     }
     if (piv != c)
       for (int q = 0; q <= k; ++q) {
-        double2 tmp = K[c][q];
+        T2 tmp = K[c][q];
         K[c][q] = K[piv][q];
         K[piv][q] = tmp;
       }
-    double2 inv = best > 0 ? crcp(K[c][c]) : make_double2(0.0, 0.0);
+    const T2 zero = cvt<T2>(make_double2(0.0, 0.0));
+    const T2 inv = best > 0 ? cscale(cconj(K[c][c]), (RT)1 / best) : zero;
     for (int r = c + 1; r < k; ++r) {
-      double2 f = cmul(K[r][c], inv);
+      const T2 f = cmul(K[r][c], inv);
       for (int q = c; q <= k; ++q) K[r][q] = csub(K[r][q], cmul(f, K[c][q]));
     }
   }
-  double2 z[8];
+  T2 z[8];
   for (int c = k - 1; c >= 0; --c) {
-    double2 x = K[c][k];
+    T2 x = K[c][k];
     for (int q = c + 1; q < k; ++q) x = csub(x, cmul(K[c][q], z[q]));
-    z[c] = cabs2(K[c][c]) > 0 ? cdiv(x, K[c][c]) : make_double2(0.0, 0.0);
+    const RT d = cabs2(K[c][c]);
+    z[c] = d > 0 ? cscale(cmul(x, cconj(K[c][c])), (RT)1 / d) : cvt<T2>(make_double2(0.0, 0.0));
   }
-  for (int t = 0; t < k; ++t) Out[(size_t)b * out_ss + (size_t)t * n + i] = from_d2<T2>(z[t]);
+  for (int t = 0; t < k; ++t) Out[(size_t)b * out_ss + (size_t)t * n + i] = z[t];
 }
 
 // ------------------------------------------------------------- reductions
@@ -477,13 +495,14 @@ __global__ void __launch_bounds__(NT) k_dot_h(int N, int nsys, const T2* __restr
 template <typename T2>
 __global__ void __launch_bounds__(NT) k_norms(int N, int nsys, const T2* __restrict__ A, size_t ss,
                                              double* __restrict__ out) {
-  __shared__ double red[32];
+  using RT = typename RealOf<T2>::T;
+  __shared__ RT red[32];
   const int b = blockIdx.x;
   if (b >= nsys) return;
-  double acc[1] = {0.0};
-  for (int e = threadIdx.x; e < N; e += NT) acc[0] += cabs2(to_d2(A[(size_t)b * ss + e]));
-  block_sum<1>(acc, red);
-  if (threadIdx.x == 0) out[b] = sqrt(acc[0]);
+  RT acc[1] = {RT(0)};
+  for (int e = threadIdx.x; e < N; e += NT) acc[0] += cabs2(A[(size_t)b * ss + e]);
+  block_sum<1, RT>(acc, red);
+  if (threadIdx.x == 0) out[b] = sqrt((double)acc[0]);
 }
 
 }  // namespace kry

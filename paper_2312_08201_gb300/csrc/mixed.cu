@@ -191,8 +191,10 @@ int mixed_apply(lyap_seed* sd, bool adjoint, const double* vinv, const int* list
   const float2* P1 = adjoint ? ms.Vb32.p : ms.Ub32.p;
   const float2* P2 = adjoint ? ms.Ub32.p : ms.Vb32.p;
   dim3 g((n + 255) / 256, nsys);
+  const int pp = prof_begin(PK_PANEL, st);
   k_panel<T2><<<g, 256, 0, st>>>(n, k, list, count, nsys, In, in_ss, P2, ms.kpad, ms.Bhi.p, ms.Blo.p);
   lyap_count_launch();
+  prof_end(pp, st, 0.0, (double)n * k * sizeof(T2) + 8.0 * n * kk, count ? 0 : nsys, count);
   LY_CUDA(cudaGetLastError());
   // algorithmic work per system: 2 (real) x (2n)^2 x k^2 MACs per product, three products
   const int ph = prof_begin(PK_TCGEMM, st);
@@ -392,9 +394,11 @@ template <>
 int SysOp<float2>::precond(const int* list, const int* count, int B, const float2* In, size_t in_ss, float2* Out,
                            size_t out_ss, cudaStream_t st) const {
   dim3 grid((sd->n + kry::NT - 1) / kry::NT, B);
+  const int ph = prof_begin(PK_PRECOND, st);
   kry::k_precond_bj<float2><<<grid, kry::NT, 0, st>>>(sd->n, sd->k, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv, In,
                                                      in_ss, Out, out_ss);
   lyap_count_launch();
+  prof_end(ph, st, 0.0, (double)sd->n * sd->k * (2 * sizeof(float2) + sd->k * sizeof(double2)), 0, count);
   LY_CUDA(cudaGetLastError());
   return LYAP_OK;
 }

@@ -9,7 +9,8 @@
 
 namespace {
 
-const char* kNames[PK_COUNT] = {"capmv64", "tc_gemm", "ortho", "precond", "gram", "tsmm", "ritz", "epi32"};
+const char* kNames[PK_COUNT] = {"capmv64", "tc_gemm", "ortho", "precond", "gram", "tsmm",
+                                "ritz",    "epi32",   "lsq",   "cycle",   "panel", "recstart"};
 
 struct Rec {
   int kernel;

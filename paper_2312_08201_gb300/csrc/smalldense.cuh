@@ -14,6 +14,31 @@ namespace sd {
 __device__ __forceinline__ int lane() { return threadIdx.x & 31; }
 __device__ __forceinline__ void wsync() { __syncwarp(); }
 __device__ __forceinline__ double cabs_(double2 z) { return sqrt(cabs2(z)); }
+__device__ __forceinline__ float cabs_(float2 z) { return sqrtf(cabs2(z)); }
+template <typename T2>
+__device__ __forceinline__ T2 zero2() {
+  T2 z;
+  z.x = 0;
+  z.y = 0;
+  return z;
+}
+template <typename T2>
+__device__ __forceinline__ T2 re2(typename RealOf<T2>::T x) {
+  T2 z;
+  z.x = x;
+  z.y = 0;
+  return z;
+}
+template <typename R>
+__device__ __forceinline__ R eps_of();
+template <>
+__device__ __forceinline__ double eps_of<double>() {
+  return 2.220446049250313e-16;
+}
+template <>
+__device__ __forceinline__ float eps_of<float>() {
+  return 1.1920929e-7f;
+}
 
 // C (m x n) = A^H B, A: K x m (lda), B: K x n (ldb)
 __device__ inline void gemm_hn(int m, int n, int K, const double2* A, int lda, const double2* B, int ldb,
@@ -103,33 +128,35 @@ __device__ inline void trsm_lower_h_left(int m, int n, const double2* L, int ldl
 
 // Householder reduction to upper Hessenberg form, A := Q^H A Q, Q accumulated
 // (Q initialised to I here). v: scratch of length m.
-__device__ inline void hessenberg(int m, double2* A, int lda, double2* Q, int ldq, double2* v) {
+template <typename T2>
+__device__ inline void hessenberg(int m, T2* A, int lda, T2* Q, int ldq, T2* v) {
+  using R = typename RealOf<T2>::T;
   for (int e = lane(); e < m * m; e += 32) {
     int i = e % m, j = e / m;
-    Q[i + (size_t)j * ldq] = mk(i == j ? 1.0 : 0.0, 0.0);
+    Q[i + (size_t)j * ldq] = re2<T2>(i == j ? R(1) : R(0));
   }
   wsync();
   for (int c = 0; c + 2 < m; ++c) {
     const int len = m - c - 1;
-    double xn2 = 0.0;
+    R xn2 = 0;
     for (int i = 0; i < len; ++i) xn2 += cabs2(A[c + 1 + i + (size_t)c * lda]);
-    double2 x0 = A[c + 1 + (size_t)c * lda];
-    double alpha = sqrt(xn2);
-    double ax0 = cabs_(x0);
-    if (alpha == 0.0 || xn2 - ax0 * ax0 <= 1e-300) {
+    T2 x0 = A[c + 1 + (size_t)c * lda];
+    R alpha = sqrt(xn2);
+    R ax0 = cabs_(x0);
+    if (alpha == R(0) || xn2 - ax0 * ax0 <= xn2 * eps_of<R>() * eps_of<R>()) {
       wsync();
       continue;  // already in Hessenberg form in this column
     }
-    double2 ph = ax0 > 0.0 ? cscale(x0, 1.0 / ax0) : mk(1.0, 0.0);
-    double2 v0 = cadd(x0, cscale(ph, alpha));
-    double vn2 = xn2 - ax0 * ax0 + cabs2(v0);
-    double beta = 2.0 / vn2;
+    T2 ph = ax0 > R(0) ? cscale(x0, R(1) / ax0) : re2<T2>(R(1));
+    T2 v0 = cadd(x0, cscale(ph, alpha));
+    R vn2 = xn2 - ax0 * ax0 + cabs2(v0);
+    R beta = R(2) / vn2;
     wsync();
     for (int i = lane(); i < len; i += 32) v[i] = i == 0 ? v0 : A[c + 1 + i + (size_t)c * lda];
     wsync();
     // left: A[c+1:, j] -= beta v (v^H A[c+1:, j]) for j >= c
     for (int j = c + lane(); j < m; j += 32) {
-      double2 s = mk(0.0, 0.0);
+      T2 s = zero2<T2>();
       for (int i = 0; i < len; ++i) s = cadd(s, cjmul(v[i], A[c + 1 + i + (size_t)j * lda]));
       s = cscale(s, beta);
       for (int i = 0; i < len; ++i) A[c + 1 + i + (size_t)j * lda] = csub(A[c + 1 + i + (size_t)j * lda], cmul(v[i], s));
@@ -137,7 +164,7 @@ __device__ inline void hessenberg(int m, double2* A, int lda, double2* Q, int ld
     wsync();
     // right: A[i, c+1:] -= beta (A[i, c+1:] v) v^H for all i; same for Q
     for (int i = lane(); i < m; i += 32) {
-      double2 s = mk(0.0, 0.0), sq = mk(0.0, 0.0);
+      T2 s = zero2<T2>(), sq = zero2<T2>();
       for (int l = 0; l < len; ++l) {
         s = cfma(A[i + (size_t)(c + 1 + l) * lda], v[l], s);
         sq = cfma(Q[i + (size_t)(c + 1 + l) * ldq], v[l], sq);
@@ -150,25 +177,26 @@ __device__ inline void hessenberg(int m, double2* A, int lda, double2* Q, int ld
       }
     }
     wsync();
-    for (int i = c + 2 + lane(); i < m; i += 32) A[i + (size_t)c * lda] = mk(0.0, 0.0);
+    for (int i = c + 2 + lane(); i < m; i += 32) A[i + (size_t)c * lda] = zero2<T2>();
     wsync();
   }
 }
 
 // Givens rotation G = [[c, s], [-conj(s), c]] with G [x; y] = [rho; 0].
-__device__ inline void givens(double2 x, double2 y, double& c, double2& s) {
-  double ax = cabs_(x), ay = cabs_(y);
-  if (ay == 0.0) {
-    c = 1.0;
-    s = mk(0.0, 0.0);
-  } else if (ax == 0.0) {
-    c = 0.0;
-    s = mk(1.0, 0.0);
+template <typename T2, typename R>
+__device__ inline void givens(T2 x, T2 y, R& c, T2& s) {
+  R ax = cabs_(x), ay = cabs_(y);
+  if (ay == R(0)) {
+    c = R(1);
+    s = zero2<T2>();
+  } else if (ax == R(0)) {
+    c = R(0);
+    s = re2<T2>(R(1));
   } else {
-    double r = hypot(ax, ay);
-    double2 al = cscale(x, 1.0 / ax);
+    R r = sqrt(ax * ax + ay * ay);
+    T2 al = cscale(x, R(1) / ax);
     c = ax / r;
-    s = cscale(cjmul(y, al), 1.0 / r);  // al * conj(y) / r
+    s = cscale(cjmul(y, al), R(1) / r);  // al * conj(y) / r
   }
 }
 
@@ -176,20 +204,22 @@ __device__ inline void givens(double2 x, double2 y, double& c, double2& s) {
 // (Wilkinson shift, exceptional shift every 10 iterations, deflation on
 // negligible subdiagonals), accumulating Q. On return H is upper triangular
 // (Schur form) and A_original = Q H Q^H. Returns 0 on success.
-__device__ inline int hqr(int m, double2* H, int ldh, double2* Q, int ldq, int maxit) {
-  const double eps = 2.220446049250313e-16;
+template <typename T2>
+__device__ inline int hqr(int m, T2* H, int ldh, T2* Q, int ldq, int maxit) {
+  using R = typename RealOf<T2>::T;
+  const R eps = eps_of<R>();
   int hi = m - 1, its = 0, total = 0;
   while (hi > 0) {
     int l = hi;
     while (l > 0) {
-      double sc = cabs_(H[l - 1 + (size_t)(l - 1) * ldh]) + cabs_(H[l + (size_t)l * ldh]);
-      if (sc == 0.0) sc = 1e-300;
+      R sc = cabs_(H[l - 1 + (size_t)(l - 1) * ldh]) + cabs_(H[l + (size_t)l * ldh]);
+      if (sc == R(0)) sc = R(1e-30);
       if (cabs_(H[l + (size_t)(l - 1) * ldh]) <= eps * sc) break;
       --l;
     }
     if (l == hi) {
       wsync();
-      if (lane() == 0) H[hi + (size_t)(hi - 1) * ldh] = mk(0.0, 0.0);
+      if (lane() == 0) H[hi + (size_t)(hi - 1) * ldh] = zero2<T2>();
       wsync();
       --hi;
       its = 0;
@@ -197,57 +227,59 @@ __device__ inline int hqr(int m, double2* H, int ldh, double2* Q, int ldq, int m
     }
     if (++total > maxit) return 1;
     ++its;
-    double2 mu;
-    double2 d = H[hi + (size_t)hi * ldh];
+    T2 mu;
+    T2 d = H[hi + (size_t)hi * ldh];
     if (its % 10 == 0) {
-      mu = cadd(d, mk(cabs_(H[hi + (size_t)(hi - 1) * ldh]), 0.0));
+      mu = cadd(d, re2<T2>(cabs_(H[hi + (size_t)(hi - 1) * ldh])));
     } else {
-      double2 a = H[hi - 1 + (size_t)(hi - 1) * ldh], b = H[hi - 1 + (size_t)hi * ldh];
-      double2 c = H[hi + (size_t)(hi - 1) * ldh];
-      double2 half = cscale(csub(a, d), 0.5);
-      double2 disc2 = cadd(cmul(half, half), cmul(b, c));
+      T2 a = H[hi - 1 + (size_t)(hi - 1) * ldh], b = H[hi - 1 + (size_t)hi * ldh];
+      T2 c = H[hi + (size_t)(hi - 1) * ldh];
+      T2 half = cscale(csub(a, d), R(0.5));
+      T2 disc2 = cadd(cmul(half, half), cmul(b, c));
       // principal complex square root
-      double r = cabs_(disc2);
-      double sr = sqrt(0.5 * (r + disc2.x));
-      double si = sqrt(fmax(0.0, 0.5 * (r - disc2.x)));
+      R r = cabs_(disc2);
+      R sr = sqrt(R(0.5) * (r + disc2.x));
+      R si = sqrt(fmax(R(0), R(0.5) * (r - disc2.x)));
       if (disc2.y < 0) si = -si;
-      double2 disc = mk(sr, si);
-      double2 tr2 = cscale(cadd(a, d), 0.5);
-      double2 m1 = cadd(tr2, disc), m2 = csub(tr2, disc);
+      T2 disc;
+      disc.x = sr;
+      disc.y = si;
+      T2 tr2 = cscale(cadd(a, d), R(0.5));
+      T2 m1 = cadd(tr2, disc), m2 = csub(tr2, disc);
       mu = cabs2(csub(m1, d)) <= cabs2(csub(m2, d)) ? m1 : m2;
     }
-    double2 x = csub(H[l + (size_t)l * ldh], mu);
-    double2 y = H[l + 1 + (size_t)l * ldh];
+    T2 x = csub(H[l + (size_t)l * ldh], mu);
+    T2 y = H[l + 1 + (size_t)l * ldh];
     for (int kk = l; kk < hi; ++kk) {
       if (kk > l) {
         x = H[kk + (size_t)(kk - 1) * ldh];
         y = H[kk + 1 + (size_t)(kk - 1) * ldh];
       }
-      double c;
-      double2 s;
+      R c;
+      T2 s;
       givens(x, y, c, s);
       wsync();
       int j0 = kk > l ? kk - 1 : kk;
       for (int j = j0 + lane(); j < m; j += 32) {
-        double2 top = H[kk + (size_t)j * ldh], bot = H[kk + 1 + (size_t)j * ldh];
+        T2 top = H[kk + (size_t)j * ldh], bot = H[kk + 1 + (size_t)j * ldh];
         H[kk + (size_t)j * ldh] = cadd(cscale(top, c), cmul(s, bot));
         H[kk + 1 + (size_t)j * ldh] = csub(cscale(bot, c), cjmul(s, top));
       }
       wsync();
       int imax = kk + 2 < hi ? kk + 2 : hi;
       for (int i = lane(); i <= imax; i += 32) {
-        double2 lft = H[i + (size_t)kk * ldh], rgt = H[i + (size_t)(kk + 1) * ldh];
+        T2 lft = H[i + (size_t)kk * ldh], rgt = H[i + (size_t)(kk + 1) * ldh];
         H[i + (size_t)kk * ldh] = cadd(cscale(lft, c), cmul(cconj(s), rgt));
         H[i + (size_t)(kk + 1) * ldh] = csub(cscale(rgt, c), cmul(s, lft));
       }
       for (int i = lane(); i < m; i += 32) {
-        double2 lft = Q[i + (size_t)kk * ldq], rgt = Q[i + (size_t)(kk + 1) * ldq];
+        T2 lft = Q[i + (size_t)kk * ldq], rgt = Q[i + (size_t)(kk + 1) * ldq];
         Q[i + (size_t)kk * ldq] = cadd(cscale(lft, c), cmul(cconj(s), rgt));
         Q[i + (size_t)(kk + 1) * ldq] = csub(cscale(rgt, c), cmul(s, lft));
       }
       wsync();
       if (kk > l) {
-        if (lane() == 0) H[kk + 1 + (size_t)(kk - 1) * ldh] = mk(0.0, 0.0);
+        if (lane() == 0) H[kk + 1 + (size_t)(kk - 1) * ldh] = zero2<T2>();
         wsync();
       }
     }
@@ -258,41 +290,87 @@ __device__ inline int hqr(int m, double2* H, int ldh, double2* Q, int ldq, int m
 // Eigenvectors of the triangular Schur form T for the selected indices,
 // back-transformed by Q: X[:, c] = Q y_c with (T - T_qq I) y_c = 0,
 // y_c[q] = 1, normalised to unit 2-norm. One lane per selected vector.
-__device__ inline void schur_vectors(int m, const double2* T, int ldt, const double2* Q, int ldq, const int* sel,
-                                     int ns, double2* Y, int ldy, double2* X, int ldx) {
-  const double small = 1e-300;
+template <typename T2>
+__device__ inline void schur_vectors(int m, const T2* T, int ldt, const T2* Q, int ldq, const int* sel, int ns, T2* Y,
+                                     int ldy, T2* X, int ldx) {
+  using R = typename RealOf<T2>::T;
   for (int c = lane(); c < ns; c += 32) {
     int q = sel[c];
-    double2 mu = T[q + (size_t)q * ldt];
-    double2* y = Y + (size_t)c * ldy;
-    for (int i = 0; i < m; ++i) y[i] = mk(0.0, 0.0);
-    y[q] = mk(1.0, 0.0);
-    double tnorm = 0.0;
+    T2 mu = T[q + (size_t)q * ldt];
+    T2* y = Y + (size_t)c * ldy;
+    for (int i = 0; i < m; ++i) y[i] = zero2<T2>();
+    y[q] = re2<T2>(R(1));
+    R tnorm = 0;
     for (int i = 0; i <= q; ++i) tnorm = fmax(tnorm, cabs_(T[i + (size_t)i * ldt]));
-    double floor_d = 1e-14 * (tnorm > 0 ? tnorm : 1.0);
+    R floor_d = R(64) * eps_of<R>() * (tnorm > R(0) ? tnorm : R(1));
     for (int i = q - 1; i >= 0; --i) {
-      double2 sum = mk(0.0, 0.0);
+      T2 sum = zero2<T2>();
       for (int j = i + 1; j <= q; ++j) sum = cfma(T[i + (size_t)j * ldt], y[j], sum);
-      double2 den = csub(T[i + (size_t)i * ldt], mu);
-      if (cabs_(den) < floor_d) den = mk(floor_d, 0.0);
-      y[i] = cscale(cdiv(sum, den), -1.0);
-      if (!(cabs2(y[i]) < 1e200)) y[i] = mk(small, 0.0);
+      T2 den = csub(T[i + (size_t)i * ldt], mu);
+      if (cabs_(den) < floor_d) den = re2<T2>(floor_d);
+      y[i] = cscale(cdiv(sum, den), R(-1));
+      if (!(cabs2(y[i]) < R(1e30))) y[i] = zero2<T2>();
     }
   }
   wsync();
   for (int e = lane(); e < m * ns; e += 32) {
     int r = e % m, c = e / m;
     int q = sel[c];
-    double2 acc = mk(0.0, 0.0);
+    T2 acc = zero2<T2>();
     for (int i = 0; i <= q; ++i) acc = cfma(Q[r + (size_t)i * ldq], Y[i + (size_t)c * ldy], acc);
     X[r + (size_t)c * ldx] = acc;
   }
   wsync();
   for (int c = lane(); c < ns; c += 32) {
-    double nrm = 0.0;
+    R nrm = 0;
     for (int r = 0; r < m; ++r) nrm += cabs2(X[r + (size_t)c * ldx]);
-    nrm = nrm > 0 ? 1.0 / sqrt(nrm) : 1.0;
+    nrm = nrm > R(0) ? R(1) / sqrt(nrm) : R(1);
     for (int r = 0; r < m; ++r) X[r + (size_t)c * ldx] = cscale(X[r + (size_t)c * ldx], nrm);
+  }
+  wsync();
+}
+
+// Householder QR of G (r x c, r >= c) in place; the reflectors are also
+// applied to F (r x nf): on return the upper triangle of G holds R and the
+// first c rows of F hold Q^H F. v: scratch of length r.
+template <typename T2>
+__device__ inline void householder_qr_apply(int r, int c, T2* G, int ldg, T2* F, int ldf, int nf, T2* v) {
+  using R = typename RealOf<T2>::T;
+  for (int k = 0; k < c; ++k) {
+    const int len = r - k;
+    R xn2 = 0;
+    for (int i = 0; i < len; ++i) xn2 += cabs2(G[k + i + (size_t)k * ldg]);
+    const T2 x0 = G[k + (size_t)k * ldg];
+    const R alpha = sqrt(xn2);
+    const R ax0 = cabs_(x0);
+    wsync();
+    if (!(alpha > R(0))) continue;
+    const T2 ph = ax0 > R(0) ? cscale(x0, R(1) / ax0) : re2<T2>(R(1));
+    const T2 v0 = cadd(x0, cscale(ph, alpha));
+    const R vn2 = xn2 - ax0 * ax0 + cabs2(v0);
+    const R beta = R(2) / vn2;
+    for (int i = lane(); i < len; i += 32) v[i] = i == 0 ? v0 : G[k + i + (size_t)k * ldg];
+    wsync();
+    for (int j = k + lane(); j < c + nf; j += 32) {
+      T2* col = j < c ? G + (size_t)j * ldg : F + (size_t)(j - c) * ldf;
+      T2 s = zero2<T2>();
+      for (int i = 0; i < len; ++i) s = cadd(s, cjmul(v[i], col[k + i]));
+      s = cscale(s, beta);
+      for (int i = 0; i < len; ++i) col[k + i] = csub(col[k + i], cmul(v[i], s));
+    }
+    wsync();
+  }
+}
+
+// X := R^{-1} X (R upper c x c, X c x n); lanes over columns
+template <typename T2>
+__device__ inline void trsm_upper_left(int c, int n, const T2* Rm, int ldr, T2* X, int ldx) {
+  for (int j = lane(); j < n; j += 32) {
+    for (int i = c - 1; i >= 0; --i) {
+      T2 x = X[i + (size_t)j * ldx];
+      for (int l = i + 1; l < c; ++l) x = csub(x, cmul(Rm[i + (size_t)l * ldr], X[l + (size_t)j * ldx]));
+      X[i + (size_t)j * ldx] = cdiv(x, Rm[i + (size_t)i * ldr]);
+    }
   }
   wsync();
 }

@@ -70,6 +70,16 @@ __global__ void k_zero_failed(size_t N, int s, const int* __restrict__ list, con
   }
 }
 
+// The recycle space is updated for systems that run another cycle, and for
+// the chunk's last system, whose space seeds the next chunk.
+__global__ void k_want_ritz(const int* __restrict__ list, const int* __restrict__ count, const int* __restrict__ flag,
+                            const int* __restrict__ jstop, int last, int* __restrict__ want) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= *count) return;
+  int b = list[s];
+  want[b] = (jstop[b] > 0 && (flag[b] > 0 || b == last)) ? 1 : 0;
+}
+
 __global__ void k_mark_rec(const int* __restrict__ list, const int* __restrict__ count, const int* __restrict__ ok,
                            int* __restrict__ hasrec) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -179,6 +189,7 @@ int KrylovWS<T2>::ensure(int B_, int N_, int m_, int s_) {
   LY_TRY(counts.alloc(8));
   LY_TRY(ok.alloc(Bs));
   LY_TRY(hasrec.alloc(Bs));
+  LY_TRY(rflag.alloc(Bs));
   return LYAP_OK;
 }
 
@@ -188,7 +199,7 @@ size_t KrylovWS<T2>::bytes() const {
          Bk.bytes() + g.bytes() + sn.bytes() + coefY.bytes() + coefR.bytes() + F.bytes() + UU.bytes() +
          work.bytes() + Pu.bytes() + Qc.bytes() + Gs.bytes() + Rinv.bytes() + Racc.bytes() + Rtmp.bytes() +
          cs.bytes() + beta.bytes() + tolabs.bytes() + tmpd.bytes() + jstop.bytes() + flag.bytes() + iters.bytes() +
-         lists.bytes() + counts.bytes() + ok.bytes() + hasrec.bytes();
+         lists.bytes() + counts.bytes() + ok.bytes() + hasrec.bytes() + rflag.bytes();
 }
 
 // ------------------------------------------------------------------ solver
@@ -263,7 +274,11 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     LY_CUDA(cudaStreamSynchronize(st));
     bool all_ok = std::all_of(okh.begin(), okh.end(), [](int v) { return v == 1; });
     if (all_ok) {
-      kry::k_project<T2><<<B, kry::NT, 0, st>>>(N, s, Lchunk, cchunk, ws.C.p, ws.U.p, ss, ws.X.p, ws.R.p); lyap_count_launch();
+      {
+        const int ph_ = prof_begin(PK_RECSTART, st);
+        kry::k_project<T2><<<B, kry::NT, 0, st>>>(N, s, Lchunk, cchunk, ws.C.p, ws.U.p, ss, ws.X.p, ws.R.p); lyap_count_launch();
+        prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+      }
       LY_CUDA(cudaGetLastError());
       s_cur = s;
     } else {
@@ -279,8 +294,12 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
   while (chunk_count > 0 && guard++ < 100000) {
     LY_CUDA(cudaMemcpyAsync(Lstart, Lchunk, sizeof(int) * B, cudaMemcpyDeviceToDevice, st));
     LY_CUDA(cudaMemcpyAsync(cstart, cchunk, sizeof(int), cudaMemcpyDeviceToDevice, st));
-    kry::k_cycle_start<T2><<<B, kry::NT, 0, st>>>(N, m, Lstart, cstart, ws.R.p, ws.V.p, ws.g.p, ws.tolabs.p,
+    {
+      const int ph_ = prof_begin(PK_CYCLE, st);
+      kry::k_cycle_start<T2><<<B, kry::NT, 0, st>>>(N, m, Lstart, cstart, ws.R.p, ws.V.p, ws.g.p, ws.tolabs.p,
                                                   ws.flag.p, ws.jstop.p, ws.beta.p); lyap_count_launch();
+      prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+    }
     kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.flag.p, La, ca); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     int* Lcur = La;
@@ -304,44 +323,80 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
         lyap_count_launch();
         prof_end(ph, st, 2.0 * 2.0 * 8.0 * nb * N, (4.0 * nb + 6.0) * N * sizeof(T2), 0, ccur);
       }
-      kry::k_lsq<<<g1, 256, 0, st>>>(j, m, Lcur, ccur, ws.H.p, ws.H0.p, ws.cs.p, ws.sn.p, ws.g.p, ws.tolabs.p,
+      {
+        const int ph_ = prof_begin(PK_LSQ, st);
+        kry::k_lsq<<<g1, 256, 0, st>>>(j, m, Lcur, ccur, ws.H.p, ws.H0.p, ws.cs.p, ws.sn.p, ws.g.p, ws.tolabs.p,
                                      ws.jstop.p, ws.flag.p, ws.iters.p, maxit); lyap_count_launch();
+        prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+      }
       kry::k_compact<<<1, 1024, 0, st>>>(Lcur, ccur, ws.flag.p, Lnext, cnext); lyap_count_launch();
       LY_CUDA(cudaGetLastError());
       std::swap(Lcur, Lnext);
       std::swap(ccur, cnext);
     }
     // ---- cycle end -----------------------------------------------------
-    kry::k_cycle_solve<<<g1, 256, 0, st>>>(m, smax, s_cur, Lstart, cstart, ws.H.p, ws.H0.p, ws.Bk.p, ws.g.p,
+    {
+      const int ph_ = prof_begin(PK_CYCLE, st);
+      kry::k_cycle_solve<<<g1, 256, 0, st>>>(m, smax, s_cur, Lstart, cstart, ws.H.p, ws.H0.p, ws.Bk.p, ws.g.p,
                                            ws.beta.p, ws.jstop.p, ws.coefY.p, ws.coefR.p); lyap_count_launch();
-    kry::k_update_xr<T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, m, smax, s_cur, Lstart, cstart, ws.jstop.p,
+      prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+    }
+    {
+      const int ph_ = prof_begin(PK_CYCLE, st);
+      kry::k_update_xr<T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, m, smax, s_cur, Lstart, cstart, ws.jstop.p,
                                                               ws.coefY.p, ws.coefR.p, ws.U.p, ws.Z.p, ws.V.p,
                                                               ws.X.p, ws.R.p); lyap_count_launch();
+      prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+    }
     k_add_iters<<<g1, 256, 0, st>>>(Lstart, cstart, ws.jstop.p, ws.iters.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     // ---- recycle update (harmonic Ritz) ----------------------------------
     if (s > 0) {
       auto Vh = seg2(seg(ws.C.p, css, NS, s_cur), segd(ws.V.p, (size_t)(m + 1) * NS, NS, ws.jstop.p, 1));
       auto Wh = seg2(seg(ws.U.p, css, NS, s_cur), segd(ws.Z.p, (size_t)m * NS, NS, ws.jstop.p, 0));
-      kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lstart, cstart, Vh, Wh, ws.F.p, LD, (size_t)LD * LD); lyap_count_launch();
+      int* Lwant = L + 5 * B;
+      int* cwant = cnt + 5;
+      k_want_ritz<<<g1, 256, 0, st>>>(Lstart, cstart, ws.flag.p, ws.jstop.p, B - 1, ws.rflag.p);
+      lyap_count_launch();
+      kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.rflag.p, Lwant, cwant);
+      lyap_count_launch();
+      {
+        const int ph_ = prof_begin(PK_GRAM, st);
+        kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lwant, cwant, Vh, Wh, ws.F.p, LD, (size_t)LD * LD); lyap_count_launch();
+        prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+      }
       if (s_cur > 0) {
         auto Us = seg2(seg(ws.U.p, css, NS, s_cur), seg(ws.U.p, css, NS, 0));
-        kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lstart, cstart, Us, Us, ws.UU.p, smax, (size_t)smax * smax); lyap_count_launch();
+        kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lwant, cwant, Us, Us, ws.UU.p, smax, (size_t)smax * smax); lyap_count_launch();
       }
-      kry::k_ritz<<<(B * 32 + 127) / 128, 128, 0, st>>>(m, smax, s_cur, s, Lstart, cstart, ws.jstop.p, ws.H0.p,
+      {
+        const int ph_ = prof_begin(PK_RITZ, st);
+        const size_t rsm = kry::ritz_smem_bytes(m, smax);
+      if (rsm > 48 * 1024) LY_CUDA(cudaFuncSetAttribute(kry::k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+      kry::k_ritz<<<B, 32, rsm, st>>>(m, smax, s_cur, s, Lwant, cwant, ws.jstop.p, ws.H0.p,
                                                         ws.Bk.p, ws.F.p, ws.UU.p, ws.work.p, ws.wstride, ws.Pu.p,
                                                         ws.Qc.p, ws.ok.p); lyap_count_launch();
+        prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+      }
       // systems whose update succeeded: new U = [U Z] Pu, C = [C V] Qc (in place)
       {
         // list of systems with ok = 1 (flag-like compaction on ok)
-        kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.ok.p, Lritz, critz); lyap_count_launch();
-        kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lritz, critz, Wh, ws.Pu.p, LD,
+        kry::k_compact<<<1, 1024, 0, st>>>(Lwant, cwant, ws.ok.p, Lritz, critz); lyap_count_launch();
+        {
+          const int ph_ = prof_begin(PK_TSMM, st);
+          kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lritz, critz, Wh, ws.Pu.p, LD,
                                                                  (size_t)LD * 16, s, ws.U.p, css, NS, 0); lyap_count_launch();
-        kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lritz, critz, Vh, ws.Qc.p, LD,
+          prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+        }
+        {
+          const int ph_ = prof_begin(PK_TSMM, st);
+          kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lritz, critz, Vh, ws.Qc.p, LD,
                                                                  (size_t)LD * 16, s, ws.C.p, css, NS, 0); lyap_count_launch();
-        k_mark_rec<<<g1, 256, 0, st>>>(Lstart, cstart, ws.ok.p, ws.hasrec.p); lyap_count_launch();
+          prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+        }
+        k_mark_rec<<<g1, 256, 0, st>>>(Lwant, cwant, ws.ok.p, ws.hasrec.p); lyap_count_launch();
         if (s_cur == 0) {
-          k_zero_failed<T2><<<dim3(gx(NS * s), B), kry::NT, 0, st>>>(NS, s, Lstart, cstart, ws.ok.p, ws.C.p,
+          k_zero_failed<T2><<<dim3(gx(NS * s), B), kry::NT, 0, st>>>(NS, s, Lwant, cwant, ws.ok.p, ws.C.p,
                                                                      ws.U.p, css);
           lyap_count_launch();
         }

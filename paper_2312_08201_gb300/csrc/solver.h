@@ -34,7 +34,7 @@ struct KrylovWS {
   DevBuf<T2> V, Z, C, U, X, R;
   DevBuf<double2> H, H0, Bk, g, sn, coefY, coefR, F, UU, work, Pu, Qc, Gs, Rinv, Racc, Rtmp;
   DevBuf<double> cs, beta, tolabs, tmpd;
-  DevBuf<int> jstop, flag, iters, lists, counts, ok, hasrec;
+  DevBuf<int> jstop, flag, iters, lists, counts, ok, hasrec, rflag;
   int ensure(int B, int N, int m, int s);
   size_t bytes() const;
 };
