@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="systems solved in lockstep (0: library default)")
     ap.add_argument("--cpu-sample", type=int, default=4, help="oracle evaluations in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["precision", "serving"], default="precision")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests per arrival rate")
+    ap.add_argument("--serving-sizes", default="200,400,800,1600", help="serving: chain lengths (masses)")
     return ap.parse_args()
 
 
@@ -163,6 +166,80 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- serving
+def run_serving(args, local):
+    """Serving workload: 8 seeds (two chains each of the given lengths,
+    k in {2,3,4}, Haar-dense), requests of 64 log-uniform parameter vectors
+    on [0.1, 10]^k. Saturation throughput from a burst, then Poisson arrivals
+    at 0.5/0.8/0.95 of it; evals/s and p50/p99 submit-to-result latency."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2312_08201_gb300 as ly
+    from workloads import workload_serving_requests, workload_serving_seeds
+
+    torch.cuda.set_device(local)
+    ly.build()
+    sizes = tuple(int(x) for x in args.serving_sizes.split(","))
+    probs = workload_serving_seeds(dense=True, sizes=sizes)
+    ctx = ly.Context(local)
+    t0 = time.perf_counter()
+    seeds = [ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E) for p in probs]
+    t_factor = time.perf_counter() - t0
+    prec = ly.FP64 if args.precision == "fp64" else ly.BF16_IR
+
+    def drive(reqs, paced):
+        srv = ly.Server(ctx, precision=prec)
+        ids = [srv.register(sd) for sd in seeds]
+        tickets = [None] * len(reqs)
+        start = time.perf_counter()
+
+        def submitter():
+            for i, (ta, si, v) in enumerate(reqs):
+                if paced:
+                    delay = start + ta - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                tickets[i] = srv.submit(ids[si], v)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        srv.run()
+        elapsed = time.perf_counter() - start
+        lat = []
+        evals = 0
+        for t, (ta, si, v) in zip(tickets, reqs):
+            r = srv.poll(t, len(v), v.shape[1])
+            lat.append(r["latency_s"])
+            evals += len(v)
+        srv.close()
+        return evals / elapsed, lat
+
+    # warm-up (recycle spaces, workspaces) and saturation
+    warm = workload_serving_requests(probs, rate_hz=1e9, count=16, seed=99)
+    drive(warm, False)
+    burst = workload_serving_requests(probs, rate_hz=1e9, count=min(128, args.requests), seed=1)
+    sat, _ = drive(burst, False)
+    rates = {}
+    for frac in (0.5, 0.8, 0.95):
+        req_rate = frac * sat / 64.0
+        reqs = workload_serving_requests(probs, rate_hz=req_rate, count=args.requests, seed=int(frac * 100))
+        thr, lat = drive(reqs, True)
+        rates[str(frac)] = dict(evals_per_s=thr, p50_ms=1e3 * float(np.percentile(lat, 50)),
+                                p99_ms=1e3 * float(np.percentile(lat, 99)), requests=len(reqs))
+    line = dict(metric=METRIC, value=rates["0.95"]["evals_per_s"], unit="evals/s", n_gpus=1, steps=args.requests,
+                warmup=16, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="bf16x3-gemm/f32-krylov/f64-refine" if prec == ly.BF16_IR else "f64", data="synthetic",
+                config=dict(workload=f"serving: 8 chain seeds {sizes} masses x2, k in {{2,3,4}}, 64 v per request, "
+                                     "Poisson arrivals", n=[p.n for p in probs], k=[p.k for p in probs]),
+                saturation_evals_per_s=sat, rates=rates, seed_factor_s=t_factor,
+                latency_ms=dict(p50=rates["0.95"]["p50_ms"], p99=rates["0.95"]["p99_ms"], request="64-vector sweep"))
+    print(json.dumps(line), flush=True)
+
+
 # -------------------------------------------------------------------- ours
 def main():
     args = parse()
@@ -171,6 +248,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.workload == "serving":
+        return run_serving(args, local) if rank == 0 else None
 
     import numpy as np
     import torch

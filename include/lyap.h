@@ -195,28 +195,40 @@ int lyap_grad(lyap_seed* seed, int nv, const double* v, int mem_kind, const lyap
               double* trace_out, double* grad_out, lyap_result_info* info);
 
 /* ----------------------------------------------------------------- serving
- * A continuous-batching server: requests (one seed, nv parameter vectors)
- * are admitted while the seeds' resident bytes plus the admitted requests'
- * workspace stay within opts->hbm_budget, join the running batch of their
- * seed at the next Krylov-cycle boundary, and retire as soon as all their
- * systems have converged. Seeds run on separate streams so their work
- * overlaps. All calls are host calls; pointers are host memory. */
+ * A continuous-batching server (spec addition; the paper solves one
+ * sweep at a time). Requests (one seed, nv parameter vectors) enter a FIFO
+ * and are admitted while the registered seeds' resident bytes plus the
+ * workspace estimate of all admitted, unfinished requests stay within
+ * opts->hbm_budget (0: 80% of the free device memory at creation). Every
+ * registered seed has its own CUDA stream and worker thread; whenever a
+ * worker finishes a batch it takes every request admitted for its seed in
+ * the meantime as its next lockstep batch, so requests arriving while
+ * others run join at the next batch boundary of their seed, and batches of
+ * different seeds overlap on the device. Factors and recycled Krylov spaces
+ * stay resident in the seeds. A registered seed must not be used directly
+ * while the server runs. All calls are host calls; pointers are host
+ * memory; the server is safe to call from several host threads. */
 int lyap_serve_create(lyap_ctx* ctx, const lyap_opts* opts, lyap_server** out);
 /* Register a seed (the server does not take ownership). */
 int lyap_serve_register_seed(lyap_server* srv, lyap_seed* seed, int* seed_id);
-/* Enqueue nv parameter vectors (nv x k row-major, copied). Returns a ticket. */
+/* Enqueue nv parameter vectors (nv x k row-major, copied); returns a ticket.
+ * Errors: LYAP_EINVAL (v_i = 0 or not finite), LYAP_ENOTFOUND (seed id),
+ * LYAP_ENOMEM (the request alone exceeds the budget). */
 int lyap_serve_submit(lyap_server* srv, int seed_id, int nv, const double* v, int want_grad,
                       uint64_t* ticket);
-/* Run scheduler ticks until no work is left or max_ticks ticks ran
- * (max_ticks <= 0: until idle). *busy (may be NULL) is set to 1 if work
- * remains. */
-int lyap_serve_run(lyap_server* srv, int max_ticks, int* busy);
+/* Wait until every submitted request is finished (max_ms <= 0) or at most
+ * max_ms milliseconds; the workers make progress on their own, this call
+ * only waits. *busy (may be NULL) is set to 1 if work remains. */
+int lyap_serve_run(lyap_server* srv, int max_ms, int* busy);
 /* LYAP_PENDING until the request is done; then copies nv traces (and
  * nv x k gradients if requested), nv infos (each may be NULL) and the
- * submit-to-completion latency in seconds, and forgets the ticket. */
+ * submit-to-completion latency in seconds, returns the request's status
+ * and forgets the ticket. A cancelled request returns LYAP_ECANCELLED. */
 int lyap_serve_poll(lyap_server* srv, uint64_t ticket, double* trace_out, double* grad_out,
                     lyap_result_info* info, double* latency_s);
+/* Cancel a request that has not been admitted yet (LYAP_EINVAL once it runs). */
 int lyap_serve_cancel(lyap_server* srv, uint64_t ticket);
+/* Finish running batches, stop the workers and free the server. */
 void lyap_serve_destroy(lyap_server* srv);
 
 /* ------------------------------------------------- allocation-free check

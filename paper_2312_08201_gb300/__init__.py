@@ -342,6 +342,64 @@ class Seed:
         return w, _infos(info, nv)
 
 
+class Server:
+    """Continuous-batching server over registered seeds (lyap_serve_*)."""
+
+    def __init__(self, ctx: Context, **opts):
+        self.lib = load()
+        o = default_opts(**opts)
+        h = _P()
+        _check(self.lib.lyap_serve_create(ctx.h, ctypes.byref(o), ctypes.byref(h)), "lyap_serve_create")
+        self.h = h
+        self.k = {}
+
+    def register(self, seed: "Seed") -> int:
+        sid = ctypes.c_int()
+        _check(self.lib.lyap_serve_register_seed(self.h, seed.h, ctypes.byref(sid)), "lyap_serve_register_seed")
+        self.k[sid.value] = seed.k
+        return sid.value
+
+    def submit(self, seed_id: int, v, want_grad: bool = False) -> int:
+        va = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1, self.k[seed_id]))
+        t = ctypes.c_uint64()
+        _check(self.lib.lyap_serve_submit(self.h, seed_id, va.shape[0], va.ctypes.data_as(ctypes.c_void_p),
+                                          1 if want_grad else 0, ctypes.byref(t)), "lyap_serve_submit")
+        return t.value
+
+    def run(self, max_ms: int = 0) -> bool:
+        busy = ctypes.c_int()
+        _check(self.lib.lyap_serve_run(self.h, max_ms, ctypes.byref(busy)), "lyap_serve_run")
+        return bool(busy.value)
+
+    def poll(self, ticket: int, nv: int, k: int, want_grad: bool = False):
+        """None while pending; else dict(f, g, info, latency_s) (raises on a failed request)."""
+        f = np.empty(nv)
+        g = np.empty((nv, k)) if want_grad else None
+        info = (ResultInfo * nv)()
+        lat = ctypes.c_double()
+        code = self.lib.lyap_serve_poll(self.h, ticket, f.ctypes.data_as(ctypes.c_void_p),
+                                        g.ctypes.data_as(ctypes.c_void_p) if g is not None else None, info,
+                                        ctypes.byref(lat))
+        if code == PENDING:
+            return None
+        _check(code, "lyap_serve_poll")
+        return dict(f=f, g=g, info=_infos(info, nv), latency_s=lat.value)
+
+    def cancel(self, ticket: int) -> int:
+        return self.lib.lyap_serve_cancel(self.h, ticket)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lyap_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def prof_enable(on: bool = True):
     """Start (clear) or stop the library's per-kernel event timing."""
     _check(load().lyap_prof_enable(1 if on else 0), "lyap_prof_enable")

@@ -256,16 +256,17 @@ int store_out(double* dst, const double* src_host, size_t count, int mem_kind, c
 // Final FP64 report for one chunk: trace, residual, error estimate, and
 // (with an adjoint solution Zadj) the gradient and the dual-weighted error
 // estimate |<z, r>| / |f|.
-int report_chunk(lyap_seed* sd, SeedWork& w, int Bc, const double2* Wp, const double2* Zadj, cudaStream_t st,
-                 double* f_host, double* grad_host, lyap_result_info* info) {
+int report_chunk(lyap_seed* sd, SeedWork& w, int Bc, const double2* Wp, const double2* Zadj, bool have_resid,
+                 cudaStream_t st, double* f_host, double* grad_host, lyap_result_info* info) {
   const int n = sd->n, k = sd->k;
   const size_t N = (size_t)n * k;
-  LY_TRY(w.Rres.alloc(std::max<size_t>(w.Rres.count, (size_t)Bc * N)));
-  LY_TRY(w.tmp.alloc(std::max<size_t>(w.tmp.count, (size_t)Bc * N)));
+  if (w.Rres.count < (size_t)Bc * N) LY_TRY(w.Rres.alloc((size_t)Bc * N));
+  if (w.tmp.count < (size_t)Bc * N) LY_TRY(w.tmp.alloc((size_t)Bc * N));
   for (DevBuf<double>* r : {&w.red0, &w.red1, &w.red2, &w.red3})
     if (r->count < (size_t)Bc * k) LY_TRY(r->alloc((size_t)Bc * k));
   kry::k_dot_h<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, Wp, N, sd->h.p, w.red0.p, nullptr); lyap_count_launch();
-  // r = Ph - T(v) W'
+  // r = Ph - T(v) W' (unless the caller already holds it in w.Rres)
+  if (!have_resid) {
   CapArgs64 a{};
   a.n = n;
   a.k = k;
@@ -283,6 +284,7 @@ int report_chunk(lyap_seed* sd, SeedWork& w, int Bc, const double2* Wp, const do
   a.mode = CAP_RESID;
   a.nsys = Bc;
   LY_TRY(capmv64_launch(a, st));
+  }
   kry::k_norms<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.Rres.p, N, w.red1.p); lyap_count_launch();
   if (Zadj) {
     k_dot_pair<<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.Rres.p, Zadj, w.red2.p); lyap_count_launch();
@@ -340,9 +342,10 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
     B = (int)std::min<size_t>(std::min<size_t>(4096, cap), (size_t)std::max(nv, 1));
   }
   B = std::min(B, std::max(nv, 1));
-  LY_TRY(w.vinv.alloc(std::max<size_t>(w.vinv.count, (size_t)B * k)));
-  LY_TRY(w.Wp.alloc(std::max<size_t>(w.Wp.count, (size_t)B * N)));
-  if (grad_host) LY_TRY(w.Zadj.alloc(std::max<size_t>(w.Zadj.count, (size_t)B * N)));
+  if (w.vinv.count < (size_t)B * k) LY_TRY(w.vinv.alloc((size_t)B * k));
+  if (w.Wp.count < (size_t)B * N) LY_TRY(w.Wp.alloc((size_t)B * N));
+  if (grad_host && w.Zadj.count < (size_t)B * N) LY_TRY(w.Zadj.alloc((size_t)B * N));
+  if (w.Rres.count < (size_t)B * N) LY_TRY(w.Rres.alloc((size_t)B * N));
   DevBuf<double> vdev;
   LY_TRY(vdev.alloc((size_t)B * k));
   std::vector<int> it, stt, ita, sta, rsteps;
@@ -352,6 +355,7 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
                             cudaMemcpyHostToDevice, st));
     k_vinv<<<grid_of((size_t)Bc * k), 256, 0, st>>>(Bc * k, vdev.p, w.vinv.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
+    bool have_resid = false;
     if (o.precision == LYAP_FP64) {
       SysOp<double2> op;
       op.sd = sd;
@@ -372,14 +376,15 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
         }
       }
     } else {
-      LY_TRY(lyap_mixed_chunk(sd, Bc, w.vinv.p, o, prm, st, w.ws32, w.ws32adj, w.Wp.p, grad_host ? w.Zadj.p : nullptr, it,
-                              stt, rsteps));
+      LY_TRY(lyap_mixed_chunk(sd, Bc, w.vinv.p, o, prm, st, w.ws32, w.ws32adj, w.Wp.p, grad_host ? w.Zadj.p : nullptr,
+                              w.Rres.p, it, stt, rsteps));
+      have_resid = true;
     }
     std::vector<double> gtmp;
     double* gh = nullptr;
     if (grad_host) gh = grad_host + (size_t)c0 * k;
     lyap_result_info* inf = info ? info + c0 : nullptr;
-    LY_TRY(report_chunk(sd, w, Bc, w.Wp.p, grad_host ? w.Zadj.p : nullptr, st, f_host + c0, gh, inf));
+    LY_TRY(report_chunk(sd, w, Bc, w.Wp.p, grad_host ? w.Zadj.p : nullptr, have_resid, st, f_host + c0, gh, inf));
     if (inf)
       for (int b = 0; b < Bc; ++b) {
         inf[b].iters = it[b];

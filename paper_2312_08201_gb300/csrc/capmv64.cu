@@ -12,6 +12,8 @@
 #include "lyap_internal.h"
 #include "prof.h"
 
+#include <mutex>
+
 namespace {
 
 constexpr int TI = 64;   // rows per tile
@@ -122,11 +124,12 @@ int capmv64_launch(const CapArgs64& a, cudaStream_t st) {
   const int kk = a.k * a.k;
   const int SB = TNC / kk;
   const size_t smem = (size_t)TI * SROW * sizeof(double2);  // >= operand tiles
-  static bool attr_set = false;
-  if (!attr_set) {
-    LY_CUDA(cudaFuncSetAttribute(k_capmv64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr_rc = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_rc = cudaFuncSetAttribute(k_capmv64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  LY_CUDA(attr_rc);
   dim3 grid((a.n + TI - 1) / TI, (a.nsys + SB - 1) / SB);
   // algorithmic work per system: the Cauchy-panel product, 8 flops per
   // complex MAC over n^2 k^2 MACs, plus the O(n k^2) epilogue

@@ -351,13 +351,17 @@ int lyap_mixed_prepare(lyap_seed* sd, cudaStream_t st) {
 
 int lyap_mixed_chunk(lyap_seed* sd, int Bc, const double* vinv, const lyap_opts& o, const SolveParams& prm,
                      cudaStream_t st, KrylovWS<float2>& ws, KrylovWS<float2>& wsadj, double2* Wp_out,
-                     double2* Zadj_out, std::vector<int>& iters, std::vector<int>& status,
+                     double2* Zadj_out, double2* Rres_out, std::vector<int>& iters, std::vector<int>& status,
                      std::vector<int>& rsteps) {
   if (!sd->mixed) return LYAP_EINVAL;
   iters.assign(Bc, 0);
   status.assign(Bc, LYAP_OK);
   rsteps.assign(Bc, 0);
   LY_TRY(refine(sd, Bc, vinv, sd->Ph.p, sd->ph_norm, false, sd->rec32, o, prm, st, ws, Wp_out, iters, status, rsteps));
+  // every system's final residual was evaluated (and kept) by its last refinement step
+  if (Rres_out)
+    LY_CUDA(cudaMemcpyAsync(Rres_out, sd->mixed->R64.p, sizeof(double2) * (size_t)Bc * sd->n * sd->k,
+                            cudaMemcpyDeviceToDevice, st));
   if (Zadj_out) {
     double hn = 0;
     {

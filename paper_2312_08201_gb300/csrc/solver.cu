@@ -16,6 +16,7 @@
 //     B = 1 this is the paper's system-to-system recycling.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "cplx.cuh"
 #include "krylov.cuh"
@@ -372,7 +373,16 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
       {
         const int ph_ = prof_begin(PK_RITZ, st);
         const size_t rsm = kry::ritz_smem_bytes(m, smax);
-      if (rsm > 48 * 1024) LY_CUDA(cudaFuncSetAttribute(kry::k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+      if (rsm > 48 * 1024) {
+        // the largest size any call needs (m <= 60, s <= 16), set once for all threads
+        static std::once_flag once;
+        static cudaError_t rc_attr = cudaSuccess;
+        std::call_once(once, [] {
+          rc_attr = cudaFuncSetAttribute(kry::k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kry::ritz_smem_bytes(60, 16));
+        });
+        LY_CUDA(rc_attr);
+      }
       kry::k_ritz<<<B, 32, rsm, st>>>(m, smax, s_cur, s, Lwant, cwant, ws.jstop.p, ws.H0.p,
                                                         ws.Bk.p, ws.F.p, ws.UU.p, ws.work.p, ws.wstride, ws.Pu.p,
                                                         ws.Qc.p, ws.ok.p); lyap_count_launch();

@@ -292,11 +292,12 @@ int make_map(CUtensorMap* map, const void* base, int rows, int kpad, int box_row
 int launch(const Maps& m, float* D, int ldd, int mrows, int mpad, int kpad, const int* count, int col_mult,
            int ncols_host, int ncols_cap, int* err, cudaStream_t st) {
   if (mpad % BM != 0 || kpad % BK != 0 || ncols_cap <= 0) return LYAP_EINVAL;
-  static bool attr = false;
-  if (!attr) {
-    LY_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr_rc = cudaSuccess;
+  std::call_once(once, [] {
+    attr_rc = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+  });
+  LY_CUDA(attr_rc);
   dim3 grid(mpad / BM, (ncols_cap + BN - 1) / BN);
   k_tc_gemm<<<grid, 192, SMEM_BYTES, st>>>(m.a_hi, m.a_lo, m.b_hi, m.b_lo, D, ldd, mrows, kpad / BK, count, col_mult,
                                           ncols_host, err);
