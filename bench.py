@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="systems solved in lockstep (0: library default)")
     ap.add_argument("--cpu-sample", type=int, default=4, help="oracle evaluations in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["precision", "serving"], default="precision")
+    ap.add_argument("--workload", choices=["precision", "serving", "kernels"], default="precision")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests per arrival rate")
     ap.add_argument("--serving-sizes", default="200,400,800,1600", help="serving: chain lengths (masses)")
     return ap.parse_args()
@@ -240,6 +240,47 @@ def run_serving(args, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ kernel probe
+def run_kernel_probe(args, local):
+    """Both capacitance operators on a full batch: T(v) applied to 1000
+    random inputs of the 800-state seed with the tensor-core operator (panel,
+    tcgen05 GEMM, epilogue) and with the FP64 kernel; CUDA-event timing per
+    kernel for the roofline. Used for ncu captures of full launches."""
+    import numpy as np
+    import torch
+
+    import paper_2312_08201_gb300 as ly
+    from workloads import workload_precision
+
+    torch.cuda.set_device(local)
+    ly.build()
+    p, vs = workload_precision()
+    ctx = ly.Context(local)
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(0)
+    v = torch.tensor(vs, dtype=torch.float64, device=dev)
+    w = torch.tensor(rng.standard_normal((len(vs), p.k, p.n, 2)), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        ly.test_apply(seed, v, w, ly.BF16_IR)
+        ly.test_apply(seed, v, w, ly.FP64)
+    ly.prof_enable(True)
+    for _ in range(max(1, args.steps)):
+        ly.test_apply(seed, v, w, ly.BF16_IR)
+    ly.test_apply(seed, v, w, ly.FP64)
+    prof, launches = ly.prof_read()
+    ly.prof_enable(False)
+    pk, how = peaks()
+    out = {}
+    for name, d in prof.items():
+        sec = d["total_ms"] / 1e3
+        out[name] = dict(launches=d["launches"], avg_ms=d["total_ms"] / d["launches"],
+                         tflops=d["flops"] / sec / 1e12 if d["flops"] else None,
+                         gbs=d["bytes"] / sec / 1e9 if d["bytes"] else None)
+    print(json.dumps(dict(probe="operators on 1000 systems, 800-state seed", kernels=out,
+                          bf16_peak_tflops=pk["bf16_tflops"], peak_source=how)), flush=True)
+
+
 # -------------------------------------------------------------------- ours
 def main():
     args = parse()
@@ -250,6 +291,8 @@ def main():
         return run_reference(args, rank)
     if args.workload == "serving":
         return run_serving(args, local) if rank == 0 else None
+    if args.workload == "kernels":
+        return run_kernel_probe(args, local) if rank == 0 else None
 
     import numpy as np
     import torch
