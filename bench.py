@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["best", "fp64", "bf16_ir"], default="best")
     ap.add_argument("--batch", type=int, default=0, help="systems solved in lockstep (0: library default)")
+    ap.add_argument("--pbar", type=int, default=-1, help="TSVD rank of the preconditioner coupling (-1: library default)")
     ap.add_argument("--cpu-sample", type=int, default=4, help="oracle evaluations in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["precision", "serving", "kernels"], default="precision")
@@ -321,6 +322,8 @@ def main():
     if precision == "best":
         precision = "bf16_ir" if _mixed_available(seed, v_dev) else "fp64"
     opts = dict(precision=ly.BF16_IR if precision == "bf16_ir" else ly.FP64, batch=args.batch)
+    if args.pbar >= 0:
+        opts["pbar"] = args.pbar
 
     # reference values of the FP64 GPU path (outside the timed region)
     f64 = seed.trace_EX(v_dev, precision=ly.FP64).cpu().numpy()
@@ -413,6 +416,7 @@ def main():
         ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="f64" if precision == "fp64" else "bf16x3-gemm/f32-krylov/f64-refine", data="synthetic",
         config=dict(workload=WORKLOAD, n=int(p.n), k=int(k), nv=int(nv), precision=precision, batch=args.batch,
+                    pbar=int(ly.default_opts(**opts).pbar),
                     l2="flushed between steps (256 MiB device write outside the timed events)",
                     parallelism="replicas" if world > 1 else "single-gpu", cond_Q=stats["cond_Q"]),
         accuracy=dict(max_rel_err_vs_fp64_path=float(acc.max()), median_rel_err=float(np.median(acc)),

@@ -88,7 +88,9 @@ typedef struct lyap_server lyap_server;
  * threshold 1e-10 tightened to 1e-12 for the FP64 path (the trace is a
  * linear functional of the capacitance solution and is wanted to 1e-10),
  * at most 300 iterations, s = 10 recycled vectors. The cycle length m is
- * not given in the paper; the default is 30. */
+ * not given in the paper; the default is 30. The TSVD rank defaults to 30
+ * (the paper uses 50 and 5 in its examples; 30 is the fastest setting of
+ * the mixed path on the 800-state benchmark). */
 typedef struct {
   double tol;        /* FP64 path: stop when ||r|| <= tol ||b||               */
   double refine_tol; /* mixed path: outer stop on the FP64 residual           */
@@ -96,8 +98,9 @@ typedef struct {
   int maxit;         /* max Krylov iterations per solve                       */
   int m;             /* cycle length (Arnoldi steps + recycled vectors)       */
   int s;             /* recycled vectors (harmonic Ritz, smallest |theta|)    */
-  int pbar;          /* rank of the off-diagonal coupling kept in the
-                        preconditioner (eq. (prec)); 0 = block diagonal only */
+  int pbar;          /* rank of the truncated SVD of the off-diagonal coupling
+                        kept in the preconditioner (eq. (prec)); 0 = block
+                        diagonal only; at most 64; default 30            */
   int batch;         /* systems solved in lockstep (0 = library's choice)    */
   int precision;     /* LYAP_FP64 or LYAP_BF16_IR                              */
   int max_refine;    /* mixed path: max refinement steps                      */

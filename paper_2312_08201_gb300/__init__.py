@@ -229,6 +229,8 @@ class Context:
 
     def close(self):
         if self.h:
+            for seed in list(getattr(self, "_seeds", [])):
+                seed.free()
             load().lyap_ctx_destroy(self.h)
             self.h = None
 
@@ -269,6 +271,11 @@ class Seed:
                                         MEM_HOST, ctypes.byref(o), ctypes.byref(h), ctypes.byref(cond))
         _check(code, "lyap_seed_factor")
         self.h = h
+        import weakref
+
+        if not hasattr(ctx, "_seeds"):
+            ctx._seeds = weakref.WeakSet()
+        ctx._seeds.add(self)
         self.n, self.k, self.g = n, k, g
         self.cond_Q = cond.value
 

@@ -10,6 +10,7 @@
 #include "lyap_internal.h"
 #include "prof.h"
 #include "mixed.h"
+#include "precond.cuh"
 #include "solver.h"
 
 // ------------------------------------------------------------- last error
@@ -26,6 +27,9 @@ struct SeedWork {
   DevBuf<double> vinv;
   DevBuf<double2> Wp, Zadj, Rres, tmp;
   DevBuf<double> red0, red1, red2, red3;
+  DevBuf<float2> wlu;
+  DevBuf<int> wpiv;
+  WoodState wood;
 };
 
 namespace {
@@ -80,7 +84,7 @@ extern "C" void lyap_opts_default(lyap_opts* o) {
   o->maxit = 300;
   o->m = 30;
   o->s = 10;
-  o->pbar = 0;
+  o->pbar = 30;
   o->batch = 0;
   o->precision = LYAP_FP64;
   o->max_refine = 10;
@@ -157,6 +161,7 @@ extern "C" int lyap_seed_factor(lyap_ctx* ctx, int n, int k, int g, const double
   lyap_opts o;
   lyap_opts_default(&o);
   if (opts) o = *opts;
+  (void)cudaGetLastError();  // a stale error of an unrelated earlier call is not this call's
   LY_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t st = pick_stream(ctx, o);
   const size_t nn = (size_t)n * n;
@@ -185,11 +190,13 @@ extern "C" int lyap_seed_factor(lyap_ctx* ctx, int n, int k, int g, const double
   }
   std::unique_ptr<lyap_seed> sd(new lyap_seed());
   sd->ctx = ctx;
+  sd->device = ctx->device;
   sd->n = n;
   sd->k = k;
   sd->g = g;
   LY_TRY(lyap_seed_build(ctx, sd.get(), pA, pU, pV, pG, pE, st));
   LY_TRY(lyap_mixed_prepare(sd.get(), st));
+  if (o.pbar > 0) LY_TRY(lyap_tsvd_prepare(sd.get(), o.pbar, st));
   sd->work = new SeedWork();
   if (cond_Q_out) *cond_Q_out = sd->cond_Q;
   *out = sd.release();
@@ -212,7 +219,7 @@ extern "C" int lyap_seed_stats_get(const lyap_seed* sd, lyap_seed_stats* o) {
 
 extern "C" int lyap_seed_free(lyap_seed* sd) {
   if (!sd) return LYAP_EINVAL;
-  cudaSetDevice(sd->ctx->device);
+  cudaSetDevice(sd->device);
   delete sd->work;
   lyap_mixed_free(sd);
   delete sd;
@@ -346,6 +353,7 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
   if (w.Wp.count < (size_t)B * N) LY_TRY(w.Wp.alloc((size_t)B * N));
   if (grad_host && w.Zadj.count < (size_t)B * N) LY_TRY(w.Zadj.alloc((size_t)B * N));
   if (w.Rres.count < (size_t)B * N) LY_TRY(w.Rres.alloc((size_t)B * N));
+  if (o.pbar > 0) LY_TRY(lyap_tsvd_prepare(sd, o.pbar, st));
   DevBuf<double> vdev;
   LY_TRY(vdev.alloc((size_t)B * k));
   std::vector<int> it, stt, ita, sta, rsteps;
@@ -356,10 +364,21 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
     k_vinv<<<grid_of((size_t)Bc * k), 256, 0, st>>>(Bc * k, vdev.p, w.vinv.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     bool have_resid = false;
+    const WoodState* wood = nullptr;
+    if (o.precision == LYAP_FP64 && o.pbar > 0 && sd->tsvd_r > 0) {
+      const int r = std::min(o.pbar, sd->tsvd_r);
+      if (w.wlu.count < (size_t)Bc * r * r) LY_TRY(w.wlu.alloc((size_t)B * r * r));
+      if (w.wpiv.count < (size_t)Bc * r) LY_TRY(w.wpiv.alloc((size_t)B * r));
+      w.wood.lu = w.wlu.p;
+      w.wood.piv = w.wpiv.p;
+      LY_TRY(wood_prepare(sd, r, Bc, w.vinv.p, false, w.wood, st));
+      wood = &w.wood;
+    }
     if (o.precision == LYAP_FP64) {
       SysOp<double2> op;
       op.sd = sd;
       op.vinv = w.vinv.p;
+      op.wood = wood;
       LY_TRY(gcrodr_chunk(op, Bc, sd->Ph.p, 0, sd->rec64, prm, w.ws64, it, stt, st));
       LY_CUDA(cudaMemcpyAsync(w.Wp.p, w.ws64.X.p, sizeof(double2) * Bc * N, cudaMemcpyDeviceToDevice, st));
       rsteps.assign(Bc, 0);
@@ -368,6 +387,7 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
         opa.sd = sd;
         opa.adjoint = true;
         opa.vinv = w.vinv.p;
+        opa.wood = wood;
         LY_TRY(gcrodr_chunk(opa, Bc, sd->h.p, 0, sd->rec64_adj, prm, w.ws64adj, ita, sta, st));
         LY_CUDA(cudaMemcpyAsync(w.Zadj.p, w.ws64adj.X.p, sizeof(double2) * Bc * N, cudaMemcpyDeviceToDevice, st));
         for (int b = 0; b < Bc; ++b) {
@@ -407,7 +427,8 @@ int entry(lyap_seed* sd, int nv, const double* v, int mem_kind, const lyap_opts*
   lyap_opts o;
   lyap_opts_default(&o);
   if (opts) o = *opts;
-  LY_CUDA(cudaSetDevice(sd->ctx->device));
+  (void)cudaGetLastError();  // a stale error of an unrelated earlier call is not this call's
+  LY_CUDA(cudaSetDevice(sd->device));
   cudaStream_t st = pick_stream(sd->ctx, o);
   CallIO io;
   LY_TRY(load_v(sd, nv, v, mem_kind, st, io));

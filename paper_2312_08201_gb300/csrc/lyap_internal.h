@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -90,6 +91,7 @@ struct lyap_ctx {
   cublasHandle_t blas = nullptr;
   cusolverDnHandle_t solver = nullptr;
   unsigned inject_pending = 0;  // host-side fault injection consumed by the next call
+  std::mutex handle_mu;         // serialises use of blas/solver across host threads
 };
 
 // Recycled subspace kept across calls (and across the parameter sequence):
@@ -106,6 +108,7 @@ struct Recycle {
 
 struct lyap_seed {
   lyap_ctx* ctx = nullptr;
+  int device = 0;  // kept here so the seed can be released after its context
   int n = 0, k = 0, g = 0;
   int real_path = 0;
   double cond_Q = 0, f0 = 0, max_re = 0, min_sum = 0;
@@ -125,6 +128,10 @@ struct lyap_seed {
   // Mixed path: Lc in two bf16 terms, real-split (see tc_gemm.cu).
   DevBuf<uint16_t> Lhi, Llo;
   int lc_ld = 0;  // padded leading dimension of the split operand
+  // Truncated SVD of the v-independent coupling operator (eq. (prec)):
+  // O ~ tsvd_N tsvd_M^T, nk x tsvd_r each (FP32), built on first use.
+  DevBuf<float2> tsvd_N, tsvd_M;
+  int tsvd_r = 0;
   // Recycle spaces: primal/adjoint x FP64/FP32-inner.
   Recycle<double2> rec64, rec64_adj;
   Recycle<float2> rec32, rec32_adj;

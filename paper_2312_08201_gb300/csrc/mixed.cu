@@ -39,6 +39,9 @@ struct MixedState {
   DevBuf<float2> R32;
   DevBuf<double> norms, vinv_c;
   DevBuf<int> act, cnt;
+  DevBuf<float2> wlu;
+  DevBuf<int> wpiv;
+  WoodState wood;
 };
 
 namespace {
@@ -296,6 +299,15 @@ int refine(lyap_seed* sd, int Bc, const double* vinv, const double2* rhs, double
     op.sd = sd;
     op.adjoint = adjoint;
     op.vinv = ms.vinv_c.p;
+    if (o.pbar > 0 && sd->tsvd_r > 0) {
+      const int r = std::min(o.pbar, sd->tsvd_r);
+      if (ms.wlu.count < (size_t)na * r * r) LY_TRY(ms.wlu.alloc((size_t)Bc * r * r));
+      if (ms.wpiv.count < (size_t)na * r) LY_TRY(ms.wpiv.alloc((size_t)Bc * r));
+      ms.wood.lu = ms.wlu.p;
+      ms.wood.piv = ms.wpiv.p;
+      LY_TRY(wood_prepare(sd, r, na, ms.vinv_c.p, adjoint, ms.wood, st));
+      op.wood = &ms.wood;
+    }
     LY_TRY(gcrodr_chunk<float2>(op, na, ms.R32.p, (size_t)N, rec, pin, ws, it, stt, st));
     k_scatter_add<<<dim3(gx(N), na), 256, 0, st>>>(N, ms.act.p, na, ws.X.p, ms.norms.p, W);
     lyap_count_launch();
@@ -404,6 +416,7 @@ int SysOp<float2>::precond(const int* list, const int* count, int B, const float
   lyap_count_launch();
   prof_end(ph, st, 0.0, (double)sd->n * sd->k * (2 * sizeof(float2) + sd->k * sizeof(double2)), 0, count);
   LY_CUDA(cudaGetLastError());
+  if (wood && wood->r > 0) LY_TRY(wood_apply<float2>(sd, *wood, adjoint, vinv, list, count, B, Out, out_ss, st));
   return LYAP_OK;
 }
 
@@ -411,7 +424,8 @@ int SysOp<float2>::precond(const int* list, const int* count, int B, const float
 extern "C" int lyap_test_apply(lyap_seed* sd, int nsys, const double* v, const double* w, int precision, int adjoint,
                                double* out) {
   if (!sd || nsys <= 0 || !v || !w || !out) return LYAP_EINVAL;
-  LY_CUDA(cudaSetDevice(sd->ctx->device));
+  (void)cudaGetLastError();
+  LY_CUDA(cudaSetDevice(sd->device));
   cudaStream_t st = sd->ctx->stream;
   const int k = sd->k;
   const size_t N = (size_t)sd->n * k;

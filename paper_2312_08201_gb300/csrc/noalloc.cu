@@ -99,7 +99,7 @@ extern "C" int lyap_check_solution_noalloc(lyap_seed* seed, int nv, const double
                         " complex doubles; split the call");
     return LYAP_EINVAL;
   }
-  LY_CUDA(cudaSetDevice(seed->ctx->device));
+  LY_CUDA(cudaSetDevice(seed->device));
   double2* scratch = nullptr;
   LY_TRY(scratch_for_current_device(&scratch));
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -105,7 +105,7 @@ void admit_locked(lyap_server* s) {
 
 void worker_loop(SeedSlot* slot) {
   lyap_server* s = slot->srv;
-  cudaSetDevice(s->ctx->device);
+  cudaSetDevice(slot->sd->device);
   for (;;) {
     std::vector<uint64_t> batch;
     {

@@ -510,5 +510,6 @@ int SysOp<double2>::precond(const int* list, const int* count, int B, const doub
   kry::k_precond_bj<double2><<<grid, kry::NT, 0, st>>>(sd->n, sd->k, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv,
                                                       In, in_ss, Out, out_ss); lyap_count_launch();
   LY_CUDA(cudaGetLastError());
+  if (wood && wood->r > 0) LY_TRY(wood_apply<double2>(sd, *wood, adjoint, vinv, list, count, B, Out, out_ss, st));
   return LYAP_OK;
 }

@@ -3,6 +3,7 @@
 #pragma once
 #include "capmv.cuh"
 #include "lyap_internal.h"
+#include "precond.cuh"
 
 struct SolveParams {
   double tol = 1e-12;
@@ -20,6 +21,7 @@ struct SysOp {
   lyap_seed* sd = nullptr;
   bool adjoint = false;
   const double* vinv = nullptr;  // B x k, device
+  const WoodState* wood = nullptr;  // truncated-SVD coupling (nullptr: block-Jacobi only)
   int apply(const int* list, const int* count, int B, const T2* In, size_t in_ss, T2* Out, size_t out_ss,
             cudaStream_t st) const;
   int apply_c0(int nvec, const T2* In, T2* Out, cudaStream_t st) const;

@@ -112,3 +112,18 @@ def test_mixed_full_size_precision_workload_sampled(ctx):
     idx = [0, 500, 999]
     ref = np.array([oracle.trace_EX(p.A0, p.U, p.V, p.G, p.E, vs[i]) for i in idx])
     assert rel_err(f16[idx], ref).max() <= TOL_MIXED
+
+
+def test_mixed_with_tsvd_preconditioner(ctx):
+    p, vs = workload_small_fp64()
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    f, info = seed.trace_EX(vs[::3], return_info=True, precision=ly.BF16_IR, pbar=20)
+    ref = oracle.sweep(p, vs[::3])
+    assert rel_err(f, ref).max() <= TOL_MIXED
+    A0, U, V, G, E, vs2 = random_problem(44, 37, 3, 5)
+    s2 = ly.Seed(ctx, A0, U, V, G, E)
+    f2, g2 = s2.grad(vs2[:3], precision=ly.BF16_IR, pbar=20)
+    for i, v in enumerate(vs2[:3]):
+        fo, go = oracle.gradient(A0, U, V, G, E, v)
+        assert rel_err(f2[i], fo) <= TOL_MIXED
+        assert np.abs(g2[i] - go).max() <= 1e-6 * np.abs(go).max()

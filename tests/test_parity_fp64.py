@@ -167,3 +167,26 @@ def test_full_size_precision_workload_sampled(ctx):
     idx = [0, 333, 666, 999]
     ref = np.array([oracle.trace_EX(p.A0, p.U, p.V, p.G, p.E, vs[i]) for i in idx])
     assert rel_err(f[idx], ref).max() <= TOL_FP64
+
+
+@pytest.mark.parametrize("pbar", [8, 30])
+def test_tsvd_preconditioner_keeps_results_and_cuts_iterations(ctx, pbar):
+    """The truncated-SVD coupling of eq. (prec) changes the iteration count,
+    never the answer (flexible recycled solver)."""
+    p, vs = workload_small_fp64()
+    sel = vs[::7]
+    s0 = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    f0, i0 = s0.trace_EX(sel, return_info=True, pbar=0)
+    s1 = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    f1, i1 = s1.trace_EX(sel, return_info=True, pbar=pbar)
+    ref = oracle.sweep(p, sel)
+    assert rel_err(f1, ref).max() <= TOL_FP64
+    assert rel_err(f0, ref).max() <= TOL_FP64
+    assert np.mean([i["iters"] for i in i1]) < np.mean([i["iters"] for i in i0])
+    A0, U, V, G, E, vs2 = random_problem(9, 37, 3, 5)
+    s2 = ly.Seed(ctx, A0, U, V, G, E)
+    f2, g2 = s2.grad(vs2[:3], pbar=pbar)
+    for i, v in enumerate(vs2[:3]):
+        fo, go = oracle.gradient(A0, U, V, G, E, v)
+        assert rel_err(f2[i], fo) <= TOL_FP64
+        assert np.abs(g2[i] - go).max() <= 1e-8 * np.abs(go).max()
