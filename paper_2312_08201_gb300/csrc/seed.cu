@@ -34,6 +34,45 @@ __global__ void k_transpose_to_complex(int n, const double* __restrict__ A, doub
   }
 }
 
+// part[blk] = (sum (A - A^T)^2, sum A^2) partial sums, fixed order
+__global__ void k_asym_partial(int n, const double* __restrict__ A, double* __restrict__ part) {
+  __shared__ double s0[256], s1[256];
+  double a = 0.0, b = 0.0;
+  const size_t total = (size_t)n * n;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = idx % n, j = idx / n;
+    const double x = A[idx], d = x - A[j + i * (size_t)n];
+    a += d * d;
+    b += x * x;
+  }
+  s0[threadIdx.x] = a;
+  s1[threadIdx.x] = b;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      s0[threadIdx.x] += s0[threadIdx.x + st];
+      s1[threadIdx.x] += s1[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s0[0];
+    part[2 * blockIdx.x + 1] = s1[0];
+  }
+}
+
+// Orthogonal eigenvectors V (real, n x n): Qp = V, Qi = V^T; lam = w (real).
+__global__ void k_from_symmetric(int n, const double* __restrict__ V, const double* __restrict__ w,
+                                 double2* __restrict__ Qp, double2* __restrict__ Qi, double2* __restrict__ lam) {
+  const size_t total = (size_t)n * n;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = idx % n, j = idx / n;
+    Qp[idx] = make_double2(V[idx], 0.0);
+    Qi[idx] = make_double2(V[j + i * (size_t)n], 0.0);
+    if (j == 0) lam[i] = make_double2(w[i], 0.0);
+  }
+}
+
 __global__ void k_real_to_complex(size_t count, const double* __restrict__ in, double2* __restrict__ out) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x)
     out[idx] = make_double2(in[idx], 0.0);
@@ -198,48 +237,93 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
   LY_TRY(W1.alloc(nn));
   LY_TRY(W2.alloc(nn));
 
-  // ---- eig(A_p), A_p = A0^T (complex FP64, right eigenvectors) ----------
-  k_transpose_to_complex<<<grid_for(nn), 256, 0, st>>>(n, A0, W1.p); lyap_count_launch();
-  LY_CUDA(cudaGetLastError());
+  // ---- symmetric A0: orthogonal eigenvectors from the symmetric solver ----
+  bool symmetric = false;
   {
-    cusolverDnParams_t params;
-    LY_SOLVER(cusolverDnCreateParams(&params));
-    size_t dws = 0, hws = 0;
-    cusolverStatus_t s1 = cusolverDnXgeev_bufferSize(
-        ctx->solver, params, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, n, CUDA_C_64F, W1.p, n,
-        CUDA_C_64F, sd->lam.p, CUDA_C_64F, nullptr, 1, CUDA_C_64F, sd->Qp.p, n, CUDA_C_64F, &dws, &hws);
-    if (s1 != CUSOLVER_STATUS_SUCCESS) {
-      cusolverDnDestroyParams(params);
-      lyap_set_last_error("cusolverDnXgeev_bufferSize failed: " + std::to_string(s1));
-      return LYAP_ESOLVER;
+    DevBuf<double> part;
+    LY_TRY(part.alloc(2 * RED_BLOCKS));
+    k_asym_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, A0, part.p);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    std::vector<double> hp(2 * RED_BLOCKS);
+    LY_CUDA(cudaMemcpyAsync(hp.data(), part.p, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
+    LY_CUDA(cudaStreamSynchronize(st));
+    double asym = 0, nrm = 0;
+    for (int b = 0; b < RED_BLOCKS; ++b) {
+      asym += hp[2 * b];
+      nrm += hp[2 * b + 1];
     }
-    DevBuf<char> dwork;
+    symmetric = asym <= 1e-28 * nrm;
+  }
+  if (symmetric) {
+    // A_p = A0^T = A0 = V diag(w) V^T: Qp = V, Qp^{-1} = V^T (repeated
+    // eigenvalues keep an orthonormal basis, unlike a general eigensolver)
+    DevBuf<double> Vr, w, work;
     DevBuf<int> dinfo;
-    int rc = dwork.alloc(dws ? dws : 1);
-    if (rc == LYAP_OK) rc = dinfo.alloc(1);
-    if (rc != LYAP_OK) {
-      cusolverDnDestroyParams(params);
-      return rc;
-    }
-    std::vector<char> hwork(hws ? hws : 1);
-    cusolverStatus_t s2 = cusolverDnXgeev(ctx->solver, params, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR,
-                                          n, CUDA_C_64F, W1.p, n, CUDA_C_64F, sd->lam.p, CUDA_C_64F, nullptr, 1,
-                                          CUDA_C_64F, sd->Qp.p, n, CUDA_C_64F, dwork.p, dws, hwork.data(), hws,
-                                          dinfo.p);
-    cusolverDnDestroyParams(params);
-    if (s2 != CUSOLVER_STATUS_SUCCESS) {
-      lyap_set_last_error("cusolverDnXgeev failed: " + std::to_string(s2));
-      return LYAP_ESOLVER;
-    }
+    LY_TRY(Vr.alloc(nn));
+    LY_TRY(w.alloc(n));
+    LY_TRY(dinfo.alloc(1));
+    LY_CUDA(cudaMemcpyAsync(Vr.p, A0, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int lwork = 0;
+    LY_SOLVER(cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, Vr.p, n,
+                                          w.p, &lwork));
+    LY_TRY(work.alloc(lwork > 0 ? lwork : 1));
+    LY_SOLVER(cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, Vr.p, n, w.p, work.p,
+                               lwork, dinfo.p));
     int info = 0;
     LY_CUDA(cudaMemcpyAsync(&info, dinfo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     LY_CUDA(cudaStreamSynchronize(st));
     if (info != 0) {
-      lyap_set_last_error("geev info = " + std::to_string(info));
+      lyap_set_last_error("syevd info = " + std::to_string(info));
       return LYAP_ESOLVER;
     }
-  }
+    k_from_symmetric<<<grid_for(nn), 256, 0, st>>>(n, Vr.p, w.p, sd->Qp.p, sd->Qi.p, sd->lam.p);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+  } else {
+    // ---- eig(A_p), A_p = A0^T (complex FP64, right eigenvectors) ----------
+    k_transpose_to_complex<<<grid_for(nn), 256, 0, st>>>(n, A0, W1.p); lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    {
+      cusolverDnParams_t params;
+      LY_SOLVER(cusolverDnCreateParams(&params));
+      size_t dws = 0, hws = 0;
+      cusolverStatus_t s1 = cusolverDnXgeev_bufferSize(
+          ctx->solver, params, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR, n, CUDA_C_64F, W1.p, n,
+          CUDA_C_64F, sd->lam.p, CUDA_C_64F, nullptr, 1, CUDA_C_64F, sd->Qp.p, n, CUDA_C_64F, &dws, &hws);
+      if (s1 != CUSOLVER_STATUS_SUCCESS) {
+        cusolverDnDestroyParams(params);
+        lyap_set_last_error("cusolverDnXgeev_bufferSize failed: " + std::to_string(s1));
+        return LYAP_ESOLVER;
+      }
+      DevBuf<char> dwork;
+      DevBuf<int> dinfo;
+      int rc = dwork.alloc(dws ? dws : 1);
+      if (rc == LYAP_OK) rc = dinfo.alloc(1);
+      if (rc != LYAP_OK) {
+        cusolverDnDestroyParams(params);
+        return rc;
+      }
+      std::vector<char> hwork(hws ? hws : 1);
+      cusolverStatus_t s2 = cusolverDnXgeev(ctx->solver, params, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR,
+                                            n, CUDA_C_64F, W1.p, n, CUDA_C_64F, sd->lam.p, CUDA_C_64F, nullptr, 1,
+                                            CUDA_C_64F, sd->Qp.p, n, CUDA_C_64F, dwork.p, dws, hwork.data(), hws,
+                                            dinfo.p);
+      cusolverDnDestroyParams(params);
+      if (s2 != CUSOLVER_STATUS_SUCCESS) {
+        lyap_set_last_error("cusolverDnXgeev failed: " + std::to_string(s2));
+        return LYAP_ESOLVER;
+      }
+      int info = 0;
+      LY_CUDA(cudaMemcpyAsync(&info, dinfo.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      LY_CUDA(cudaStreamSynchronize(st));
+      if (info != 0) {
+        lyap_set_last_error("geev info = " + std::to_string(info));
+        return LYAP_ESOLVER;
+      }
+    }
 
+  }
   // ---- stability and uniqueness -----------------------------------------
   {
     DevBuf<double> stats;
@@ -259,8 +343,8 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
     }
   }
 
-  // ---- Qi = Qp^{-1} by LU -------------------------------------------------
-  {
+  // ---- Qi = Qp^{-1} by LU (general case) ------------------------------------
+  if (!symmetric) {
     LY_CUDA(cudaMemcpyAsync(W1.p, sd->Qp.p, nn * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     k_identity<<<grid_for(nn), 256, 0, st>>>(n, sd->Qi.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
