@@ -31,6 +31,7 @@ METRIC = "trace(EX(v)) evals/sec at rel err<=1e-8 vs FP64 path; p50/p99 request 
 WORKLOAD = "chain400 n=800 k=2, 1000 v log-uniform [1e-2,1e2]^2 NN-ordered, Haar-dense"
 FP64_PEAK_FLOPS_PER_CLK_SM = 4.0  # 2 FP64 FMA per clock per SM (1.25 TFLOP/s at 2070 MHz x 152 SMs)
 SMS = 152
+FP32_LANES_PER_SM = 128.0  # FP32 lane-instructions per clock per SM
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--precision", choices=["best", "fp64", "bf16_ir"], default="best")
     ap.add_argument("--batch", type=int, default=0, help="systems solved in lockstep (0: library default)")
     ap.add_argument("--pbar", type=int, default=-1, help="TSVD rank of the preconditioner coupling (-1: library default)")
+    ap.add_argument("--residual", choices=["ff", "fp64"], default="ff",
+                    help="arithmetic of the mixed path's refinement residual")
     ap.add_argument("--cpu-sample", type=int, default=4, help="oracle evaluations in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["precision", "serving", "kernels"], default="precision")
@@ -324,6 +327,8 @@ def main():
     opts = dict(precision=ly.BF16_IR if precision == "bf16_ir" else ly.FP64, batch=args.batch)
     if args.pbar >= 0:
         opts["pbar"] = args.pbar
+    if precision == "bf16_ir":
+        opts["residual"] = ly.RESID_FF if args.residual == "ff" else ly.RESID_FP64
 
     # reference values of the FP64 GPU path (outside the timed region)
     f64 = seed.trace_EX(v_dev, precision=ly.FP64).cpu().numpy()
@@ -395,6 +400,15 @@ def main():
             roof = dict(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=None,
                         kernel=dom_name, peak_source="FP64 FMA pipe: 152 SMs x 4 flop/clk x max SM clock",
                         launches=d["launches"], avg_launch_ms=d["total_ms"] / d["launches"])
+        elif dom_name == "capmv_ff":
+            sm_clock = float(pk.get("sm_max_mhz", 2070.0))
+            peak = FP32_LANES_PER_SM * SMS * sm_clock * 1e6 / 1e12
+            ach = d["flops"] / sec / 1e12
+            roof = dict(bound="alu", achieved=ach, peak=peak, unit="Tinst/s", frac=ach / peak, traffic=None,
+                        kernel=dom_name,
+                        peak_source="FP32 pipe: 152 SMs x 128 lane-instructions/clk x max SM clock "
+                                    "(achieved: 54 FP32 instructions per float-float complex MAC)",
+                        launches=d["launches"], avg_launch_ms=d["total_ms"] / d["launches"])
         elif dom_name == "tc_gemm":
             peak = float(pk["bf16_tflops_sustained"])
             ach = d["flops"] / sec / 1e12
@@ -414,9 +428,11 @@ def main():
     line = dict(
         metric=METRIC, value=value, unit="evals/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="f64" if precision == "fp64" else "bf16x3-gemm/f32-krylov/f64-refine", data="synthetic",
+        dtype="f64" if precision == "fp64" else
+        "bf16x3-gemm/f32-krylov/" + ("ff-refine" if args.residual == "ff" else "f64-refine"), data="synthetic",
         config=dict(workload=WORKLOAD, n=int(p.n), k=int(k), nv=int(nv), precision=precision, batch=args.batch,
                     pbar=int(ly.default_opts(**opts).pbar),
+                    residual=args.residual if precision == "bf16_ir" else "fp64",
                     l2="flushed between steps (256 MiB device write outside the timed events)",
                     parallelism="replicas" if world > 1 else "single-gpu", cond_Q=stats["cond_Q"]),
         accuracy=dict(max_rel_err_vs_fp64_path=float(acc.max()), median_rel_err=float(np.median(acc)),

@@ -74,6 +74,13 @@ extern "C" {
 #define LYAP_FP64 0
 #define LYAP_BF16_IR 2
 
+/* Arithmetic of the mixed path's refinement residual (lyap_opts.residual).
+ * Both evaluate P - T(v) W with an error of the order of FP64 rounding:
+ * FF pairs two FP32 values per number (about 48 significant bits, exact
+ * products by FMA) and runs on the FP32 pipes; FP64 uses the FP64 pipes. */
+#define LYAP_RESID_FF 0
+#define LYAP_RESID_FP64 1
+
 /* Fault-injection bits for lyap_opts.inject (host-side only; no GPU fault). */
 #define LYAP_INJECT_ALLOC_FAIL 0x1u   /* next workspace allocation fails     */
 #define LYAP_INJECT_FORCE_MAXIT 0x2u  /* solver stops after one cycle         */
@@ -107,6 +114,7 @@ typedef struct {
   size_t hbm_budget; /* serving: admission budget in bytes (0 = 80% of free)  */
   void* stream;      /* cudaStream_t to run on (NULL = the context's stream)  */
   unsigned inject;   /* LYAP_INJECT_* bits (tests only)                       */
+  int residual;      /* mixed path: LYAP_RESID_FF (default) or LYAP_RESID_FP64 */
 } lyap_opts;
 
 /* Per-result report. */
@@ -198,7 +206,7 @@ int lyap_grad(lyap_seed* seed, int nv, const double* v, int mem_kind, const lyap
               double* trace_out, double* grad_out, lyap_result_info* info);
 
 /* ----------------------------------------------------------------- serving
- * A continuous-batching server (spec addition; the paper solves one
+ * A continuous-batching server (an addition; the paper solves one
  * sweep at a time). Requests (one seed, nv parameter vectors) enter a FIFO
  * and are admitted while the registered seeds' resident bytes plus the
  * workspace estimate of all admitted, unfinished requests stay within

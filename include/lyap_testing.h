@@ -16,8 +16,11 @@ extern "C" {
  * v: device, nsys x k row-major; w, out: device, nsys x n x k complex128
  * (column-major per system). precision LYAP_FP64 uses the FP64 Cauchy-panel
  * kernel; LYAP_BF16_IR the tensor-core operator of the mixed path (inputs
- * rounded to FP32, BF16-split GEMM, FP32 epilogue). Synchronises. Returns
- * LYAP_EDEVICE_TIMEOUT if a bounded device wait expired. */
+ * rounded to FP32, BF16-split GEMM, FP32 epilogue); LYAP_TEST_FF the
+ * float-float kernel of the mixed path's refinement residual (FP64 in and
+ * out, float-float products). Synchronises. Returns LYAP_EDEVICE_TIMEOUT if
+ * a bounded device wait expired. */
+#define LYAP_TEST_FF 3
 int lyap_test_apply(lyap_seed* seed, int nsys, const double* v, const double* w, int precision, int adjoint,
                     double* out);
 

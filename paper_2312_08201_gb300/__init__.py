@@ -41,6 +41,9 @@ BF16_IR = 2
 INJECT_ALLOC_FAIL = 0x1
 INJECT_FORCE_MAXIT = 0x2
 INJECT_DEVICE_WAIT = 0x4
+RESID_FF = 0
+RESID_FP64 = 1
+TEST_FF = 3  # lyap_test_apply: float-float residual kernel
 
 
 class LyapOpts(ctypes.Structure):
@@ -58,6 +61,7 @@ class LyapOpts(ctypes.Structure):
         ("hbm_budget", ctypes.c_size_t),
         ("stream", ctypes.c_void_p),
         ("inject", ctypes.c_uint),
+        ("residual", ctypes.c_int),
     ]
 
 

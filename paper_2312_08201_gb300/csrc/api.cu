@@ -91,6 +91,7 @@ extern "C" void lyap_opts_default(lyap_opts* o) {
   o->hbm_budget = 0;
   o->stream = nullptr;
   o->inject = 0;
+  o->residual = LYAP_RESID_FF;
 }
 
 extern "C" const char* lyap_strerror(int code) {

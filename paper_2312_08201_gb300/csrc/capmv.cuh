@@ -41,3 +41,12 @@ struct CapArgs64 {
 };
 
 int capmv64_launch(const CapArgs64& a, cudaStream_t st);
+
+// The same operator in float-float arithmetic on the FP32 pipes (FP64-level
+// accuracy; see capmv_df.cu). Lff: n x n pairs (re hi, re lo, im hi, im lo) of
+// lc_scale * Lc, built by capmv_df_build_lc; p_scale: power of two applied to
+// P2; sw: device scratch indexed by system (>= largest system index + 1),
+// overwritten with each listed system's W scale.
+int capmv_df_build_lc(int n, const double2* lam, double lc_scale, float4* Lff, cudaStream_t st);
+int capmv_df_launch(const CapArgs64& a, const float4* Lff, double lc_scale, double p_scale, double* sw,
+                    cudaStream_t st);

@@ -1,4 +1,4 @@
-// Mixed-precision path (spec addition 1, built on paper §2.1):
+// Mixed-precision path (an addition to the paper's FP64 method of §2.1):
 //  * inner operator T~(v) in FP32 with the Cauchy-panel product on tcgen05
 //    tensor cores. The complex product Lc Z is one real GEMM with
 //      A[2i][2j] = Re Lc_ij, A[2i][2j+1] = -Im Lc_ij,
@@ -9,8 +9,9 @@
 //    accumulates hi*hi + hi*lo + lo*hi in FP32 (about 16 significant bits);
 //  * FP32 recycled Krylov inner solves (same batched GCRO-DR, float vectors,
 //    FP64 small matrices);
-//  * iterative refinement on the FP64 capacitance residual
-//    r = P - T(v) W (FP64 kernel), W += ||r|| * solve(T~, r/||r||), until
+//  * iterative refinement on the capacitance residual r = P - T(v) W,
+//    evaluated to FP64 accuracy (float-float kernel on the FP32 pipes, or
+//    the FP64 kernel), W += ||r|| * solve(T~, r/||r||), until
 //    ||r|| <= refine_tol ||P||. The trace and the update stay in FP64.
 #include <cuda_bf16.h>
 
@@ -23,6 +24,7 @@
 #include "mixed.h"
 #include "prof.h"
 #include "tc_gemm.cuh"
+#include "lyap_testing.h"
 
 struct MixedState {
   int mpad = 0, kpad = 0;
@@ -42,6 +44,10 @@ struct MixedState {
   DevBuf<float2> wlu;
   DevBuf<int> wpiv;
   WoodState wood;
+  // float-float residual operands (capmv_df.cu)
+  DevBuf<float4> Lff;  // n x n
+  double lc_scale = 1.0, p_scale = 1.0;
+  DevBuf<double> sw;   // bcap
 };
 
 namespace {
@@ -222,6 +228,7 @@ int ensure_refine(lyap_seed* sd, int Bc) {
   LY_TRY(ms.vinv_c.alloc((size_t)Bc * sd->k));
   LY_TRY(ms.act.alloc(Bc));
   LY_TRY(ms.cnt.alloc(1));
+  LY_TRY(ms.sw.alloc(Bc));
   ms.bcap = Bc;
   return LYAP_OK;
 }
@@ -270,7 +277,8 @@ int refine(lyap_seed* sd, int Bc, const double* vinv, const double2* rhs, double
       a.list = ms.act.p;
       a.count = ms.cnt.p;
       a.nsys = nact;
-      LY_TRY(capmv64_launch(a, st));
+      if (o.residual == LYAP_RESID_FP64) LY_TRY(capmv64_launch(a, st));
+      else LY_TRY(capmv_df_launch(a, ms.Lff.p, ms.lc_scale, ms.p_scale, ms.sw.p, st));
       kry::k_norms<double2><<<Bc, kry::NT, 0, st>>>(N, Bc, ms.R64.p, N, ms.norms.p);
       lyap_count_launch();
       LY_CUDA(cudaGetLastError());
@@ -351,12 +359,32 @@ int lyap_mixed_prepare(lyap_seed* sd, cudaStream_t st) {
   k_to_f32<<<gx((size_t)n * k * k), 256, 0, st>>>((size_t)n * k * k, sd->Gd.p, ms->Gd32.p);
   lyap_count_launch(3);
   LY_CUDA(cudaGetLastError());
+  {
+    // power-of-two scales that bring Lc and Ub/Vb to magnitudes near 1 for the
+    // float-float residual (max |Lc| = 1 / min |lam_i + lam_j|)
+    std::vector<double2> hu((size_t)n * k), hv((size_t)n * k);
+    LY_CUDA(cudaMemcpyAsync(hu.data(), sd->Ub.p, sizeof(double2) * hu.size(), cudaMemcpyDeviceToHost, st));
+    LY_CUDA(cudaMemcpyAsync(hv.data(), sd->Vb.p, sizeof(double2) * hv.size(), cudaMemcpyDeviceToHost, st));
+    LY_CUDA(cudaStreamSynchronize(st));
+    double pm = 0.0;
+    for (size_t e = 0; e < hu.size(); ++e)
+      pm = std::max({pm, std::fabs(hu[e].x), std::fabs(hu[e].y), std::fabs(hv[e].x), std::fabs(hv[e].y)});
+    const auto pow2_inv = [](double m) {
+      const int e = (m > 0.0 && std::isfinite(m)) ? std::max(-600, std::min(600, std::ilogb(m))) : 0;
+      return std::ldexp(1.0, -e);
+    };
+    ms->p_scale = pow2_inv(pm);
+    ms->lc_scale = pow2_inv(sd->min_sum > 0.0 ? 1.0 / sd->min_sum : 1.0);
+    LY_TRY(ms->Lff.alloc((size_t)n * n));
+    LY_TRY(capmv_df_build_lc(n, sd->lam.p, ms->lc_scale, ms->Lff.p, st));
+  }
   LY_TRY(tc::make_map(&ms->maps.a_hi, ms->Ahi.p, ms->mpad, ms->kpad, tc::BM));
   LY_TRY(tc::make_map(&ms->maps.a_lo, ms->Alo.p, ms->mpad, ms->kpad, tc::BM));
   LY_TRY(ms->err.alloc(1));
   LY_CUDA(cudaMemsetAsync(ms->err.p, 0, sizeof(int), st));
   LY_CUDA(cudaStreamSynchronize(st));
-  sd->resident_bytes += ms->Ahi.bytes() + ms->Alo.bytes() + ms->Ub32.bytes() + ms->Vb32.bytes() + ms->Gd32.bytes();
+  sd->resident_bytes += ms->Ahi.bytes() + ms->Alo.bytes() + ms->Ub32.bytes() + ms->Vb32.bytes() + ms->Gd32.bytes() +
+                        ms->Lff.bytes();
   sd->mixed = ms.release();
   return LYAP_OK;
 }
@@ -436,7 +464,7 @@ extern "C" int lyap_test_apply(lyap_seed* sd, int nsys, const double* v, const d
   LY_CUDA(cudaStreamSynchronize(st));
   for (double& x : hv) x = 1.0 / x;
   LY_CUDA(cudaMemcpyAsync(vinv.p, hv.data(), sizeof(double) * hv.size(), cudaMemcpyHostToDevice, st));
-  if (precision == LYAP_FP64) {
+  if (precision == LYAP_FP64 || precision == LYAP_TEST_FF) {
     CapArgs64 a{};
     a.n = sd->n;
     a.k = k;
@@ -452,7 +480,14 @@ extern "C" int lyap_test_apply(lyap_seed* sd, int nsys, const double* v, const d
     a.ldo = N;
     a.mode = CAP_T;
     a.nsys = nsys;
-    LY_TRY(capmv64_launch(a, st));
+    if (precision == LYAP_FP64) {
+      LY_TRY(capmv64_launch(a, st));
+    } else {
+      DevBuf<double> sw;
+      LY_TRY(sw.alloc(nsys));
+      LY_TRY(capmv_df_launch(a, sd->mixed->Lff.p, sd->mixed->lc_scale, sd->mixed->p_scale, sw.p, st));
+      LY_CUDA(cudaStreamSynchronize(st));
+    }
   } else {
     LY_TRY(mixed_apply<double2>(sd, adjoint != 0, vinv.p, nullptr, nullptr, nsys, reinterpret_cast<const double2*>(w),
                                 N, reinterpret_cast<double2*>(out), N, CAP_T, st));

@@ -21,7 +21,9 @@ enum ProfKernel {
   PK_CYCLE = 9,     // cycle start/solve/update kernels
   PK_PANEL = 10,    // panel build for the tensor-core GEMM
   PK_RECSTART = 11, // recycle start (AU, CholQR2, projection)
-  PK_COUNT = 12
+  PK_CAPMV_FF = 12, // float-float capacitance matvec (mixed-path residual);
+                    // its "flops" are FP32 lane instructions
+  PK_COUNT = 13
 };
 
 void lyap_count_launch(int n = 1);

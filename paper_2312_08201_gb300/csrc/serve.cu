@@ -1,4 +1,4 @@
-// Serving loop (spec addition 5): continuous batching of parameter
+// Serving loop (an addition; the paper solves one sweep at a time): continuous batching of parameter
 // sweeps from different seeds, admission by device-memory footprint,
 // per-request latency.
 //

@@ -5,6 +5,9 @@ Tolerances:
   * GEMM: |D - A B^T| <= 2^-13 |A| |B|^T elementwise (two-term BF16 split,
     FP32 accumulation: about 16 significant bits per product);
   * operator: ||T~ w - T w|| <= 1e-4 ||T w|| per system;
+  * float-float residual kernel: ||T_ff w - T w|| <= 1e-12 ||T w|| per
+    system (about 48 significant bits per product; the sums run over n
+    terms), unchanged under power-of-two rescaling of w;
   * traces after refinement: 1e-8 relative to the oracle;
   * gradients after refinement: 1e-6 relative to the largest component.
 """
@@ -127,3 +130,50 @@ def test_mixed_with_tsvd_preconditioner(ctx):
         fo, go = oracle.gradient(A0, U, V, G, E, v)
         assert rel_err(f2[i], fo) <= TOL_MIXED
         assert np.abs(g2[i] - go).max() <= 1e-6 * np.abs(go).max()
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_float_float_operator_matches_fp64_operator(ctx, adjoint):
+    import torch
+
+    p, vs = workload_small_fp64()
+    A0, U, V, G, E, vs2 = random_problem(55, 70, 8, 3)
+    for A0_, U_, V_, G_, E_, vv in ((p.A0, p.U, p.V, p.G, p.E, vs), (A0, U, V, G, E, vs2)):
+        seed = ly.Seed(ctx, A0_, U_, V_, G_, E_)
+        n, k = U_.shape
+        rng = np.random.default_rng(2)
+        w = rng.standard_normal((9, k, n, 2))
+        v = torch.tensor(vv[:9], dtype=torch.float64, device="cuda")
+        for scale in (1.0, 2.0**-700, 2.0**400, 1e-30):
+            wt = torch.tensor(w * scale, dtype=torch.float64, device="cuda")
+            y64 = ly.test_apply(seed, v, wt, ly.FP64, adjoint).cpu().numpy()
+            yff = ly.test_apply(seed, v, wt, ly.TEST_FF, adjoint).cpu().numpy()
+            assert np.isfinite(yff).all()
+            for b in range(9):
+                assert np.linalg.norm(yff[b] - y64[b]) <= 1e-12 * np.linalg.norm(y64[b]), (scale, b)
+
+
+def test_float_float_operator_at_converged_solution(ctx):
+    """At the solution T W = P the kernel output must reproduce P to the
+    accuracy the refinement asks for (refine_tol 1e-11)."""
+    import torch
+
+    p, vs = workload_precision()
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    W, _ = seed.param_solve(vs[:16], precision=ly.FP64)
+    v = torch.tensor(vs[:16], dtype=torch.float64, device="cuda")
+    wt = torch.tensor(np.stack([W.real, W.imag], axis=-1), dtype=torch.float64, device="cuda")
+    y64 = ly.test_apply(seed, v, wt, ly.FP64, False).cpu().numpy()
+    yff = ly.test_apply(seed, v, wt, ly.TEST_FF, False).cpu().numpy()
+    for b in range(16):
+        assert np.linalg.norm(yff[b] - y64[b]) <= 1e-13 * np.linalg.norm(y64[b])
+
+
+def test_mixed_residual_arithmetic_options_agree(ctx):
+    p, vs = workload_small_fp64()
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    ref = oracle.sweep(p, vs[::4])
+    for resid in (ly.RESID_FF, ly.RESID_FP64):
+        f, info = seed.trace_EX(vs[::4], return_info=True, precision=ly.BF16_IR, residual=resid)
+        assert rel_err(f, ref).max() <= TOL_MIXED
+        assert all(i["status"] == 0 and i["rel_resid"] <= 1e-11 for i in info)
