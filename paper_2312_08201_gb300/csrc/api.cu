@@ -27,8 +27,7 @@ struct SeedWork {
   DevBuf<double> vinv;
   DevBuf<double2> Wp, Zadj, Rres, tmp;
   DevBuf<double> red0, red1, red2, red3;
-  DevBuf<float2> wlu;
-  DevBuf<int> wpiv;
+  DevBuf<float2> wcinv, wpart;
   WoodState wood;
 };
 
@@ -368,10 +367,10 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
     const WoodState* wood = nullptr;
     if (o.precision == LYAP_FP64 && o.pbar > 0 && sd->tsvd_r > 0) {
       const int r = std::min(o.pbar, sd->tsvd_r);
-      if (w.wlu.count < (size_t)Bc * r * r) LY_TRY(w.wlu.alloc((size_t)B * r * r));
-      if (w.wpiv.count < (size_t)Bc * r) LY_TRY(w.wpiv.alloc((size_t)B * r));
-      w.wood.lu = w.wlu.p;
-      w.wood.piv = w.wpiv.p;
+      if (w.wcinv.count < (size_t)Bc * r * r) LY_TRY(w.wcinv.alloc((size_t)B * r * r));
+      if (w.wpart.count < wood_part_count(n, k, Bc, r)) LY_TRY(w.wpart.alloc(wood_part_count(n, k, B, r)));
+      w.wood.cinv = w.wcinv.p;
+      w.wood.cpart = w.wpart.p;
       LY_TRY(wood_prepare(sd, r, Bc, w.vinv.p, false, w.wood, st));
       wood = &w.wood;
     }

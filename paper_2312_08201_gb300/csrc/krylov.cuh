@@ -410,65 +410,6 @@ __global__ void __launch_bounds__(NT) k_project(int N, int s, const int* __restr
   }
 }
 
-// -------------------------------------------------- block-Jacobi preconditioner
-// The block-diagonal part of T(v) (eq. (N1M1) and its (2,2) analogue; both
-// act with the same k x k matrices on the reduced unknown): for row i,
-// K_i[t, p] = delta_tp / v_t - Gd[i, p, t]  (adjoint: transpose). Apply
-// z[i, :] = K_i^{-1} r[i, :] by Gaussian elimination with partial pivoting.
-template <typename T2>
-__global__ void __launch_bounds__(NT) k_precond_bj(int n, int k, const int* __restrict__ list,
-                                                  const int* __restrict__ count, const double2* __restrict__ Gd,
-                                                  int gT, const double* __restrict__ vinv, const T2* __restrict__ In,
-                                                  size_t in_ss, T2* __restrict__ Out, size_t out_ss) {
-  const int slot = blockIdx.y;
-  if (slot >= *count) return;
-  const int b = list[slot];
-  const int i = blockIdx.x * NT + threadIdx.x;
-  if (i >= n) return;
-  using RT = typename RealOf<T2>::T;
-  T2 K[8][9];
-  for (int t = 0; t < k; ++t) {
-    for (int p = 0; p < k; ++p) {
-      size_t gi = gT ? ((size_t)(t * k + p) * n + i) : ((size_t)(p * k + t) * n + i);
-      double2 v = cscale(Gd[gi], -1.0);
-      if (t == p) v.x += vinv[(size_t)b * k + t];
-      K[t][p] = cvt<T2>(v);
-    }
-    K[t][k] = In[(size_t)b * in_ss + (size_t)t * n + i];
-  }
-  for (int c = 0; c < k; ++c) {
-    int piv = c;
-    RT best = cabs2(K[c][c]);
-    for (int r = c + 1; r < k; ++r) {
-      RT a = cabs2(K[r][c]);
-      if (a > best) {
-        best = a;
-        piv = r;
-      }
-    }
-    if (piv != c)
-      for (int q = 0; q <= k; ++q) {
-        T2 tmp = K[c][q];
-        K[c][q] = K[piv][q];
-        K[piv][q] = tmp;
-      }
-    const T2 zero = cvt<T2>(make_double2(0.0, 0.0));
-    const T2 inv = best > 0 ? cscale(cconj(K[c][c]), (RT)1 / best) : zero;
-    for (int r = c + 1; r < k; ++r) {
-      const T2 f = cmul(K[r][c], inv);
-      for (int q = c; q <= k; ++q) K[r][q] = csub(K[r][q], cmul(f, K[c][q]));
-    }
-  }
-  T2 z[8];
-  for (int c = k - 1; c >= 0; --c) {
-    T2 x = K[c][k];
-    for (int q = c + 1; q < k; ++q) x = csub(x, cmul(K[c][q], z[q]));
-    const RT d = cabs2(K[c][c]);
-    z[c] = d > 0 ? cscale(cmul(x, cconj(K[c][c])), (RT)1 / d) : cvt<T2>(make_double2(0.0, 0.0));
-  }
-  for (int t = 0; t < k; ++t) Out[(size_t)b * out_ss + (size_t)t * n + i] = z[t];
-}
-
 // ------------------------------------------------------------- reductions
 // out[b] = Re sum_e a_b[e] * h[e] (h shared) ; used for the trace <h, W'>
 template <typename T2>

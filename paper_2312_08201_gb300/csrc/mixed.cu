@@ -41,8 +41,7 @@ struct MixedState {
   DevBuf<float2> R32;
   DevBuf<double> norms, vinv_c;
   DevBuf<int> act, cnt;
-  DevBuf<float2> wlu;
-  DevBuf<int> wpiv;
+  DevBuf<float2> wcinv, wpart;
   WoodState wood;
   // float-float residual operands (capmv_df.cu)
   DevBuf<float4> Lff;  // n x n
@@ -309,10 +308,10 @@ int refine(lyap_seed* sd, int Bc, const double* vinv, const double2* rhs, double
     op.vinv = ms.vinv_c.p;
     if (o.pbar > 0 && sd->tsvd_r > 0) {
       const int r = std::min(o.pbar, sd->tsvd_r);
-      if (ms.wlu.count < (size_t)na * r * r) LY_TRY(ms.wlu.alloc((size_t)Bc * r * r));
-      if (ms.wpiv.count < (size_t)na * r) LY_TRY(ms.wpiv.alloc((size_t)Bc * r));
-      ms.wood.lu = ms.wlu.p;
-      ms.wood.piv = ms.wpiv.p;
+      if (ms.wcinv.count < (size_t)na * r * r) LY_TRY(ms.wcinv.alloc((size_t)Bc * r * r));
+      if (ms.wpart.count < wood_part_count(sd->n, k, na, r)) LY_TRY(ms.wpart.alloc(wood_part_count(sd->n, k, Bc, r)));
+      ms.wood.cinv = ms.wcinv.p;
+      ms.wood.cpart = ms.wpart.p;
       LY_TRY(wood_prepare(sd, r, na, ms.vinv_c.p, adjoint, ms.wood, st));
       op.wood = &ms.wood;
     }
@@ -437,15 +436,7 @@ int SysOp<float2>::apply_c0(int nvec, const float2* In, float2* Out, cudaStream_
 template <>
 int SysOp<float2>::precond(const int* list, const int* count, int B, const float2* In, size_t in_ss, float2* Out,
                            size_t out_ss, cudaStream_t st) const {
-  dim3 grid((sd->n + kry::NT - 1) / kry::NT, B);
-  const int ph = prof_begin(PK_PRECOND, st);
-  kry::k_precond_bj<float2><<<grid, kry::NT, 0, st>>>(sd->n, sd->k, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv, In,
-                                                     in_ss, Out, out_ss);
-  lyap_count_launch();
-  prof_end(ph, st, 0.0, (double)sd->n * sd->k * (2 * sizeof(float2) + sd->k * sizeof(double2)), 0, count);
-  LY_CUDA(cudaGetLastError());
-  if (wood && wood->r > 0) LY_TRY(wood_apply<float2>(sd, *wood, adjoint, vinv, list, count, B, Out, out_ss, st));
-  return LYAP_OK;
+  return prec_apply<float2>(sd, wood, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st);
 }
 
 // ------------------------------------------------------------ testing hooks

@@ -85,77 +85,124 @@ int orth(cusolverDnHandle_t sol, int m, int L, double2* Y, cudaStream_t st) {
   return LYAP_OK;
 }
 
-// Solve the k x k system K_j x = rhs (K_j[t][p] = delta/v_t - Gd[j,p,t],
-// transposed when gT) by Gaussian elimination with partial pivoting.
-__device__ __forceinline__ void solve_block(int n, int k, int j, const double2* __restrict__ Gd, int gT,
-                                            const double* __restrict__ vinv_b, float2 (&x)[8]) {
-  float2 K[8][9];
-  for (int t = 0; t < k; ++t) {
-    for (int p = 0; p < k; ++p) {
-      const size_t gi = gT ? ((size_t)(t * k + p) * n + j) : ((size_t)(p * k + t) * n + j);
-      double2 v = cscale(Gd[gi], -1.0);
-      if (t == p) v.x += vinv_b[t];
-      K[t][p] = make_float2((float)v.x, (float)v.y);
-    }
-    K[t][k] = x[t];
-  }
-  for (int c = 0; c < k; ++c) {
-    int piv = c;
-    float best = cabs2(K[c][c]);
-    for (int r = c + 1; r < k; ++r) {
-      const float a = cabs2(K[r][c]);
+// Solve K_j x = x in place for the k x k block of row j,
+//   K_j[t][p] = delta_tp / v_t - Gd[j, p, t]   (transposed when gT),
+// by Gaussian elimination with partial pivoting. k is a template argument and
+// each elimination step is its own instantiation (Elim<K, C>), so every index
+// is a compile-time constant and the block stays in registers; rows are
+// exchanged by selects.
+template <int K, int C>
+struct Elim {
+  static __device__ __forceinline__ void run(float (&Ar)[K][K], float (&Ai)[K][K], float2 (&x)[K]) {
+    float best = Ar[C][C] * Ar[C][C] + Ai[C][C] * Ai[C][C];
+    int piv = C;
+#pragma unroll
+    for (int r = C + 1; r < K; ++r) {
+      const float a = Ar[r][C] * Ar[r][C] + Ai[r][C] * Ai[r][C];
       if (a > best) {
         best = a;
         piv = r;
       }
     }
-    if (piv != c)
-      for (int q = 0; q <= k; ++q) {
-        const float2 tmp = K[c][q];
-        K[c][q] = K[piv][q];
-        K[piv][q] = tmp;
+#pragma unroll
+    for (int r = C + 1; r < K; ++r) {
+      const bool sw = r == piv;
+#pragma unroll
+      for (int q = C; q < K; ++q) {
+        const float ar = Ar[C][q], ai = Ai[C][q], br = Ar[r][q], bi = Ai[r][q];
+        Ar[C][q] = sw ? br : ar;
+        Ai[C][q] = sw ? bi : ai;
+        Ar[r][q] = sw ? ar : br;
+        Ai[r][q] = sw ? ai : bi;
       }
-    const float2 inv = best > 0.f ? cscale(cconj(K[c][c]), 1.f / best) : make_float2(0.f, 0.f);
-    for (int r = c + 1; r < k; ++r) {
-      const float2 f = cmul(K[r][c], inv);
-      for (int q = c; q <= k; ++q) K[r][q] = csub(K[r][q], cmul(f, K[c][q]));
+      const float2 a = x[C], b = x[r];
+      x[C] = sw ? b : a;
+      x[r] = sw ? a : b;
     }
+    // 1 / pivot = conj(pivot) / |pivot|^2
+    const float2 inv = best > 0.f ? make_float2(Ar[C][C] / best, -Ai[C][C] / best) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = C + 1; r < K; ++r) {
+      const float2 f = cmul(make_float2(Ar[r][C], Ai[r][C]), inv);
+#pragma unroll
+      for (int q = C + 1; q < K; ++q) {
+        const float2 v = csub(make_float2(Ar[r][q], Ai[r][q]), cmul(f, make_float2(Ar[C][q], Ai[C][q])));
+        Ar[r][q] = v.x;
+        Ai[r][q] = v.y;
+      }
+      x[r] = csub(x[r], cmul(f, x[C]));
+    }
+    Elim<K, C + 1>::run(Ar, Ai, x);
   }
-  for (int c = k - 1; c >= 0; --c) {
-    float2 s = K[c][k];
-    for (int q = c + 1; q < k; ++q) s = csub(s, cmul(K[c][q], x[q]));
-    const float d = cabs2(K[c][c]);
-    x[c] = d > 0.f ? cscale(cmul(s, cconj(K[c][c])), 1.f / d) : make_float2(0.f, 0.f);
+};
+template <int K>
+struct Elim<K, K> {
+  static __device__ __forceinline__ void run(float (&)[K][K], float (&)[K][K], float2 (&)[K]) {}
+};
+
+template <int K>
+__device__ __forceinline__ void bsolve(int n, int j, const double2* __restrict__ Gd, int gT, const double (&vb)[K],
+                                       float2 (&x)[K]) {
+  float Ar[K][K], Ai[K][K];
+#pragma unroll
+  for (int t = 0; t < K; ++t)
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+      const size_t gi = gT ? ((size_t)(t * K + p) * n + j) : ((size_t)(p * K + t) * n + j);
+      const double2 g = Gd[gi];
+      Ar[t][p] = (float)((t == p ? vb[t] : 0.0) - g.x);
+      Ai[t][p] = (float)(-g.y);
+    }
+  Elim<K, 0>::run(Ar, Ai, x);
+#pragma unroll
+  for (int c = K - 1; c >= 0; --c) {
+    float2 s = x[c];
+#pragma unroll
+    for (int q = c + 1; q < K; ++q) s = csub(s, cmul(make_float2(Ar[c][q], Ai[c][q]), x[q]));
+    const float d = Ar[c][c] * Ar[c][c] + Ai[c][c] * Ai[c][c];
+    x[c] = d > 0.f ? make_float2((s.x * Ar[c][c] + s.y * Ai[c][c]) / d, (s.y * Ar[c][c] - s.x * Ai[c][c]) / d)
+                   : make_float2(0.f, 0.f);
   }
 }
 
-// Cap_b = I - Ml^T K_b^{-1} Nl (r x r), then its LU with partial pivoting
-// (one CTA per system; warp 0 factors).
-__global__ void __launch_bounds__(WT) k_cap_build(int n, int k, int r, const double2* __restrict__ Gd,
+template <int K>
+__device__ __forceinline__ void load_vb(const double* __restrict__ vinv, int b, double (&vb)[K]) {
+#pragma unroll
+  for (int t = 0; t < K; ++t) vb[t] = vinv[(size_t)b * K + t];
+}
+
+// Cap_b^{-1} with Cap_b = I - Ml^T K_b^{-1} Nl (r x r, column-major), one CTA
+// per system: the product accumulates over chunks of J rows, then
+// Gauss-Jordan elimination with partial pivoting inverts it in shared memory.
+template <int K>
+__global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const double2* __restrict__ Gd,
                                                   const double* __restrict__ vinv, const float2* __restrict__ Nl,
-                                                  const float2* __restrict__ Ml, int ldr, float2* __restrict__ lu,
-                                                  int* __restrict__ piv) {
-  extern __shared__ float2 sw[];  // [J x k x r] K^{-1} Nl rows, [J x k x r] Ml rows; then r x r
+                                                  const float2* __restrict__ Ml, int ldr, float2* __restrict__ cinv) {
+  extern __shared__ float2 sw[];  // [J x K x r] K^{-1} Nl rows, [J x K x r] Ml rows; then C, Inv (r x r each)
+  __shared__ float2 fcol[RMAX];
+  __shared__ int piv_s;
   constexpr int J = 8;
-  float2* sm = sw + (size_t)J * k * r;
+  float2* sm = sw + (size_t)J * K * r;
   const int b = blockIdx.x;
-  const double* vb = vinv + (size_t)b * k;
+  double vb[K];
+  load_vb<K>(vinv, b, vb);
   const int nout = r * r;
   float2 acc[16];
 #pragma unroll
   for (int u = 0; u < 16; ++u) acc[u] = make_float2(0.f, 0.f);
   for (int j0 = 0; j0 < n; j0 += J) {
-    // W_j = K_j^{-1} Nl[(., j), l]  for j in the chunk, all l
     for (int e = threadIdx.x; e < J * r; e += WT) {
       const int jj = e / r, l = e % r, j = j0 + jj;
-      float2 x[8];
+      float2 x[K];
       if (j < n) {
-        for (int t = 0; t < k; ++t) x[t] = Nl[(size_t)t * n + j + (size_t)l * ldr];
-        solve_block(n, k, j, Gd, 0, vb, x);
+#pragma unroll
+        for (int t = 0; t < K; ++t) x[t] = Nl[(size_t)t * n + j + (size_t)l * ldr];
+        bsolve<K>(n, j, Gd, 0, vb, x);
       }
-      for (int t = 0; t < k; ++t) {
-        sw[((size_t)jj * k + t) * r + l] = j < n ? x[t] : make_float2(0.f, 0.f);
-        sm[((size_t)jj * k + t) * r + l] = j < n ? Ml[(size_t)t * n + j + (size_t)l * ldr] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < K; ++t) {
+        sw[((size_t)jj * K + t) * r + l] = j < n ? x[t] : make_float2(0.f, 0.f);
+        sm[((size_t)jj * K + t) * r + l] = j < n ? Ml[(size_t)t * n + j + (size_t)l * ldr] : make_float2(0.f, 0.f);
       }
     }
     __syncthreads();
@@ -165,157 +212,257 @@ __global__ void __launch_bounds__(WT) k_cap_build(int n, int k, int r, const dou
       if (o < nout) {
         const int l = o % r, l2 = o / r;
         float2 a = acc[u];
-        for (int q = 0; q < J * k; ++q) a = cfma(sm[(size_t)q * r + l], sw[(size_t)q * r + l2], a);
+        for (int q = 0; q < J * K; ++q) a = cfma(sm[(size_t)q * r + l], sw[(size_t)q * r + l2], a);
         acc[u] = a;
       }
     }
     __syncthreads();
   }
-  float2* C = sw;  // r x r, column-major
+  float2* C = sw;            // r x r, column-major: C[i + q r]
+  float2* Inv = sw + nout;   // r x r
 #pragma unroll
   for (int u = 0; u < 16; ++u) {
     const int o = threadIdx.x + u * WT;
     if (o < nout) {
       const int l = o % r, l2 = o / r;
       C[o] = make_float2((l == l2 ? 1.f : 0.f) - acc[u].x, -acc[u].y);
+      Inv[o] = make_float2(l == l2 ? 1.f : 0.f, 0.f);
     }
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    int* pv = piv + (size_t)b * r;
-    for (int c = 0; c < r; ++c) {
+  for (int c = 0; c < r; ++c) {
+    if (threadIdx.x < 32) {
+      float best = -1.f;
       int p = c;
-      float best = cabs2(C[c + c * r]);
-      for (int i = c + 1; i < r; ++i) {
+      for (int i = c + threadIdx.x; i < r; i += 32) {
         const float a = cabs2(C[i + c * r]);
         if (a > best) {
           best = a;
           p = i;
         }
       }
-      __syncwarp();
-      if (p != c)
-        for (int q = lane; q < r; q += 32) {
-          const float2 tmp = C[c + q * r];
-          C[c + q * r] = C[p + q * r];
-          C[p + q * r] = tmp;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int op = __shfl_xor_sync(0xffffffffu, p, off);
+        if (ob > best || (ob == best && op < p)) {
+          best = ob;
+          p = op;
         }
-      if (lane == 0) pv[c] = p;
-      __syncwarp();
-      const float2 d = C[c + c * r];
-      const float dd = cabs2(d);
-      const float2 inv = dd > 0.f ? cscale(cconj(d), 1.f / dd) : make_float2(0.f, 0.f);
-      for (int i = c + 1 + lane; i < r; i += 32) C[i + c * r] = cmul(C[i + c * r], inv);
-      __syncwarp();
-      for (int q = c + 1 + lane; q < r; q += 32) {
-        const float2 cq = C[c + q * r];
-        for (int i = c + 1; i < r; ++i) C[i + q * r] = csub(C[i + q * r], cmul(C[i + c * r], cq));
       }
-      __syncwarp();
+      if (threadIdx.x == 0) piv_s = p;
     }
+    __syncthreads();
+    const int p = piv_s;
+    if (p != c)
+      for (int q = threadIdx.x; q < 2 * r; q += WT) {
+        float2* M = q < r ? C : Inv;
+        const int qq = q < r ? q : q - r;
+        const float2 t = M[c + qq * r];
+        M[c + qq * r] = M[p + qq * r];
+        M[p + qq * r] = t;
+      }
+    __syncthreads();
+    const float2 d = C[c + c * r];
+    const float dd = cabs2(d);
+    const float2 dinv = dd > 0.f ? cscale(cconj(d), 1.f / dd) : make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < r; i += WT) fcol[i] = i == c ? make_float2(0.f, 0.f) : C[i + c * r];
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * r; q += WT) {
+      float2* M = q < r ? C : Inv;
+      const int qq = q < r ? q : q - r;
+      M[c + qq * r] = cmul(M[c + qq * r], dinv);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * nout; e += WT) {
+      float2* M = e < nout ? C : Inv;
+      const int ee = e < nout ? e : e - nout;
+      const int i = ee % r, q = ee / r;
+      if (i != c) M[i + q * r] = csub(M[i + q * r], cmul(fcol[i], M[c + q * r]));
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int o = threadIdx.x; o < nout; o += WT) lu[(size_t)b * nout + o] = C[o];
+  for (int o = threadIdx.x; o < nout; o += WT) cinv[(size_t)b * nout + o] = Inv[o];
 }
 
-// z_b += K^{-1} A Cap^{-1} B^T z_b  (primal: A = Nl, B = Ml; adjoint:
-// A = Ml, B = Nl, K and Cap transposed).
-template <typename T2>
-__global__ void __launch_bounds__(WT) k_wood_apply(int n, int k, int r, const int* __restrict__ list,
-                                                   const int* __restrict__ count, const double2* __restrict__ Gd,
-                                                   int adjoint, const double* __restrict__ vinv,
-                                                   const float2* __restrict__ Aop, const float2* __restrict__ Bop,
-                                                   int ldr, const float2* __restrict__ lu, const int* __restrict__ piv,
-                                                   T2* __restrict__ Z, size_t z_ss) {
-  __shared__ float red[32 * 32];
-  __shared__ float2 c[RMAX], y[RMAX];
-  const int slot = blockIdx.x;
-  if (slot >= *count) return;
-  const int b = list[slot];
-  const int N = n * k;
-  T2* z = Z + (size_t)b * z_ss;
-  for (int l0 = 0; l0 < r; l0 += 16) {
-    float acc[32];
+// Preconditioner apply for the listed systems:
+//   z = K^{-1} r, then (rank r > 0) z += K^{-1} A Cap^{-1} B^T z
+// with A = Nl, B = Ml (primal) or A = Ml, B = Nl, K^T and Cap^{-T}
+// (adjoint). Two kernels over tiles of PRT rows x PST systems (a few hundred
+// CTAs for a full batch; every row of A and B read from L2 serves PST
+// systems):
+//   k_prec_a: z = K^{-1} r for the tile, and the tile's partial sums of
+//             c = B^T z, written per row tile (no atomics: deterministic);
+//   k_prec_b: c = sum of the partials, y = Cap^{-1} c (recomputed by every
+//             row tile of the system tile), z += K^{-1} (A y) for the tile.
+// FP32 arithmetic; input and output in the Krylov precision.
+constexpr int PST = 16;
+template <int K>
+struct PrecTile {
+  static constexpr int RT = K <= 4 ? 64 : 32;
+};
+
+template <typename T2, int K>
+__global__ void __launch_bounds__(WT) k_prec_a(int n, const int* __restrict__ list, const int* __restrict__ count,
+                                               const double2* __restrict__ Gd, int adj,
+                                               const double* __restrict__ vinv, const T2* __restrict__ In,
+                                               size_t in_ss, T2* __restrict__ Out, size_t out_ss, int r,
+                                               const float2* __restrict__ Bop, int ldr, float2* __restrict__ Cp,
+                                               int nslots) {
+  constexpr int RT = PrecTile<K>::RT;
+  __shared__ float2 zs[PST][K][RT + 1];
+  const int nact = *count;
+  const int s0 = blockIdx.y * PST;
+  if (s0 >= nact) return;
+  const int j0 = blockIdx.x * RT;
+  for (int e = threadIdx.x; e < RT * PST; e += WT) {
+    const int row = e % RT, sl = e / RT;
+    const int j = j0 + row;
+    float2 x[K];
+    if (s0 + sl < nact && j < n) {
+      const int b = list[s0 + sl];
+      double vb[K];
+      load_vb<K>(vinv, b, vb);
+      const T2* in = In + (size_t)b * in_ss;
 #pragma unroll
-    for (int u = 0; u < 32; ++u) acc[u] = 0.f;
-    for (int e = threadIdx.x; e < N; e += WT) {
-      const double2 zd = to_d2(z[e]);
-      const float2 ze = make_float2((float)zd.x, (float)zd.y);
+      for (int t = 0; t < K; ++t) {
+        const double2 v = to_d2(in[(size_t)t * n + j]);
+        x[t] = make_float2((float)v.x, (float)v.y);
+      }
+      bsolve<K>(n, j, Gd, adj, vb, x);
+      T2* out = Out + (size_t)b * out_ss;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        if (l0 + u < r) {
-          const float2 m = Bop[e + (size_t)(l0 + u) * ldr];
-          acc[2 * u] += m.x * ze.x - m.y * ze.y;
-          acc[2 * u + 1] += m.x * ze.y + m.y * ze.x;
-        }
-      }
-    }
-    kry::block_sum<32, float>(acc, red);
-    if (threadIdx.x < 16 && l0 + threadIdx.x < r) c[l0 + threadIdx.x] = make_float2(acc[2 * threadIdx.x], acc[2 * threadIdx.x + 1]);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    // y = Cap^{-1} c (P Cap = L U) or y = Cap^{-T} c (Cap^T = U^T L^T P)
-    const float2* C = lu + (size_t)b * r * r;
-    const int* pv = piv + (size_t)b * r;
-    if (!adjoint) {
-      for (int i = 0; i < r; ++i) y[i] = c[i];
-      for (int i = 0; i < r; ++i) {
-        const int p = pv[i];
-        if (p != i) {
-          const float2 t = y[i];
-          y[i] = y[p];
-          y[p] = t;
-        }
-      }
-      for (int i = 0; i < r; ++i)
-        for (int q = 0; q < i; ++q) y[i] = csub(y[i], cmul(C[i + q * r], y[q]));
-      for (int i = r - 1; i >= 0; --i) {
-        float2 s = y[i];
-        for (int q = i + 1; q < r; ++q) s = csub(s, cmul(C[i + q * r], y[q]));
-        const float2 d = C[i + i * r];
-        const float dd = cabs2(d);
-        y[i] = dd > 0.f ? cscale(cmul(s, cconj(d)), 1.f / dd) : make_float2(0.f, 0.f);
-      }
+      for (int t = 0; t < K; ++t) out[(size_t)t * n + j] = from_d2<T2>(make_double2(x[t].x, x[t].y));
     } else {
-      // U^T w = c (forward), L^T y' = w (backward, unit), y = P^T y'
-      for (int i = 0; i < r; ++i) {
-        float2 s = c[i];
-        for (int q = 0; q < i; ++q) s = csub(s, cmul(C[q + i * r], y[q]));
-        const float2 d = C[i + i * r];
-        const float dd = cabs2(d);
-        y[i] = dd > 0.f ? cscale(cmul(s, cconj(d)), 1.f / dd) : make_float2(0.f, 0.f);
-      }
-      for (int i = r - 1; i >= 0; --i)
-        for (int q = i + 1; q < r; ++q) y[i] = csub(y[i], cmul(C[q + i * r], y[q]));
-      for (int i = r - 1; i >= 0; --i) {
-        const int p = pv[i];
-        if (p != i) {
-          const float2 t = y[i];
-          y[i] = y[p];
-          y[p] = t;
-        }
-      }
+#pragma unroll
+      for (int t = 0; t < K; ++t) x[t] = make_float2(0.f, 0.f);
+    }
+    if (r > 0) {
+#pragma unroll
+      for (int t = 0; t < K; ++t) zs[sl][t][row] = x[t];
     }
   }
+  if (r <= 0) return;
   __syncthreads();
-  const double* vb = vinv + (size_t)b * k;
-  for (int j = threadIdx.x; j < n; j += WT) {
-    float2 x[8];
-    for (int t = 0; t < k; ++t) {
-      float2 s = make_float2(0.f, 0.f);
-      for (int l = 0; l < r; ++l) s = cfma(Aop[(size_t)t * n + j + (size_t)l * ldr], y[l], s);
-      x[t] = s;
+  const int rows = min(RT, n - j0);
+  for (int e = threadIdx.x; e < r * PST; e += WT) {
+    const int sl = e % PST, l = e / PST;
+    if (s0 + sl >= nact) continue;
+    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+      const float2* bcol = Bop + (size_t)t * n + j0 + (size_t)l * ldr;
+      int q = 0;
+#pragma unroll 4
+      for (; q + 1 < rows; q += 2) {
+        a0 = cfma(bcol[q], zs[sl][t][q], a0);
+        a1 = cfma(bcol[q + 1], zs[sl][t][q + 1], a1);
+      }
+      if (q < rows) a0 = cfma(bcol[q], zs[sl][t][q], a0);
     }
-    solve_block(n, k, j, Gd, adjoint, vb, x);
-    for (int t = 0; t < k; ++t) {
-      const size_t e = (size_t)t * n + j;
-      const double2 zd = to_d2(z[e]);
-      z[e] = from_d2<T2>(make_double2(zd.x + x[t].x, zd.y + x[t].y));
+    Cp[((size_t)blockIdx.x * nslots + s0 + sl) * r + l] = cadd(a0, a1);
+  }
+}
+
+template <typename T2, int K>
+__global__ void __launch_bounds__(WT) k_prec_b(int n, const int* __restrict__ list, const int* __restrict__ count,
+                                               const double2* __restrict__ Gd, int adj,
+                                               const double* __restrict__ vinv, T2* __restrict__ Out, size_t out_ss,
+                                               int r, const float2* __restrict__ Aop, int ldr,
+                                               const float2* __restrict__ cinv, const float2* __restrict__ Cp,
+                                               int nslots, int ntx) {
+  constexpr int RT = PrecTile<K>::RT;
+  __shared__ float2 cs[PST][RMAX + 1];
+  __shared__ float2 ys[PST][RMAX + 1];
+  const int nact = *count;
+  const int s0 = blockIdx.y * PST;
+  if (s0 >= nact) return;
+  const int j0 = blockIdx.x * RT;
+  for (int e = threadIdx.x; e < r * PST; e += WT) {
+    const int sl = e % PST, l = e / PST;
+    float2 c = make_float2(0.f, 0.f);
+    if (s0 + sl < nact)
+      for (int tx = 0; tx < ntx; ++tx) c = cadd(c, Cp[((size_t)tx * nslots + s0 + sl) * r + l]);
+    cs[sl][l] = c;
+  }
+  __syncthreads();
+  // y = Cap^{-1} c, or Cap^{-T} c for the adjoint
+  for (int e = threadIdx.x; e < r * PST; e += WT) {
+    const int sl = e % PST, l = e / PST;
+    float2 y = make_float2(0.f, 0.f);
+    if (s0 + sl < nact) {
+      const float2* Ci = cinv + (size_t)list[s0 + sl] * r * r;
+      for (int q = 0; q < r; ++q) y = cfma(adj ? Ci[q + (size_t)l * r] : Ci[l + (size_t)q * r], cs[sl][q], y);
+    }
+    ys[sl][l] = y;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RT * PST; e += WT) {
+    const int row = e % RT, sl = e / RT;
+    const int j = j0 + row;
+    if (s0 + sl >= nact || j >= n) continue;
+    const int b = list[s0 + sl];
+    float2 x[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+      const float2* arow = Aop + (size_t)t * n + j;
+      float2 s0v = make_float2(0.f, 0.f), s1v = make_float2(0.f, 0.f);
+      int l = 0;
+      for (; l + 1 < r; l += 2) {
+        s0v = cfma(arow[(size_t)l * ldr], ys[sl][l], s0v);
+        s1v = cfma(arow[(size_t)(l + 1) * ldr], ys[sl][l + 1], s1v);
+      }
+      if (l < r) s0v = cfma(arow[(size_t)l * ldr], ys[sl][l], s0v);
+      x[t] = cadd(s0v, s1v);
+    }
+    double vb[K];
+    load_vb<K>(vinv, b, vb);
+    bsolve<K>(n, j, Gd, adj, vb, x);
+    T2* out = Out + (size_t)b * out_ss;
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+      const size_t e2 = (size_t)t * n + j;
+      const double2 zd = to_d2(out[e2]);
+      out[e2] = from_d2<T2>(make_double2(zd.x + x[t].x, zd.y + x[t].y));
     }
   }
 }
+
+template <int K>
+size_t cap_smem(int r) {
+  return sizeof(float2) * std::max<size_t>((size_t)2 * 8 * K * r, (size_t)2 * r * r);
+}
+
+template <int K>
+int launch_cap_build(lyap_seed* sd, int r, int B, const double* vinv, const WoodState& ws, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t attr_rc = cudaSuccess;
+  std::call_once(once, [] {
+    attr_rc = cudaFuncSetAttribute(k_cap_build<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)cap_smem<K>(RMAX));
+  });
+  LY_CUDA(attr_rc);
+  k_cap_build<K><<<B, WT, cap_smem<K>(r), st>>>(sd->n, r, sd->Gd.p, vinv, ws.Nl, ws.Ml, ws.ldr, ws.cinv);
+  return LYAP_OK;
+}
+
+template <typename T2, int K>
+void launch_prec(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* vinv, const int* list,
+                 const int* count, int B, const T2* In, size_t in_ss, T2* Out, size_t out_ss, cudaStream_t st) {
+  constexpr int RT = PrecTile<K>::RT;
+  const int n = sd->n;
+  const int r = ws ? ws->r : 0;
+  const int ntx = (n + RT - 1) / RT;
+  const dim3 grid(ntx, (B + PST - 1) / PST);
+  const float2* A = ws ? (adjoint ? ws->Ml : ws->Nl) : nullptr;
+  const float2* Bm = ws ? (adjoint ? ws->Nl : ws->Ml) : nullptr;
+  k_prec_a<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv, In, in_ss, Out, out_ss, r, Bm,
+                                       ws ? ws->ldr : 0, ws ? ws->cpart : nullptr, B);
+  if (r > 0)
+    k_prec_b<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv, Out, out_ss, r, A, ws->ldr,
+                                         ws->cinv, ws->cpart, B, ntx);
+}
+
 
 }  // namespace
 
@@ -398,6 +545,11 @@ int lyap_tsvd_prepare(lyap_seed* sd, int r, cudaStream_t st) {
   return LYAP_OK;
 }
 
+size_t wood_part_count(int n, int k, int B, int r) {
+  const int RT = k <= 4 ? PrecTile<1>::RT : PrecTile<8>::RT;
+  return (size_t)((n + RT - 1) / RT) * (size_t)B * (size_t)std::max(r, 0);
+}
+
 int wood_prepare(lyap_seed* sd, int r, int B, const double* vinv, bool /*adjoint*/, WoodState& ws, cudaStream_t st) {
   r = std::min(r, sd->tsvd_r);
   ws.r = r;
@@ -406,36 +558,52 @@ int wood_prepare(lyap_seed* sd, int r, int B, const double* vinv, bool /*adjoint
   ws.Ml = sd->tsvd_M.p;
   ws.ldr = sd->n * sd->k;
   if (r <= 0 || B <= 0) return LYAP_OK;
-  const size_t smem = std::max(sizeof(float2) * 2 * 8 * sd->k * r, sizeof(float2) * r * r);
-  static std::once_flag once;
-  static cudaError_t attr_rc = cudaSuccess;
-  std::call_once(once, [] {
-    attr_rc = cudaFuncSetAttribute(k_cap_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(float2) * 2 * 8 * 8 * RMAX));
-  });
-  LY_CUDA(attr_rc);
-  const int ph = prof_begin(PK_PRECOND, st);
-  k_cap_build<<<B, WT, smem, st>>>(sd->n, sd->k, r, sd->Gd.p, vinv, ws.Nl, ws.Ml, ws.ldr, ws.lu, ws.piv);
+  const int ph = prof_begin(PK_CAPBUILD, st);
+  int rc = LYAP_EINVAL;
+  switch (sd->k) {
+    case 1: rc = launch_cap_build<1>(sd, r, B, vinv, ws, st); break;
+    case 2: rc = launch_cap_build<2>(sd, r, B, vinv, ws, st); break;
+    case 3: rc = launch_cap_build<3>(sd, r, B, vinv, ws, st); break;
+    case 4: rc = launch_cap_build<4>(sd, r, B, vinv, ws, st); break;
+    case 5: rc = launch_cap_build<5>(sd, r, B, vinv, ws, st); break;
+    case 6: rc = launch_cap_build<6>(sd, r, B, vinv, ws, st); break;
+    case 7: rc = launch_cap_build<7>(sd, r, B, vinv, ws, st); break;
+    case 8: rc = launch_cap_build<8>(sd, r, B, vinv, ws, st); break;
+  }
+  if (rc != LYAP_OK) return rc;
   lyap_count_launch();
-  prof_end(ph, st, 8.0 * sd->n * sd->k * r * r, 0.0, B, nullptr);
+  prof_end(ph, st, 8.0 * sd->n * sd->k * r * r + 16.0 * r * r * r, 0.0, B, nullptr);
   LY_CUDA(cudaGetLastError());
   return LYAP_OK;
 }
 
 template <typename T2>
-int wood_apply(lyap_seed* sd, const WoodState& ws, bool adjoint, const double* vinv, const int* list,
-               const int* count, int B, T2* Z, size_t z_ss, cudaStream_t st) {
-  if (ws.r <= 0) return LYAP_OK;
-  const float2* A = adjoint ? ws.Ml : ws.Nl;
-  const float2* Bm = adjoint ? ws.Nl : ws.Ml;
-  k_wood_apply<T2><<<B, WT, 0, st>>>(sd->n, sd->k, ws.r, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv, A, Bm, ws.ldr,
-                                     ws.lu, ws.piv, Z, z_ss);
-  lyap_count_launch();
+int prec_apply(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* vinv, const int* list,
+               const int* count, int B, const T2* In, size_t in_ss, T2* Out, size_t out_ss, cudaStream_t st) {
+  if (ws && ws->r <= 0) ws = nullptr;
+  const int ph = prof_begin(PK_PRECOND, st);
+  switch (sd->k) {
+    case 1: launch_prec<T2, 1>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 2: launch_prec<T2, 2>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 3: launch_prec<T2, 3>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 4: launch_prec<T2, 4>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 5: launch_prec<T2, 5>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 6: launch_prec<T2, 6>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 7: launch_prec<T2, 7>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 8: launch_prec<T2, 8>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    default: return LYAP_EINVAL;
+  }
+  lyap_count_launch(ws ? 2 : 1);
+  // algorithmic bytes per system: read r, write z, read+write z again when r > 0
+  const int r = ws ? ws->r : 0;
+  const double N = (double)sd->n * sd->k;
+  prof_end(ph, st, 8.0 * N * sd->k + (r > 0 ? 16.0 * N * r + 8.0 * N * sd->k + 8.0 * r * r : 0.0),
+           N * sizeof(T2) * (r > 0 ? 4.0 : 2.0), 0, count);
   LY_CUDA(cudaGetLastError());
   return LYAP_OK;
 }
 
-template int wood_apply<double2>(lyap_seed*, const WoodState&, bool, const double*, const int*, const int*, int,
-                                 double2*, size_t, cudaStream_t);
-template int wood_apply<float2>(lyap_seed*, const WoodState&, bool, const double*, const int*, const int*, int,
-                                float2*, size_t, cudaStream_t);
+template int prec_apply<double2>(lyap_seed*, const WoodState*, bool, const double*, const int*, const int*, int,
+                                 const double2*, size_t, double2*, size_t, cudaStream_t);
+template int prec_apply<float2>(lyap_seed*, const WoodState*, bool, const double*, const int*, const int*, int,
+                                const float2*, size_t, float2*, size_t, cudaStream_t);

@@ -20,10 +20,10 @@
 struct lyap_seed;
 
 struct WoodState {
-  int r = 0;           // rank in use (0: block-Jacobi only)
-  int B = 0;           // systems with a factored Cap
-  float2* lu = nullptr;  // B x r x r (LU of Cap, column-major, unit lower)
-  int* piv = nullptr;    // B x r
+  int r = 0;             // rank in use (0: block-Jacobi only)
+  int B = 0;             // systems with an inverted Cap
+  float2* cinv = nullptr;  // B x r x r: Cap^{-1}, column-major
+  float2* cpart = nullptr; // wood_part_count(n, k, B, r) entries: partial sums of the apply
   const float2* Nl = nullptr;  // nk x rmax (seed)
   const float2* Ml = nullptr;
   int ldr = 0;  // leading dimension (rows) of Nl/Ml = nk
@@ -33,11 +33,16 @@ struct WoodState {
 // power iterations). Builds seed-resident Nl, Ml (FP32) once per rank.
 int lyap_tsvd_prepare(lyap_seed* sd, int r, cudaStream_t st);
 
-// Per chunk: factor Cap(v_b) for systems b < B (vinv: B x k). ws must stay
-// alive while the chunk runs.
+// Entries of WoodState::cpart that a batch of B systems needs.
+size_t wood_part_count(int n, int k, int B, int r);
+
+// Per chunk: invert Cap(v_b) for systems b < B (vinv: B x k) into ws.cinv
+// (caller-owned, B r^2 entries). ws must stay alive while the chunk runs.
 int wood_prepare(lyap_seed* sd, int r, int B, const double* vinv, bool adjoint, WoodState& ws, cudaStream_t st);
 
-// z (already K^{-1} r, in place) += K^{-1} Nl Cap^{-1} Ml^T z  for listed systems.
+// Out_b = P(v_b)^{-1} In_b for the listed systems: block-Jacobi K^{-1}, plus
+// the Woodbury term K^{-1} Nl Cap^{-1} Ml^T K^{-1} when ws has rank > 0
+// (ws == nullptr: block-Jacobi only). Adjoint: P^T.
 template <typename T2>
-int wood_apply(lyap_seed* sd, const WoodState& ws, bool adjoint, const double* vinv, const int* list,
-               const int* count, int B, T2* Z, size_t z_ss, cudaStream_t st);
+int prec_apply(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* vinv, const int* list,
+               const int* count, int B, const T2* In, size_t in_ss, T2* Out, size_t out_ss, cudaStream_t st);

@@ -12,7 +12,7 @@ enum ProfKernel {
   PK_CAPMV64 = 0,   // FP64 capacitance matvec (Cauchy-panel GEMM)
   PK_TCGEMM = 1,    // tcgen05 Cauchy-panel GEMM (mixed path)
   PK_ORTHO = 2,     // CGS2 Arnoldi orthogonalisation
-  PK_PRECOND = 3,   // block-Jacobi preconditioner
+  PK_PRECOND = 3,   // preconditioner apply (block-Jacobi + Woodbury term)
   PK_GRAM = 4,      // batched Gram matrices (recycle update)
   PK_TSMM = 5,      // batched tall-skinny products
   PK_RITZ = 6,      // harmonic-Ritz small dense problems
@@ -23,7 +23,8 @@ enum ProfKernel {
   PK_RECSTART = 11, // recycle start (AU, CholQR2, projection)
   PK_CAPMV_FF = 12, // float-float capacitance matvec (mixed-path residual);
                     // its "flops" are FP32 lane instructions
-  PK_COUNT = 13
+  PK_CAPBUILD = 13, // Woodbury capacitance Cap(v)^{-1} per system
+  PK_COUNT = 14
 };
 
 void lyap_count_launch(int n = 1);

@@ -506,10 +506,5 @@ int SysOp<double2>::apply_c0(int nvec, const double2* In, double2* Out, cudaStre
 template <>
 int SysOp<double2>::precond(const int* list, const int* count, int B, const double2* In, size_t in_ss,
                             double2* Out, size_t out_ss, cudaStream_t st) const {
-  dim3 grid((sd->n + kry::NT - 1) / kry::NT, B);
-  kry::k_precond_bj<double2><<<grid, kry::NT, 0, st>>>(sd->n, sd->k, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv,
-                                                      In, in_ss, Out, out_ss); lyap_count_launch();
-  LY_CUDA(cudaGetLastError());
-  if (wood && wood->r > 0) LY_TRY(wood_apply<double2>(sd, *wood, adjoint, vinv, list, count, B, Out, out_ss, st));
-  return LYAP_OK;
+  return prec_apply<double2>(sd, wood, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st);
 }
