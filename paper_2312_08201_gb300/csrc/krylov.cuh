@@ -74,17 +74,41 @@ __global__ void k_compact(const int* __restrict__ in_list, const int* __restrict
 __global__ void k_iota(int B, int* list, int* count);
 
 // ----------------------------------------------------------- CGS2 Arnoldi
+// Sum 32 per-thread values over a warp: after the call lane l holds, in
+// v[0], the warp total of value l (a butterfly that halves the values per
+// lane at every step: 31 shuffles instead of 32 x 5).
+template <typename R>
+__device__ __forceinline__ void warp_reduce_scatter32(R (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const R send = upper ? v[i] : v[i + s];
+      const R keep = upper ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+}
+
+constexpr int OT = 512;  // threads per system in the orthogonalisation
+
 // w = V_b[j+1] is orthogonalised against the recycled C_b (s_cur vectors)
-// and V_b[0..j] with two classical Gram-Schmidt passes; coefficients go to
-// Bk (C part) and H (V part) in FP64, then w is normalised.
+// and V_b[0..j] with two classical Gram-Schmidt passes, then normalised; the
+// summed coefficients of both passes go to Bk (C part) and H (V part) in
+// FP64. The first pass's update and the second pass's inner products share
+// one sweep over the basis, and the second update computes ||w||: the
+// basis is read three times.
 template <typename T2>
-__global__ void __launch_bounds__(NT) k_ortho(int N, int j, int m, int s_cur, const int* __restrict__ list,
+__global__ void __launch_bounds__(OT, sizeof(T2) == 8 ? 2 : 1) k_ortho(int N, int j, int m, int s_cur, const int* __restrict__ list,
                                              const int* __restrict__ count, T2* __restrict__ V,
                                              const T2* __restrict__ C, size_t c_ss, double2* __restrict__ H,
                                              double2* __restrict__ Bk, int smax) {
   using R = typename RealOf<T2>::T;
-  __shared__ R red[32 * 32];
-  __shared__ T2 coef[128];
+  constexpr int NW = OT / 32;
+  __shared__ R red[NW][32];
+  __shared__ T2 coef[2][64];
   const int slot = blockIdx.x;
   if (slot >= *count) return;
   const int b = list[slot];
@@ -92,58 +116,99 @@ __global__ void __launch_bounds__(NT) k_ortho(int N, int j, int m, int s_cur, co
   T2* w = Vb + (size_t)(j + 1) * N;
   const T2* Cb = C + (size_t)b * c_ss;
   const int nb = s_cur + j + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   auto basis = [&](int q) -> const T2* { return q < s_cur ? Cb + (size_t)q * N : Vb + (size_t)(q - s_cur) * N; };
+  // block sum of 16 complex inner products held as 32 reals per thread
+  auto reduce16 = [&](R (&acc)[32], T2* out, int q0) {
+    warp_reduce_scatter32<R>(acc);
+    red[warp][lane] = acc[0];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      R s = R(0);
+#pragma unroll
+      for (int w2 = 0; w2 < NW; ++w2) s += red[w2][threadIdx.x];
+      const R im = __shfl_xor_sync(0xffffffffu, s, 1);
+      const int q = q0 + (threadIdx.x >> 1);
+      if ((threadIdx.x & 1) == 0 && q < nb) {
+        T2 c;
+        c.x = s;
+        c.y = im;
+        out[q] = c;
+      }
+    }
+    __syncthreads();
+  };
+  // w -= sum_q basis_q[e] * cf[q], with the basis loads issued eight at a time
+  auto update = [&](int e, T2 we, const T2* cf) -> T2 {
+    for (int p0 = 0; p0 < nb; p0 += 8) {
+      T2 qv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) qv[u] = p0 + u < nb ? basis(p0 + u)[e] : cvt<T2>(make_double2(0.0, 0.0));
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (p0 + u < nb) we = csub(we, cmul(qv[u], cf[p0 + u]));
+    }
+    return we;
+  };
+  auto accumulate = [&](R (&acc)[32], int e, int q0, T2 we) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      if (q0 + u < nb) {
+        const T2 qe = basis(q0 + u)[e];
+        acc[2 * u] += qe.x * we.x + qe.y * we.y;
+        acc[2 * u + 1] += qe.x * we.y - qe.y * we.x;
+      }
+    }
+  };
+  // pass 1: inner products
+  for (int q0 = 0; q0 < nb; q0 += 16) {
+    R acc[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) acc[u] = R(0);
+    for (int e = threadIdx.x; e < N; e += OT) accumulate(acc, e, q0, w[e]);
+    reduce16(acc, coef[0], q0);
+  }
+  // pass 1 update, fused with the pass 2 inner products
+  for (int q0 = 0; q0 < nb; q0 += 16) {
+    R acc[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) acc[u] = R(0);
+    for (int e = threadIdx.x; e < N; e += OT) {
+      T2 we = w[e];
+      if (q0 == 0) {
+        we = update(e, we, coef[0]);
+        w[e] = we;
+      }
+      accumulate(acc, e, q0, we);
+    }
+    reduce16(acc, coef[1], q0);
+  }
+  // pass 2 update and the norm
+  R nr = R(0);
+  for (int e = threadIdx.x; e < N; e += OT) {
+    const T2 we = update(e, w[e], coef[1]);
+    w[e] = we;
+    nr += cabs2(we);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(0xffffffffu, nr, o);
+  if (lane == 0) red[warp][0] = nr;
+  __syncthreads();
+  R tot = R(0);
+#pragma unroll
+  for (int w2 = 0; w2 < NW; ++w2) tot += red[w2][0];
+  const double nrm = sqrt((double)tot);
   double2* Hc = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
   double2* Bc = Bk + (size_t)b * smax * m + (size_t)j * smax;
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int q0 = 0; q0 < nb; q0 += 16) {
-      R acc[32];
-#pragma unroll
-      for (int u = 0; u < 32; ++u) acc[u] = R(0);
-      for (int e = threadIdx.x; e < N; e += NT) {
-        const T2 we = w[e];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          if (q0 + u < nb) {
-            const T2 qe = basis(q0 + u)[e];
-            acc[2 * u] += qe.x * we.x + qe.y * we.y;
-            acc[2 * u + 1] += qe.x * we.y - qe.y * we.x;
-          }
-        }
-      }
-      block_sum<32, R>(acc, red);
-      if (threadIdx.x < 16 && q0 + threadIdx.x < nb) {
-        T2 c;
-        c.x = acc[2 * threadIdx.x];
-        c.y = acc[2 * threadIdx.x + 1];
-        coef[q0 + threadIdx.x] = c;
-      }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < N; e += NT) {
-      T2 we = w[e];
-      for (int q = 0; q < nb; ++q) we = csub(we, cmul(basis(q)[e], coef[q]));
-      w[e] = we;
-    }
-    if (threadIdx.x < nb) {
-      const int q = threadIdx.x;
-      const double2 cval = to_d2(coef[q]);
-      if (q < s_cur) {
-        Bc[q] = pass == 0 ? cval : cadd(Bc[q], cval);
-      } else {
-        const int r = q - s_cur;
-        Hc[r] = pass == 0 ? cval : cadd(Hc[r], cval);
-      }
-    }
-    __syncthreads();
+  if (threadIdx.x < nb) {
+    const int q = threadIdx.x;
+    const double2 cval = cadd(to_d2(coef[0][q]), to_d2(coef[1][q]));
+    if (q < s_cur) Bc[q] = cval;
+    else Hc[q - s_cur] = cval;
   }
-  R nr[1] = {R(0)};
-  for (int e = threadIdx.x; e < N; e += NT) nr[0] += cabs2(w[e]);
-  block_sum<1, R>(nr, red);
-  const double nrm = sqrt((double)nr[0]);
   if (threadIdx.x == 0) Hc[j + 1] = make_double2(nrm, 0.0);
   const R inv = nrm > 0.0 ? (R)(1.0 / nrm) : R(0);
-  for (int e = threadIdx.x; e < N; e += NT) w[e] = cscale(w[e], inv);
+  for (int e = threadIdx.x; e < N; e += OT) w[e] = cscale(w[e], inv);
 }
 
 // ------------------------------------------------------ Givens least squares

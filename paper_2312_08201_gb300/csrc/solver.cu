@@ -316,13 +316,13 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
       LY_TRY(op.apply(Lcur, ccur, B, Zj + (size_t)j * NS, (size_t)m * NS, Vj + (size_t)(j + 1) * NS,
                       (size_t)(m + 1) * NS, st));
       {
-        // CGS2: two passes, each reading nb basis vectors twice (dots, update) and w twice
+        // CGS2: the basis is read three times (dots, update + dots, update), w five times
         const int nb = s_cur + j + 1;
         const int ph = prof_begin(PK_ORTHO, st);
-        kry::k_ortho<T2><<<B, kry::NT, 0, st>>>(N, j, m, s_cur, Lcur, ccur, ws.V.p, ws.C.p, css, ws.H.p, ws.Bk.p,
+        kry::k_ortho<T2><<<B, kry::OT, 0, st>>>(N, j, m, s_cur, Lcur, ccur, ws.V.p, ws.C.p, css, ws.H.p, ws.Bk.p,
                                                 smax);
         lyap_count_launch();
-        prof_end(ph, st, 2.0 * 2.0 * 8.0 * nb * N, (4.0 * nb + 6.0) * N * sizeof(T2), 0, ccur);
+        prof_end(ph, st, 2.0 * 2.0 * 8.0 * nb * N, (3.0 * nb + 7.0) * N * sizeof(T2), 0, ccur);
       }
       {
         const int ph_ = prof_begin(PK_LSQ, st);
