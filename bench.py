@@ -414,7 +414,7 @@ def main():
             roof = dict(bound="alu", achieved=ach, peak=peak, unit="Tinst/s", frac=ach / peak, traffic=None,
                         kernel=dom_name,
                         peak_source="FP32 pipe: 152 SMs x 128 lane-instructions/clk x max SM clock "
-                                    "(achieved: 54 FP32 instructions per float-float complex MAC)",
+                                    "(achieved: 49.5 FP32 instructions per float-float complex MAC)",
                         launches=d["launches"], avg_launch_ms=d["total_ms"] / d["launches"])
         elif dom_name == "tc_gemm":
             peak = float(pk["bf16_tflops_sustained"])

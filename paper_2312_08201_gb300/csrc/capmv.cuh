@@ -46,7 +46,8 @@ int capmv64_launch(const CapArgs64& a, cudaStream_t st);
 // accuracy; see capmv_df.cu). Lff: n x n pairs (re hi, re lo, im hi, im lo) of
 // lc_scale * Lc, built by capmv_df_build_lc; p_scale: power of two applied to
 // P2; sw: device scratch indexed by system (>= largest system index + 1),
-// overwritten with each listed system's W scale.
+// overwritten with each listed system's W scale; panel: device scratch of
+// nsys k^2 n float4 (the float-float panel of each listed system).
 int capmv_df_build_lc(int n, const double2* lam, double lc_scale, float4* Lff, cudaStream_t st);
 int capmv_df_launch(const CapArgs64& a, const float4* Lff, double lc_scale, double p_scale, double* sw,
-                    cudaStream_t st);
+                    float4* panel, cudaStream_t st);

@@ -5,8 +5,8 @@
 // as the FP64 kernel (capmv64.cu) in float-float arithmetic: every value is
 // an unevaluated sum hi + lo of two floats; a product keeps hi*hi exactly
 // (FMA residue) plus the two cross terms; accumulation is an exact two-sum
-// with the rounding errors gathered in the low word and renormalised after
-// every K step. About 48 significant bits survive, so the residual error is
+// with the rounding errors gathered in the low word and renormalised every
+// few K steps. About 48 significant bits survive, so the residual error is
 // within a small multiple of FP64 rounding of the terms it cancels.
 //
 // Range: float has an 8-bit exponent, so the operands are scaled by powers
@@ -23,8 +23,11 @@
 
 namespace {
 
-constexpr int TI = 64, TNC = 64, TJ = 16, SROW = TNC + 1;
-constexpr double kFFInstrPerCmac = 54.0;
+constexpr int TI = 64, TNC = 64, TJ = 16, SROW = TNC + 1, SBROW = TNC + 1;
+constexpr int NORM_EVERY = 4;
+// FP32 instructions per float-float complex multiply-add: 4 products of 12
+// and two renormalisations of 3 every NORM_EVERY steps
+constexpr double kFFInstrPerCmac = 48.0 + 6.0 / NORM_EVERY;
 
 struct ff2 {  // complex float-float: re = rh + rl, im = ih + il
   float rh, rl, ih, il;
@@ -71,13 +74,20 @@ __device__ __forceinline__ void cmac_ff(const ff2& a, const ff2& b, Acc& c) {
   ff_mac(a.ih, a.il, b.rh, b.rl, c.ih, c.il);
 }
 
-// Per-system power-of-two scale of W (listed systems): sw[b] = 2^-ilogb(max |W_b|).
-__global__ void __launch_bounds__(256) k_sys_scale(CapArgs64 a, double* __restrict__ sw) {
+// Float-float panel of the listed systems, built once per launch so that the
+// product loop runs on FP32 pipes only. Slot s (system b = list[s]) gets
+//   sw[b] = 2^-ilogb(max |W_b|),
+//   panel[s][p k + t][j] = split((W_b[j, p] sw[b]) (P2[j, t] sp))
+// as float4 (re hi, re lo, im hi, im lo).
+__global__ void __launch_bounds__(256) k_panel_ff(CapArgs64 a, double sp, double* __restrict__ sw,
+                                                  float4* __restrict__ panel) {
   __shared__ double red[256];
   const int nsys = a.count ? *a.count : a.nsys;
-  if ((int)blockIdx.x >= nsys) return;
-  const int b = a.list ? a.list[blockIdx.x] : (int)blockIdx.x;
-  const size_t N = (size_t)a.n * a.k;
+  const int slot = blockIdx.x;
+  if (slot >= nsys) return;
+  const int b = a.list ? a.list[slot] : slot;
+  const int n = a.n, k = a.k, kk = k * k;
+  const size_t N = (size_t)n * k;
   const double2* W = a.W + (size_t)b * a.ldw;
   double mx = 0.0;
   for (size_t e = threadIdx.x; e < N; e += 256) mx = fmax(mx, fmax(fabs(W[e].x), fabs(W[e].y)));
@@ -87,19 +97,26 @@ __global__ void __launch_bounds__(256) k_sys_scale(CapArgs64 a, double* __restri
     if ((int)threadIdx.x < st) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + st]);
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const double m = red[0];
-    int e = (m > 0.0 && isfinite(m)) ? ilogb(m) : 0;
-    e = max(-600, min(600, e));
-    sw[b] = ldexp(1.0, -e);
+  const double m = red[0];
+  int ex = (m > 0.0 && isfinite(m)) ? ilogb(m) : 0;
+  ex = max(-600, min(600, ex));
+  const double sws = ldexp(1.0, -ex);
+  if (threadIdx.x == 0) sw[b] = sws;
+  float4* out = panel + (size_t)slot * kk * n;
+  for (size_t e = threadIdx.x; e < (size_t)kk * n; e += 256) {
+    const int pt = (int)(e / n), j = (int)(e % n);
+    const int p = pt / k, t = pt % k;
+    const ff2 v = to_ff(cmul(cscale(W[(size_t)p * n + j], sws), cscale(a.P2[(size_t)t * n + j], sp)));
+    out[e] = make_float4(v.rh, v.rl, v.ih, v.il);
   }
 }
 
-__global__ void __launch_bounds__(256) k_capmv_df(CapArgs64 a, const float4* __restrict__ Lff, double sp,
-                                                  double inv_lp, const double* __restrict__ sw) {
+__global__ void __launch_bounds__(256, 2) k_capmv_df(CapArgs64 a, const float4* __restrict__ Lff,
+                                                     const float4* __restrict__ panel, double inv_lp,
+                                                     const double* __restrict__ sw) {
   extern __shared__ double2 smem[];
   ff2* sA = reinterpret_cast<ff2*>(smem);  // [TJ][TI]
-  ff2* sB = sA + TJ * TI;                   // [TJ][TNC]
+  ff2* sB = sA + TJ * TI;                   // [TJ][SBROW]
   const int n = a.n, k = a.k, kk = k * k;
   const int SB = TNC / kk;
   const int ncols = SB * kk;
@@ -129,31 +146,39 @@ __global__ void __launch_bounds__(256) k_capmv_df(CapArgs64 a, const float4* __r
     }
 #pragma unroll
     for (int q = 0; q < (TJ * TNC) / 256; ++q) {
+      // 16 consecutive threads read 16 consecutive rows of one panel column
       const int e = tid + 256 * q;
-      const int jj = e / TNC, cc = e % TNC;
+      const int jj = e % TJ, cc = e / TJ;
       const int j = j0 + jj;
       ff2 v{0.f, 0.f, 0.f, 0.f};
       const int sl = cc / kk;
       if (cc < ncols && j < n && s0 + sl < nsys) {
-        const int pt = cc % kk, p = pt / k, t = pt % k;
-        const int b = a.list ? a.list[s0 + sl] : s0 + sl;
-        v = to_ff(cmul(cscale(a.W[(size_t)b * a.ldw + (size_t)p * n + j], sw[b]), cscale(a.P2[(size_t)t * n + j], sp)));
+        const float4 f = panel[((size_t)(s0 + sl) * kk + cc % kk) * n + j];
+        v = ff2{f.x, f.y, f.z, f.w};
       }
-      sB[jj * TNC + cc] = v;
+      sB[jj * SBROW + cc] = v;
     }
     __syncthreads();
-#pragma unroll 2
-    for (int jj = 0; jj < TJ; ++jj) {
-      ff2 av[4], bv[4];
+#pragma unroll 1
+    for (int jq = 0; jq < TJ; jq += NORM_EVERY) {
+#pragma unroll 1
+      for (int jj = jq; jj < jq + NORM_EVERY; ++jj) {
+        ff2 bv[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) av[r] = sA[jj * TI + ty + 16 * r];
+        for (int c = 0; c < 4; ++c) bv[c] = sB[jj * SBROW + tx + 16 * c];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) bv[c] = sB[jj * TNC + tx + 16 * c];
+        for (int r = 0; r < 4; ++r) {
+          const ff2 av = sA[jj * TI + ty + 16 * r];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) cmac_ff(av, bv[c], acc[r][c]);
+        }
+      }
+      // fold the low words back every NORM_EVERY steps: between folds each low
+      // word gathers 2 NORM_EVERY rounding errors of at most 2^-24 of the sum
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          cmac_ff(av[r], bv[c], acc[r][c]);
           ff_norm(acc[r][c].rh, acc[r][c].rl);
           ff_norm(acc[r][c].ih, acc[r][c].il);
         }
@@ -220,7 +245,7 @@ int capmv_df_build_lc(int n, const double2* lam, double lc_scale, float4* Lff, c
 }
 
 int capmv_df_launch(const CapArgs64& a, const float4* Lff, double lc_scale, double p_scale, double* sw,
-                    cudaStream_t st) {
+                    float4* panel, cudaStream_t st) {
   if (a.k < 1 || a.k > 8) return LYAP_EINVAL;
   if (a.nsys <= 0) return LYAP_OK;
   const int kk = a.k * a.k;
@@ -232,13 +257,13 @@ int capmv_df_launch(const CapArgs64& a, const float4* Lff, double lc_scale, doub
     attr_rc = cudaFuncSetAttribute(k_capmv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   LY_CUDA(attr_rc);
-  k_sys_scale<<<a.nsys, 256, 0, st>>>(a, sw);
+  k_panel_ff<<<a.nsys, 256, 0, st>>>(a, p_scale, sw, panel);
   lyap_count_launch();
   dim3 grid((a.n + TI - 1) / TI, (a.nsys + SB - 1) / SB);
-  // work per system: n^2 k^2 float-float complex multiply-adds of 54 FP32
-  // instructions each (4 products of 12, two renormalisations of 3)
+  // work per system: n^2 k^2 float-float complex multiply-adds of
+  // kFFInstrPerCmac FP32 instructions each
   const int ph = prof_begin(PK_CAPMV_FF, st);
-  k_capmv_df<<<grid, 256, smem, st>>>(a, Lff, p_scale, 1.0 / (lc_scale * p_scale), sw);
+  k_capmv_df<<<grid, 256, smem, st>>>(a, Lff, panel, 1.0 / (lc_scale * p_scale), sw);
   lyap_count_launch();
   prof_end(ph, st, kFFInstrPerCmac * (double)a.n * a.n * kk, 2.0 * (double)a.n * a.k * sizeof(double2),
            a.count ? 0 : a.nsys, a.count);

@@ -47,6 +47,7 @@ struct MixedState {
   DevBuf<float4> Lff;  // n x n
   double lc_scale = 1.0, p_scale = 1.0;
   DevBuf<double> sw;   // bcap
+  DevBuf<float4> panel_ff;  // bcap x k^2 n
 };
 
 namespace {
@@ -228,6 +229,7 @@ int ensure_refine(lyap_seed* sd, int Bc) {
   LY_TRY(ms.act.alloc(Bc));
   LY_TRY(ms.cnt.alloc(1));
   LY_TRY(ms.sw.alloc(Bc));
+  LY_TRY(ms.panel_ff.alloc((size_t)Bc * sd->k * sd->k * sd->n));
   ms.bcap = Bc;
   return LYAP_OK;
 }
@@ -277,7 +279,7 @@ int refine(lyap_seed* sd, int Bc, const double* vinv, const double2* rhs, double
       a.count = ms.cnt.p;
       a.nsys = nact;
       if (o.residual == LYAP_RESID_FP64) LY_TRY(capmv64_launch(a, st));
-      else LY_TRY(capmv_df_launch(a, ms.Lff.p, ms.lc_scale, ms.p_scale, ms.sw.p, st));
+      else LY_TRY(capmv_df_launch(a, ms.Lff.p, ms.lc_scale, ms.p_scale, ms.sw.p, ms.panel_ff.p, st));
       kry::k_norms<double2><<<Bc, kry::NT, 0, st>>>(N, Bc, ms.R64.p, N, ms.norms.p);
       lyap_count_launch();
       LY_CUDA(cudaGetLastError());
@@ -475,8 +477,10 @@ extern "C" int lyap_test_apply(lyap_seed* sd, int nsys, const double* v, const d
       LY_TRY(capmv64_launch(a, st));
     } else {
       DevBuf<double> sw;
+      DevBuf<float4> panel;
       LY_TRY(sw.alloc(nsys));
-      LY_TRY(capmv_df_launch(a, sd->mixed->Lff.p, sd->mixed->lc_scale, sd->mixed->p_scale, sw.p, st));
+      LY_TRY(panel.alloc((size_t)nsys * k * k * sd->n));
+      LY_TRY(capmv_df_launch(a, sd->mixed->Lff.p, sd->mixed->lc_scale, sd->mixed->p_scale, sw.p, panel.p, st));
       LY_CUDA(cudaStreamSynchronize(st));
     }
   } else {
