@@ -34,53 +34,6 @@ __global__ void k_compact(const int* __restrict__ in_list, const int* __restrict
   if (threadIdx.x == blockDim.x - 1) *out_count = sc[threadIdx.x];
 }
 
-// status codes kept per system
-enum { ST_RUN = 0, ST_CONV = 1, ST_MAXIT = 2, ST_BREAK = 3, ST_NONFINITE = 4 };
-
-__global__ void k_lsq(int j, int m, const int* __restrict__ list, const int* __restrict__ count,
-                      double2* __restrict__ H, double2* __restrict__ H0, double* __restrict__ cs,
-                      double2* __restrict__ sn, double2* __restrict__ g, const double* __restrict__ tolabs,
-                      int* __restrict__ jstop, int* __restrict__ flag, const int* __restrict__ iters_done, int maxit) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= *count) return;
-  const int b = list[slot];
-  double2* h = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
-  double2* h0 = H0 + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
-  for (int i = 0; i <= j + 1; ++i) h0[i] = h[i];
-  double* c = cs + (size_t)b * m;
-  double2* s = sn + (size_t)b * m;
-  double2* gb = g + (size_t)b * (m + 1);
-  for (int i = 0; i < j; ++i) {
-    double2 top = h[i], bot = h[i + 1];
-    h[i] = cadd(cscale(top, c[i]), cmul(s[i], bot));
-    h[i + 1] = csub(cscale(bot, c[i]), cjmul(s[i], top));
-  }
-  double cj;
-  double2 sj;
-  sd::givens<double2, double>(h[j], h[j + 1], cj, sj);
-  double2 rho = cadd(cscale(h[j], cj), cmul(sj, h[j + 1]));
-  const double sub = h0[j + 1].x;
-  h[j] = rho;
-  h[j + 1] = make_double2(0.0, 0.0);
-  c[j] = cj;
-  s[j] = sj;
-  double2 gj = gb[j];
-  gb[j] = cscale(gj, cj);
-  gb[j + 1] = cscale(cjmul(sj, gj), -1.0);
-  const double res = sqrt(cabs2(gb[j + 1]));
-  int st = ST_RUN;
-  if (!isfinite(res) || !isfinite(rho.x) || !isfinite(rho.y)) st = ST_NONFINITE;
-  else if (res <= tolabs[b]) st = ST_CONV;
-  else if (!(sub > 1e-14 * sqrt(cabs2(rho)))) st = ST_CONV;  // invariant subspace: exact in the space
-  else if (iters_done[b] + j + 1 >= maxit) st = ST_MAXIT;
-  if (st != ST_RUN) {
-    jstop[b] = j + 1;
-    flag[b] = -st;  // negative: stopped this cycle with a final status
-  } else {
-    jstop[b] = j + 1;  // provisional (cycle may end here)
-  }
-}
-
 __global__ void k_cycle_solve(int m, int smax, int s_cur, const int* __restrict__ list,
                               const int* __restrict__ count, const double2* __restrict__ H,
                               const double2* __restrict__ H0, const double2* __restrict__ Bk,

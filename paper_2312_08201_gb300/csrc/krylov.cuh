@@ -73,6 +73,62 @@ __global__ void k_compact(const int* __restrict__ in_list, const int* __restrict
                           const int* __restrict__ flag, int* __restrict__ out_list, int* __restrict__ out_count);
 __global__ void k_iota(int B, int* list, int* count);
 
+// ------------------------------------------------------ Givens least squares
+// status codes kept per system
+enum { ST_RUN = 0, ST_CONV = 1, ST_MAXIT = 2, ST_BREAK = 3, ST_NONFINITE = 4 };
+
+struct LsqArgs {
+  double2* H0;
+  double* cs;
+  double2* sn;
+  double2* g;
+  const double* tolabs;
+  int* jstop;
+  int* flag;
+  const int* iters_done;
+  int maxit;
+};
+
+// Column j of H (rows 0..j+1) is copied to H0 (unrotated, for the residual
+// and the harmonic-Ritz problem), rotated by the previous rotations, and a
+// new rotation zeroes H[j+1, j]. |g[j+1]| is the residual norm of the
+// projected problem; when it reaches tolabs, or H[j+1, j] vanishes
+// (breakdown: exact solution in the space), the system stops this cycle.
+// Run by one thread per system, right after the column is complete.
+__device__ __forceinline__ void lsq_column(int b, int j, int m, double2* __restrict__ H, const LsqArgs& L) {
+  double2* h = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
+  double2* h0 = L.H0 + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
+  for (int i = 0; i <= j + 1; ++i) h0[i] = h[i];
+  double* c = L.cs + (size_t)b * m;
+  double2* s = L.sn + (size_t)b * m;
+  double2* gb = L.g + (size_t)b * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    const double2 top = h[i], bot = h[i + 1];
+    h[i] = cadd(cscale(top, c[i]), cmul(s[i], bot));
+    h[i + 1] = csub(cscale(bot, c[i]), cjmul(s[i], top));
+  }
+  double cj;
+  double2 sj;
+  sd::givens<double2, double>(h[j], h[j + 1], cj, sj);
+  const double2 rho = cadd(cscale(h[j], cj), cmul(sj, h[j + 1]));
+  const double sub = h0[j + 1].x;
+  h[j] = rho;
+  h[j + 1] = make_double2(0.0, 0.0);
+  c[j] = cj;
+  s[j] = sj;
+  const double2 gj = gb[j];
+  gb[j] = cscale(gj, cj);
+  gb[j + 1] = cscale(cjmul(sj, gj), -1.0);
+  const double res = sqrt(cabs2(gb[j + 1]));
+  int st = ST_RUN;
+  if (!isfinite(res) || !isfinite(rho.x) || !isfinite(rho.y)) st = ST_NONFINITE;
+  else if (res <= L.tolabs[b]) st = ST_CONV;
+  else if (!(sub > 1e-14 * sqrt(cabs2(rho)))) st = ST_CONV;  // invariant subspace: exact in the space
+  else if (L.iters_done[b] + j + 1 >= L.maxit) st = ST_MAXIT;
+  L.jstop[b] = j + 1;  // provisional when still running (the cycle may end here)
+  if (st != ST_RUN) L.flag[b] = -st;  // negative: stopped this cycle with a final status
+}
+
 // ----------------------------------------------------------- CGS2 Arnoldi
 // Sum 32 per-thread values over a warp: after the call lane l holds, in
 // v[0], the warp total of value l (a butterfly that halves the values per
@@ -95,7 +151,8 @@ __device__ __forceinline__ void warp_reduce_scatter32(R (&v)[32]) {
 constexpr int OT = 512;  // threads per system in the orthogonalisation
 
 // w = V_b[j+1] is orthogonalised against the recycled C_b (s_cur vectors)
-// and V_b[0..j] with two classical Gram-Schmidt passes, then normalised; the
+// and V_b[0..j] with two classical Gram-Schmidt passes, then normalised, and
+// the new column of H enters the Givens least-squares update; the
 // summed coefficients of both passes go to Bk (C part) and H (V part) in
 // FP64. The first pass's update and the second pass's inner products share
 // one sweep over the basis, and the second update computes ||w||: the
@@ -104,7 +161,7 @@ template <typename T2>
 __global__ void __launch_bounds__(OT, sizeof(T2) == 8 ? 2 : 1) k_ortho(int N, int j, int m, int s_cur, const int* __restrict__ list,
                                              const int* __restrict__ count, T2* __restrict__ V,
                                              const T2* __restrict__ C, size_t c_ss, double2* __restrict__ H,
-                                             double2* __restrict__ Bk, int smax) {
+                                             double2* __restrict__ Bk, int smax, LsqArgs L) {
   using R = typename RealOf<T2>::T;
   constexpr int NW = OT / 32;
   __shared__ R red[NW][32];
@@ -207,20 +264,11 @@ __global__ void __launch_bounds__(OT, sizeof(T2) == 8 ? 2 : 1) k_ortho(int N, in
     else Hc[q - s_cur] = cval;
   }
   if (threadIdx.x == 0) Hc[j + 1] = make_double2(nrm, 0.0);
+  __syncthreads();
+  if (threadIdx.x == 0) lsq_column(b, j, m, H, L);  // while the others normalise w
   const R inv = nrm > 0.0 ? (R)(1.0 / nrm) : R(0);
   for (int e = threadIdx.x; e < N; e += OT) w[e] = cscale(w[e], inv);
 }
-
-// ------------------------------------------------------ Givens least squares
-// Column j of H (rows 0..j+1) is copied to H0 (unrotated, for the residual
-// and the harmonic-Ritz problem), rotated by the previous rotations, and a
-// new rotation zeroes H[j+1, j]. |g[j+1]| is the residual norm of the
-// projected problem; when it reaches tolabs, or H[j+1, j] vanishes
-// (breakdown: exact solution in the space), the system stops this cycle.
-__global__ void k_lsq(int j, int m, const int* __restrict__ list, const int* __restrict__ count,
-                      double2* __restrict__ H, double2* __restrict__ H0, double* __restrict__ cs,
-                      double2* __restrict__ sn, double2* __restrict__ g, const double* __restrict__ tolabs,
-                      int* __restrict__ jstop, int* __restrict__ flag, const int* __restrict__ iters_done, int maxit);
 
 // ---------------------------------------------------------------- starts
 // beta = ||r_b||, V_b[0] = r_b / beta, g = beta e1; systems already below

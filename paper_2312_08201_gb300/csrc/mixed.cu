@@ -41,7 +41,7 @@ struct MixedState {
   DevBuf<float2> R32;
   DevBuf<double> norms, vinv_c;
   DevBuf<int> act, cnt;
-  DevBuf<float2> wcinv, wpart;
+  DevBuf<float2> wcinv, wpart, wcinv_full;
   WoodState wood;
   // float-float residual operands (capmv_df.cu)
   DevBuf<float4> Lff;  // n x n
@@ -314,7 +314,8 @@ int refine(lyap_seed* sd, int Bc, const double* vinv, const double2* rhs, double
       if (ms.wpart.count < wood_part_count(sd->n, k, na, r)) LY_TRY(ms.wpart.alloc(wood_part_count(sd->n, k, Bc, r)));
       ms.wood.cinv = ms.wcinv.p;
       ms.wood.cpart = ms.wpart.p;
-      LY_TRY(wood_prepare(sd, r, na, ms.vinv_c.p, adjoint, ms.wood, st));
+      // Cap(v)^{-1} of every chunk system was built once by lyap_mixed_chunk
+      LY_TRY(wood_bind(sd, r, na, ms.wcinv_full.p, ms.act.p, ms.wood, st));
       op.wood = &ms.wood;
     }
     LY_TRY(gcrodr_chunk<float2>(op, na, ms.R32.p, (size_t)N, rec, pin, ws, it, stt, st));
@@ -398,6 +399,16 @@ int lyap_mixed_chunk(lyap_seed* sd, int Bc, const double* vinv, const lyap_opts&
   iters.assign(Bc, 0);
   status.assign(Bc, LYAP_OK);
   rsteps.assign(Bc, 0);
+  MixedState& ms = *sd->mixed;
+  if (o.pbar > 0 && sd->tsvd_r > 0) {
+    // Cap(v_b)^{-1} for the whole chunk, shared by every refinement step and
+    // by the adjoint solves (which apply its transpose)
+    const int r = std::min(o.pbar, sd->tsvd_r);
+    if (ms.wcinv_full.count < (size_t)Bc * r * r) LY_TRY(ms.wcinv_full.alloc((size_t)Bc * r * r));
+    WoodState full;
+    full.cinv = ms.wcinv_full.p;
+    LY_TRY(wood_prepare(sd, r, Bc, vinv, false, full, st));
+  }
   LY_TRY(refine(sd, Bc, vinv, sd->Ph.p, sd->ph_norm, false, sd->rec32, o, prm, st, ws, Wp_out, iters, status, rsteps));
   // every system's final residual was evaluated (and kept) by its last refinement step
   if (Rres_out)

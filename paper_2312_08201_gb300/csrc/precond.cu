@@ -464,6 +464,15 @@ void launch_prec(lyap_seed* sd, const WoodState* ws, bool adjoint, const double*
 }
 
 
+__global__ void k_gather_cinv(const float2* __restrict__ src, const int* __restrict__ idx, int B, int rr,
+                              float2* __restrict__ dst) {
+  const size_t total = (size_t)B * rr;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = e / rr, o = e % rr;
+    dst[e] = src[(size_t)idx[c] * rr + o];
+  }
+}
+
 }  // namespace
 
 int lyap_tsvd_prepare(lyap_seed* sd, int r, cudaStream_t st) {
@@ -542,6 +551,21 @@ int lyap_tsvd_prepare(lyap_seed* sd, int r, cudaStream_t st) {
   LY_CUDA(cudaStreamSynchronize(st));
   sd->tsvd_r = r;
   sd->resident_bytes += sd->tsvd_N.bytes() + sd->tsvd_M.bytes();
+  return LYAP_OK;
+}
+
+int wood_bind(lyap_seed* sd, int r, int B, const float2* cinv_full, const int* idx, WoodState& ws, cudaStream_t st) {
+  r = std::min(r, sd->tsvd_r);
+  ws.r = r;
+  ws.B = B;
+  ws.Nl = sd->tsvd_N.p;
+  ws.Ml = sd->tsvd_M.p;
+  ws.ldr = sd->n * sd->k;
+  if (r <= 0 || B <= 0) return LYAP_OK;
+  const size_t total = (size_t)B * r * r;
+  k_gather_cinv<<<gridn(total), 256, 0, st>>>(cinv_full, idx, B, r * r, ws.cinv);
+  lyap_count_launch();
+  LY_CUDA(cudaGetLastError());
   return LYAP_OK;
 }
 

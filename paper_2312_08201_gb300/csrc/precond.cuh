@@ -40,6 +40,10 @@ size_t wood_part_count(int n, int k, int B, int r);
 // (caller-owned, B r^2 entries). ws must stay alive while the chunk runs.
 int wood_prepare(lyap_seed* sd, int r, int B, const double* vinv, bool adjoint, WoodState& ws, cudaStream_t st);
 
+// Per refinement step: ws.cinv[c] = cinv_full[idx[c]] for c < B (Cap(v)
+// depends on v only, so the inverses of a chunk are built once).
+int wood_bind(lyap_seed* sd, int r, int B, const float2* cinv_full, const int* idx, WoodState& ws, cudaStream_t st);
+
 // Out_b = P(v_b)^{-1} In_b for the listed systems: block-Jacobi K^{-1}, plus
 // the Woodbury term K^{-1} Nl Cap^{-1} Ml^T K^{-1} when ws has rank > 0
 // (ws == nullptr: block-Jacobi only). Adjoint: P^T.

@@ -17,7 +17,7 @@ enum ProfKernel {
   PK_TSMM = 5,      // batched tall-skinny products
   PK_RITZ = 6,      // harmonic-Ritz small dense problems
   PK_EPI32 = 7,     // FP32 operator epilogue (mixed path)
-  PK_LSQ = 8,       // Givens least-squares step
+  PK_LSQ = 8,       // (no launches: the Givens step runs in the orthogonalisation kernel)
   PK_CYCLE = 9,     // cycle start/solve/update kernels
   PK_PANEL = 10,    // panel build for the tensor-core GEMM
   PK_RECSTART = 11, // recycle start (AU, CholQR2, projection)

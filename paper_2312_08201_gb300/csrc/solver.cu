@@ -319,16 +319,13 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
         // CGS2: the basis is read three times (dots, update + dots, update), w five times
         const int nb = s_cur + j + 1;
         const int ph = prof_begin(PK_ORTHO, st);
+        // the same kernel applies the Givens least-squares update to the new column
+        const kry::LsqArgs la{ws.H0.p, ws.cs.p, ws.sn.p, ws.g.p, ws.tolabs.p, ws.jstop.p, ws.flag.p, ws.iters.p,
+                              maxit};
         kry::k_ortho<T2><<<B, kry::OT, 0, st>>>(N, j, m, s_cur, Lcur, ccur, ws.V.p, ws.C.p, css, ws.H.p, ws.Bk.p,
-                                                smax);
+                                                smax, la);
         lyap_count_launch();
         prof_end(ph, st, 2.0 * 2.0 * 8.0 * nb * N, (3.0 * nb + 7.0) * N * sizeof(T2), 0, ccur);
-      }
-      {
-        const int ph_ = prof_begin(PK_LSQ, st);
-        kry::k_lsq<<<g1, 256, 0, st>>>(j, m, Lcur, ccur, ws.H.p, ws.H0.p, ws.cs.p, ws.sn.p, ws.g.p, ws.tolabs.p,
-                                     ws.jstop.p, ws.flag.p, ws.iters.p, maxit); lyap_count_launch();
-        prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
       }
       kry::k_compact<<<1, 1024, 0, st>>>(Lcur, ccur, ws.flag.p, Lnext, cnext); lyap_count_launch();
       LY_CUDA(cudaGetLastError());
