@@ -94,15 +94,17 @@ __global__ void __launch_bounds__(32) k_ritz(int m, int smax, int s_cur, int s_n
     if (sd::lane() == 0) ok[b] = 0;
     return;
   }
+  // shared matrices use leading dimension LS = m + 1 >= re (re x me at most)
+  const int LS = m + 1;
   extern __shared__ float2 smf[];
-  float2* Gf = smf;                          // LD x LD
-  float2* Ff = Gf + (size_t)LD * LD;         // LD x LD -> Qg^H Fhat
-  float2* K = Ff + (size_t)LD * LD;          // LD x LD
-  float2* Q = K + (size_t)LD * LD;           // LD x LD
-  float2* vt = Q + (size_t)LD * LD;          // LD
-  float2* Yz = vt + LD;                      // LD x 16
-  float2* Xf = Yz + (size_t)LD * 16;         // LD x 16
-  int* sel = reinterpret_cast<int*>(Xf + (size_t)LD * 16);  // 16
+  float2* Gf = smf;                          // LS x LS
+  float2* Ff = Gf + (size_t)LS * LS;         // LS x LS -> Qg^H Fhat
+  float2* K = Ff + (size_t)LS * LS;          // LS x LS
+  float2* Q = K + (size_t)LS * LS;           // LS x LS
+  float2* vt = Q + (size_t)LS * LS;          // LS
+  float2* Yz = vt + LS;                      // LS x 16
+  float2* Xf = Yz + (size_t)LS * 16;         // LS x 16
+  int* sel = reinterpret_cast<int*>(Xf + (size_t)LS * 16);  // 16
   double2* w = work + (size_t)b * wstride;
   double2* Gh = w;                           // LD x LD (FP64)
   double2* P = Gh + (size_t)LD * LD;         // LD x 16
@@ -131,27 +133,27 @@ __global__ void __launch_bounds__(32) k_ritz(int m, int smax, int s_cur, int s_n
       if (ii <= cc + 1) v = H0b[ii + (size_t)cc * (m + 1)];
     }
     Gh[i + (size_t)c * LD] = v;
-    Gf[i + (size_t)c * LD] = make_float2((float)v.x, (float)v.y);
+    Gf[i + (size_t)c * LS] = make_float2((float)v.x, (float)v.y);
     double2 f = Fb[i + (size_t)c * LD];
     if (c < s_cur) f = cscale(f, D[c]);
-    Ff[i + (size_t)c * LD] = make_float2((float)f.x, (float)f.y);
+    Ff[i + (size_t)c * LS] = make_float2((float)f.x, (float)f.y);
   }
   sd::wsync();
-  sd::householder_qr_apply<float2>(re, me, Gf, LD, Ff, LD, me, vt);
-  for (int e = sd::lane(); e < me * me; e += 32) K[(e % me) + (size_t)(e / me) * LD] = Ff[(e % me) + (size_t)(e / me) * LD];
+  sd::householder_qr_apply<float2>(re, me, Gf, LS, Ff, LS, me, vt);
+  for (int e = sd::lane(); e < me * me; e += 32) K[(e % me) + (size_t)(e / me) * LS] = Ff[(e % me) + (size_t)(e / me) * LS];
   sd::wsync();
-  sd::trsm_upper_left<float2>(me, me, Gf, LD, K, LD);
+  sd::trsm_upper_left<float2>(me, me, Gf, LS, K, LS);
   bool fin = true;
   for (int e = sd::lane(); e < me * me; e += 32) {
-    const float2 v = K[(e % me) + (size_t)(e / me) * LD];
+    const float2 v = K[(e % me) + (size_t)(e / me) * LS];
     fin &= isfinite(v.x) && isfinite(v.y);
   }
   if (!__all_sync(0xffffffffu, fin)) {
     if (sd::lane() == 0) ok[b] = 0;
     return;
   }
-  sd::hessenberg<float2>(me, K, LD, Q, LD, vt);
-  if (sd::hqr<float2>(me, K, LD, Q, LD, 60 * me)) {
+  sd::hessenberg<float2>(me, K, LS, Q, LS, vt);
+  if (sd::hqr<float2>(me, K, LS, Q, LS, 60 * me)) {
     if (sd::lane() == 0) ok[b] = 0;
     return;
   }
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(32) k_ritz(int m, int smax, int s_cur, int s_n
         bool used = false;
         for (int q = 0; q < c; ++q) used |= sel[q] == i;
         if (used) continue;
-        const float a = cabs2(K[i + (size_t)i * LD]);
+        const float a = cabs2(K[i + (size_t)i * LS]);
         if (a > bv) {
           bv = a;
           best = i;
@@ -173,9 +175,9 @@ __global__ void __launch_bounds__(32) k_ritz(int m, int smax, int s_cur, int s_n
     }
   }
   sd::wsync();
-  sd::schur_vectors<float2>(me, K, LD, Q, LD, sel, s_new, Yz, LD, Xf, LD);
+  sd::schur_vectors<float2>(me, K, LS, Q, LS, sel, s_new, Yz, LS, Xf, LS);
   for (int e = sd::lane(); e < me * s_new; e += 32) {
-    const float2 x = Xf[(e % me) + (size_t)(e / me) * LD];
+    const float2 x = Xf[(e % me) + (size_t)(e / me) * LS];
     P[(e % me) + (size_t)(e / me) * LD] = make_double2(x.x, x.y);
   }
   sd::wsync();
@@ -208,9 +210,9 @@ __global__ void __launch_bounds__(32) k_ritz(int m, int smax, int s_cur, int s_n
   if (sd::lane() == 0) ok[b] = 1;
 }
 
-size_t ritz_smem_bytes(int m, int smax) {
-  const int LD = m + smax + 1;
-  return sizeof(float2) * ((size_t)4 * LD * LD + LD + (size_t)2 * LD * 16) + 16 * sizeof(int);
+size_t ritz_smem_bytes(int m, int /*smax*/) {
+  const int LS = m + 1;
+  return sizeof(float2) * ((size_t)4 * LS * LS + LS + (size_t)2 * LS * 16) + 16 * sizeof(int);
 }
 
 __global__ void k_chol_rinv(int s, const int* __restrict__ list, const int* __restrict__ count,

@@ -345,7 +345,11 @@ __global__ void __launch_bounds__(NT) k_update_xr(int N, int m, int smax, int s_
 }
 
 // ------------------------------------------------- batched Gram: A^H B
-// out_b (na x nb, ld = ldo, system stride os) = [A segs]^H [B segs]
+// out_b (na x nb, ld = ldo, system stride os) = [A segs]^H [B segs], one CTA
+// per system, na, nb <= 64. K tiles of TK elements are staged with TK
+// consecutive threads reading one vector (coalesced); each thread owns up to
+// four 2 x 2 output tiles (one shared load per complex multiply-add), sums
+// each K tile in the vector precision and accumulates in FP64.
 template <typename T2>
 __global__ void __launch_bounds__(NT) k_gram(int N, const int* __restrict__ list, const int* __restrict__ count,
                                             Seg2<T2> A, Seg2<T2> Bm, double2* __restrict__ out, int ldo,
@@ -356,38 +360,54 @@ __global__ void __launch_bounds__(NT) k_gram(int N, const int* __restrict__ list
   if (slot >= *count) return;
   const int b = list[slot];
   const int na = A.cnt(b), nbb = Bm.cnt(b);
-  const int nout = na * nbb;
-  double2 acc[16];
+  const int ta = (na + 1) / 2, tb = (nbb + 1) / 2, ntile = ta * tb;  // <= 1024 = 4 NT
+  const T2 z = cvt<T2>(make_double2(0.0, 0.0));
+  double2 acc[4][4];
 #pragma unroll
-  for (int u = 0; u < 16; ++u) acc[u] = make_double2(0.0, 0.0);
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = make_double2(0.0, 0.0);
+  const int cmax = max(2 * ta, 2 * tb);
   for (int e0 = 0; e0 < N; e0 += TK) {
-    for (int q = threadIdx.x; q < TK * MAXC; q += NT) {
-      int l = q / MAXC, c = q % MAXC;
-      int e = e0 + l;
-      const T2 z = cvt<T2>(make_double2(0.0, 0.0));
+    for (int q = threadIdx.x; q < TK * cmax; q += NT) {
+      const int c = q / TK, l = q % TK;
+      const int e = e0 + l;
       sa[l][c] = (c < na && e < N) ? A.vec(b, c)[e] : z;
       sb[l][c] = (c < nbb && e < N) ? Bm.vec(b, c)[e] : z;
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      int o = threadIdx.x + u * NT;
-      if (o < nout) {
-        int i = o % na, jj = o / na;
-        T2 t = cvt<T2>(make_double2(0.0, 0.0));
+    for (int u = 0; u < 4; ++u) {
+      const int tile = threadIdx.x + u * NT;
+      if (tile < ntile) {
+        const int i0 = 2 * (tile % ta), j0 = 2 * (tile / ta);
+        T2 t00 = z, t01 = z, t10 = z, t11 = z;
 #pragma unroll
-        for (int l = 0; l < TK; ++l) t = cadd(t, cjmul(sa[l][i], sb[l][jj]));
-        acc[u] = cadd(acc[u], to_d2(t));
+        for (int l = 0; l < TK; ++l) {
+          const T2 a0 = sa[l][i0], a1 = sa[l][i0 + 1], b0 = sb[l][j0], b1 = sb[l][j0 + 1];
+          t00 = cadd(t00, cjmul(a0, b0));
+          t10 = cadd(t10, cjmul(a1, b0));
+          t01 = cadd(t01, cjmul(a0, b1));
+          t11 = cadd(t11, cjmul(a1, b1));
+        }
+        acc[u][0] = cadd(acc[u][0], to_d2(t00));
+        acc[u][1] = cadd(acc[u][1], to_d2(t10));
+        acc[u][2] = cadd(acc[u][2], to_d2(t01));
+        acc[u][3] = cadd(acc[u][3], to_d2(t11));
       }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    int o = threadIdx.x + u * NT;
-    if (o < nout) {
-      int i = o % na, jj = o / na;
-      out[(size_t)b * os + i + (size_t)jj * ldo] = acc[u];
+  for (int u = 0; u < 4; ++u) {
+    const int tile = threadIdx.x + u * NT;
+    if (tile < ntile) {
+      const int i0 = 2 * (tile % ta), j0 = 2 * (tile / ta);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = i0 + (v & 1), jj = j0 + (v >> 1);
+        if (i < na && jj < nbb) out[(size_t)b * os + i + (size_t)jj * ldo] = acc[u][v];
+      }
     }
   }
 }
