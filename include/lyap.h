@@ -95,9 +95,12 @@ typedef struct lyap_server lyap_server;
  * threshold 1e-10 tightened to 1e-12 for the FP64 path (the trace is a
  * linear functional of the capacitance solution and is wanted to 1e-10),
  * at most 300 iterations, s = 10 recycled vectors. The cycle length m is
- * not given in the paper; the default is 30. The TSVD rank defaults to 30
- * (the paper uses 50 and 5 in its examples; 30 is the fastest setting of
- * the mixed path on the 800-state benchmark). */
+ * not given in the paper; the default 40 is the fastest of 24..60 for both
+ * paths on the 800-state benchmark. The TSVD rank defaults to 30 (the paper
+ * uses 50 and 5 in its examples; 30 is the fastest setting of the mixed path
+ * on that benchmark). The mixed path's inner tolerance defaults to 1e-4:
+ * the tensor-core operator is accurate to about 1e-5, so a tighter inner
+ * solve does not save refinement steps, and 1e-4 minimised the time. */
 typedef struct {
   double tol;        /* FP64 path: stop when ||r|| <= tol ||b||               */
   double refine_tol; /* mixed path: outer stop on the FP64 residual           */
@@ -222,6 +225,10 @@ int lyap_grad(lyap_seed* seed, int nv, const double* v, int mem_kind, const lyap
 int lyap_serve_create(lyap_ctx* ctx, const lyap_opts* opts, lyap_server** out);
 /* Register a seed (the server does not take ownership). */
 int lyap_serve_register_seed(lyap_server* srv, lyap_seed* seed, int* seed_id);
+/* Device bytes that admission charges for a request of nv vectors on a
+ * registered seed (the estimate lyap_serve_submit compares with the budget).
+ * Errors: LYAP_EINVAL, LYAP_ENOTFOUND (seed id). */
+int lyap_serve_estimate(lyap_server* srv, int seed_id, int nv, int want_grad, size_t* bytes);
 /* Enqueue nv parameter vectors (nv x k row-major, copied); returns a ticket.
  * Errors: LYAP_EINVAL (v_i = 0 or not finite), LYAP_ENOTFOUND (seed id),
  * LYAP_ENOMEM (the request alone exceeds the budget). */

@@ -143,6 +143,9 @@ _SIGS = {
     "lyap_serve_submit": (
         ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
     ),
+    "lyap_serve_estimate": (
+        ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    ),
     "lyap_serve_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "lyap_serve_poll": (
         ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, ctypes.POINTER(ResultInfo), ctypes.POINTER(ctypes.c_double)]
@@ -369,6 +372,13 @@ class Server:
         _check(self.lib.lyap_serve_register_seed(self.h, seed.h, ctypes.byref(sid)), "lyap_serve_register_seed")
         self.k[sid.value] = seed.k
         return sid.value
+
+    def estimate(self, seed_id: int, nv: int, want_grad: bool = False) -> int:
+        """Device bytes admission charges for a request of nv vectors."""
+        b = ctypes.c_size_t()
+        _check(self.lib.lyap_serve_estimate(self.h, seed_id, nv, 1 if want_grad else 0, ctypes.byref(b)),
+               "lyap_serve_estimate")
+        return b.value
 
     def submit(self, seed_id: int, v, want_grad: bool = False) -> int:
         va = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1, self.k[seed_id]))

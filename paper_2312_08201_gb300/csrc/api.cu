@@ -79,9 +79,9 @@ extern "C" void lyap_opts_default(lyap_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->tol = 1e-12;
   o->refine_tol = 1e-11;
-  o->inner_tol = 1e-5;
+  o->inner_tol = 1e-4;
   o->maxit = 300;
-  o->m = 30;
+  o->m = 40;
   o->s = 10;
   o->pbar = 30;
   o->batch = 0;

@@ -73,12 +73,19 @@ struct SeedSlot {
   std::thread worker;
 };
 
+// Device bytes a request of nv vectors may hold while it runs: the Krylov
+// workspace (basis, preconditioned basis, recycled pairs, iterate, residual),
+// the small dense matrices, the FP64 solution/residual vectors, and for the
+// mixed path the float-float residual panel (k^2 n pairs of float2) and the
+// Woodbury capacitance inverses. Gradients double the solve part.
 size_t request_bytes(const lyap_seed* sd, const lyap_opts& o, int nv, bool grad) {
-  const size_t N = (size_t)sd->n * sd->k;
+  const size_t n = (size_t)sd->n, k = (size_t)sd->k, N = n * k;
   const size_t vec = o.precision == LYAP_FP64 ? 16 : 8;
-  size_t per = (size_t)(2 * o.m + 2 * o.s + 6) * N * vec + (size_t)(o.m + o.s + 1) * (o.m + o.s + 1) * 8 * 16 +
-               (size_t)4 * N * 16;
+  const size_t LD = (size_t)(o.m + o.s + 1);
+  size_t per = (size_t)(2 * o.m + 2 * o.s + 6) * N * vec + LD * LD * 8 * 16 + (size_t)4 * N * 16;
   if (grad) per *= 2;
+  if (o.precision != LYAP_FP64) per += k * k * n * 16;
+  if (o.pbar > 0) per += (size_t)2 * o.pbar * o.pbar * 8;
   return per * (size_t)nv;
 }
 
@@ -200,6 +207,14 @@ extern "C" int lyap_serve_register_seed(lyap_server* s, lyap_seed* sd, int* seed
   SeedSlot* raw = slot.get();
   s->seeds.push_back(std::move(slot));
   raw->worker = std::thread(worker_loop, raw);
+  return LYAP_OK;
+}
+
+extern "C" int lyap_serve_estimate(lyap_server* s, int seed_id, int nv, int want_grad, size_t* bytes) {
+  if (!s || !bytes || nv <= 0) return LYAP_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (seed_id < 0 || seed_id >= (int)s->seeds.size()) return LYAP_ENOTFOUND;
+  *bytes = request_bytes(s->seeds[seed_id]->sd, s->opts, nv, want_grad != 0);
   return LYAP_OK;
 }
 

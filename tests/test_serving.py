@@ -82,8 +82,11 @@ def test_admission_by_memory_budget(setup):
 
 def test_cancel_and_bad_input(setup):
     ctx, probs, seeds, reqs = setup
-    # room for one 16-vector request (about 9 MiB of workspace) but not two
-    srv = ly.Server(ctx, hbm_budget=sum(s.stats()["resident_bytes"] for s in seeds) + (14 << 20))
+    # room for one 16-vector request but not two
+    probe = ly.Server(ctx)
+    one = probe.estimate(probe.register(seeds[1]), 16)
+    probe.close()
+    srv = ly.Server(ctx, hbm_budget=sum(s.stats()["resident_bytes"] for s in seeds) + one + one // 2)
     sid = srv.register(seeds[1])
     t1 = srv.submit(sid, reqs[1][1])
     t2 = srv.submit(sid, reqs[1][1])
