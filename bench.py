@@ -31,6 +31,12 @@ METRIC = "trace(EX(v)) evals/sec at rel err<=1e-8 vs FP64 path; p50/p99 request 
 WORKLOAD = "chain400 n=800 k=2, 1000 v log-uniform [1e-2,1e2]^2 NN-ordered, Haar-dense"
 FP64_PEAK_FLOPS_PER_CLK_SM = 4.0  # 2 FP64 FMA per clock per SM (1.25 TFLOP/s at 2070 MHz x 152 SMs)
 SMS = 152
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, averaged over the
+# launches of one 1000-vector sweep of the 800-state workload, from one ncu capture of
+# `bench.py --steps 1 --warmup 3 --no-cpu-baseline --profile-sweep` (cold caches: ncu
+# flushes them before every launch). Valid for the kernels as they stand; a kernel
+# change invalidates its entry.
+MEASURED_TRAFFIC_PER_LAUNCH = {"ortho": 95.62e6, "capmv_ff": 78.52e6, "tc_gemm": 17.11e6, "precond": 12.77e6}
 FP32_LANES_PER_SM = 128.0  # FP32 lane-instructions per clock per SM
 L2_FLUSH_BYTES = 256 << 20
 
@@ -46,6 +52,10 @@ def parse():
     ap.add_argument("--pbar", type=int, default=-1, help="TSVD rank of the preconditioner coupling (-1: library default)")
     ap.add_argument("--residual", choices=["ff", "fp64"], default="ff",
                     help="arithmetic of the mixed path's refinement residual")
+    ap.add_argument("--nv", type=int, default=0, help="parameter vectors of the sweep (0: all 1000)")
+    ap.add_argument("--profile-sweep", action="store_true",
+                    help="after the measurements, run one more sweep between cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--cpu-sample", type=int, default=4, help="oracle evaluations in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["precision", "serving", "kernels"], default="precision")
@@ -236,7 +246,7 @@ def run_serving(args, local):
                                 p99_ms=1e3 * float(np.percentile(lat, 99)), requests=len(reqs))
     line = dict(metric=METRIC, value=rates["0.95"]["evals_per_s"], unit="evals/s", n_gpus=1, steps=args.requests,
                 warmup=16, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="bf16x3-gemm/f32-krylov/f64-refine" if prec == ly.BF16_IR else "f64", data="synthetic",
+                dtype="bf16x3-gemm/f32-krylov/ff-refine" if prec == ly.BF16_IR else "f64", data="synthetic",
                 config=dict(workload=f"serving: 8 chain seeds {sizes} masses x2, k in {{2,3,4}}, 64 v per request, "
                                      "Poisson arrivals", n=[p.n for p in probs], k=[p.k for p in probs]),
                 saturation_evals_per_s=sat, rates=rates, seed_factor_s=t_factor,
@@ -246,10 +256,13 @@ def run_serving(args, local):
 
 # ------------------------------------------------------------ kernel probe
 def run_kernel_probe(args, local):
-    """Both capacitance operators on a full batch: T(v) applied to 1000
+    """The capacitance operators on a full batch: T(v) applied to 1000
     random inputs of the 800-state seed with the tensor-core operator (panel,
-    tcgen05 GEMM, epilogue) and with the FP64 kernel; CUDA-event timing per
-    kernel for the roofline. Used for ncu captures of full launches."""
+    tcgen05 GEMM, epilogue), the float-float kernel and the FP64 kernel;
+    CUDA-event timing per kernel for the roofline, and the float-float
+    operator's error against the FP64 one. One more application of each
+    operator runs between cudaProfilerStart/Stop, for ncu captures of full
+    launches (--profile-from-start off)."""
     import numpy as np
     import torch
 
@@ -267,13 +280,23 @@ def run_kernel_probe(args, local):
     w = torch.tensor(rng.standard_normal((len(vs), p.k, p.n, 2)), dtype=torch.float64, device=dev)
     for _ in range(2):
         ly.test_apply(seed, v, w, ly.BF16_IR)
-        ly.test_apply(seed, v, w, ly.FP64)
+        ly.test_apply(seed, v, w, ly.TEST_FF)
+        y64 = ly.test_apply(seed, v, w, ly.FP64)
     ly.prof_enable(True)
     for _ in range(max(1, args.steps)):
         ly.test_apply(seed, v, w, ly.BF16_IR)
+        yff = ly.test_apply(seed, v, w, ly.TEST_FF)
     ly.test_apply(seed, v, w, ly.FP64)
     prof, launches = ly.prof_read()
     ly.prof_enable(False)
+    ff_err = float(((yff - y64).flatten(1).norm(dim=1) / y64.flatten(1).norm(dim=1)).max())
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    ly.test_apply(seed, v, w, ly.BF16_IR)
+    ly.test_apply(seed, v, w, ly.TEST_FF)
+    ly.test_apply(seed, v, w, ly.FP64)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     pk, how = peaks()
     out = {}
     for name, d in prof.items():
@@ -282,7 +305,8 @@ def run_kernel_probe(args, local):
                          tflops=d["flops"] / sec / 1e12 if d["flops"] else None,
                          gbs=d["bytes"] / sec / 1e9 if d["bytes"] else None)
     print(json.dumps(dict(probe="operators on 1000 systems, 800-state seed", kernels=out,
-                          bf16_peak_tflops=pk["bf16_tflops"], peak_source=how)), flush=True)
+                          ff_max_rel_err_vs_fp64=ff_err, bf16_peak_tflops=pk["bf16_tflops"],
+                          peak_source=how)), flush=True)
 
 
 # -------------------------------------------------------------------- ours
@@ -314,6 +338,8 @@ def main():
 
     ly.build()
     p, vs = workload_precision()
+    if args.nv:
+        vs = vs[: args.nv]
     nv, k = vs.shape
     ctx = ly.Context(local)
     seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
@@ -428,6 +454,12 @@ def main():
             roof = dict(bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak, traffic=None,
                         kernel=dom_name, peak_source=f"hbm copy ({how})", launches=d["launches"],
                         avg_launch_ms=d["total_ms"] / d["launches"])
+    if roof is not None:
+        d = prof[dom_name]
+        roof["algorithmic_bytes_per_launch"] = d["bytes"] / d["launches"]
+        if dom_name in MEASURED_TRAFFIC_PER_LAUNCH and precision == "bf16_ir" and nv == 1000:
+            roof["traffic"] = MEASURED_TRAFFIC_PER_LAUNCH[dom_name]
+            roof["traffic_note"] = "DRAM bytes per launch from one ncu capture of a full sweep (cold caches)"
     kernels = {kname: dict(launches=v["launches"], ms=round(v["total_ms"], 3),
                            share=round(v["total_ms"] / max(1e-9, sum(x["total_ms"] for x in prof.values())), 4))
                for kname, v in prof.items()}
@@ -459,6 +491,12 @@ def main():
                                     max_rel_err_gpu_vs_oracle=err)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if args.profile_sweep:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        seed.trace_EX(v_dev, **opts)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     if dist:
         dist.destroy_process_group()
 
