@@ -94,14 +94,16 @@ __global__ void __launch_bounds__(32) k_ritz(int m, int smax, int s_cur, int s_n
     if (sd::lane() == 0) ok[b] = 0;
     return;
   }
-  // shared matrices use leading dimension LS = m + 1 >= re (re x me at most)
+  // shared matrices use leading dimension LS = m + 1 >= re (re x me at most).
+  // K is formed in place of Qg^H Fhat, and Q takes the space of Gf once its
+  // triangular factor has been used.
   const int LS = m + 1;
   extern __shared__ float2 smf[];
   float2* Gf = smf;                          // LS x LS
-  float2* Ff = Gf + (size_t)LS * LS;         // LS x LS -> Qg^H Fhat
-  float2* K = Ff + (size_t)LS * LS;          // LS x LS
-  float2* Q = K + (size_t)LS * LS;           // LS x LS
-  float2* vt = Q + (size_t)LS * LS;          // LS
+  float2* Ff = Gf + (size_t)LS * LS;         // LS x LS -> Qg^H Fhat -> K
+  float2* K = Ff;
+  float2* Q = Gf;                            // after the triangular solve
+  float2* vt = Ff + (size_t)LS * LS;         // LS
   float2* Yz = vt + LS;                      // LS x 16
   float2* Xf = Yz + (size_t)LS * 16;         // LS x 16
   int* sel = reinterpret_cast<int*>(Xf + (size_t)LS * 16);  // 16
@@ -140,9 +142,7 @@ __global__ void __launch_bounds__(32) k_ritz(int m, int smax, int s_cur, int s_n
   }
   sd::wsync();
   sd::householder_qr_apply<float2>(re, me, Gf, LS, Ff, LS, me, vt);
-  for (int e = sd::lane(); e < me * me; e += 32) K[(e % me) + (size_t)(e / me) * LS] = Ff[(e % me) + (size_t)(e / me) * LS];
-  sd::wsync();
-  sd::trsm_upper_left<float2>(me, me, Gf, LS, K, LS);
+  sd::trsm_upper_left<float2>(me, me, Gf, LS, K, LS);  // K = Rg^{-1} (Qg^H Fhat), in place
   bool fin = true;
   for (int e = sd::lane(); e < me * me; e += 32) {
     const float2 v = K[(e % me) + (size_t)(e / me) * LS];
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(32) k_ritz(int m, int smax, int s_cur, int s_n
 
 size_t ritz_smem_bytes(int m, int /*smax*/) {
   const int LS = m + 1;
-  return sizeof(float2) * ((size_t)4 * LS * LS + LS + (size_t)2 * LS * 16) + 16 * sizeof(int);
+  return sizeof(float2) * ((size_t)2 * LS * LS + LS + (size_t)2 * LS * 16) + 16 * sizeof(int);
 }
 
 __global__ void k_chol_rinv(int s, const int* __restrict__ list, const int* __restrict__ count,

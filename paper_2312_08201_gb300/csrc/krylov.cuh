@@ -9,6 +9,8 @@
 // matrix is FP64 and summed in a fixed order, so results do not depend on
 // which other systems share the batch.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "cplx.cuh"
 #include "smalldense.cuh"
 
@@ -345,46 +347,77 @@ __global__ void __launch_bounds__(NT) k_update_xr(int N, int m, int smax, int s_
 }
 
 // ------------------------------------------------- batched Gram: A^H B
-// out_b (na x nb, ld = ldo, system stride os) = [A segs]^H [B segs], one CTA
-// per system, na, nb <= 64. K tiles of TK elements are staged with TK
-// consecutive threads reading one vector (coalesced); each thread owns up to
-// four 2 x 2 output tiles (one shared load per complex multiply-add), sums
-// each K tile in the vector precision and accumulates in FP64.
+// out_b (na x nb, ld = ldo, system stride os) = [A segs]^H [B segs],
+// na, nb <= 64. Each system is served by a cluster of gridDim.y CTAs (GT
+// threads each; 1 for full batches, GSPLIT when few systems need a Gram)
+// that split the vector length: CTA r sums elements
+// [r N / gridDim.y, (r+1) N / gridDim.y), and CTA 0 adds the partial Grams of
+// the cluster in rank order through distributed shared memory
+// (deterministic).
+// Within a CTA, K tiles are staged with consecutive threads reading one
+// vector (coalesced); the tile length grows when the matrices are narrow.
+// Outputs are 2 x 2 tiles; when there are fewer tiles than threads, Q
+// consecutive threads share a tile and split each K tile (their partial
+// sums meet through shuffles). Each K tile is summed in the vector precision
+// and accumulated in FP64.
+constexpr int GT = 256, GSPLIT = 8, GK_ELEMS = 2048;  // staged elements per operand
+
+// dynamic shared memory of k_gram: two staging buffers, reused for the na x nb partial Gram
 template <typename T2>
-__global__ void __launch_bounds__(NT) k_gram(int N, const int* __restrict__ list, const int* __restrict__ count,
-                                            Seg2<T2> A, Seg2<T2> Bm, double2* __restrict__ out, int ldo,
-                                            size_t os) {
-  constexpr int TK = 16, MAXC = 64;
-  __shared__ T2 sa[TK][MAXC + 1], sb[TK][MAXC + 1];
+__host__ __device__ constexpr size_t gram_smem_bytes() {
+  return (2 * GK_ELEMS * sizeof(T2) > 64 * 64 * sizeof(double2)) ? 2 * GK_ELEMS * sizeof(T2)
+                                                                  : 64 * 64 * sizeof(double2);
+}
+
+template <typename T2>
+__global__ void __launch_bounds__(GT)
+    k_gram(int N, const int* __restrict__ list, const int* __restrict__ count, Seg2<T2> A, Seg2<T2> Bm,
+           double2* __restrict__ out, int ldo, size_t os) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) unsigned char gsm[];
+  T2* sa = reinterpret_cast<T2*>(gsm);
+  T2* sb = sa + GK_ELEMS;
+  double2* part = reinterpret_cast<double2*>(gsm);  // after the K loop
+  cg::cluster_group cluster = cg::this_cluster();
   const int slot = blockIdx.x;
-  if (slot >= *count) return;
+  if (slot >= *count) return;  // uniform over the cluster (same slot)
+  const int rank = (int)cluster.block_rank();
+  const int nsplit = (int)gridDim.y;  // the launch makes the cluster span gridDim.y
   const int b = list[slot];
   const int na = A.cnt(b), nbb = Bm.cnt(b);
-  const int ta = (na + 1) / 2, tb = (nbb + 1) / 2, ntile = ta * tb;  // <= 1024 = 4 NT
+  const int ta = (na + 1) / 2, tb = (nbb + 1) / 2, ntile = ta * tb;  // <= 1024 = 4 GT
+  int Q = 1;
+  while (Q < 32 && ntile * Q * 2 <= GT) Q *= 2;
+  const int q = threadIdx.x % Q, tslot = threadIdx.x / Q, tstride = GT / Q;
+  const int cmax = max(2 * ta, 2 * tb);
+  const int ld = cmax + 1;  // padded row of a staged K element
+  int tk = GK_ELEMS / ld;
+  if (tk >= 32) tk -= tk % 32;
+  const int e_beg = (int)((long long)N * rank / nsplit), e_end = (int)((long long)N * (rank + 1) / nsplit);
   const T2 z = cvt<T2>(make_double2(0.0, 0.0));
   double2 acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = make_double2(0.0, 0.0);
-  const int cmax = max(2 * ta, 2 * tb);
-  for (int e0 = 0; e0 < N; e0 += TK) {
-    for (int q = threadIdx.x; q < TK * cmax; q += NT) {
-      const int c = q / TK, l = q % TK;
-      const int e = e0 + l;
-      sa[l][c] = (c < na && e < N) ? A.vec(b, c)[e] : z;
-      sb[l][c] = (c < nbb && e < N) ? Bm.vec(b, c)[e] : z;
+  for (int e0 = e_beg; e0 < e_end; e0 += tk) {
+    for (int e = threadIdx.x; e < tk * cmax; e += GT) {
+      const int c = e / tk, l = e % tk;
+      const int ee = e0 + l;
+      sa[l * ld + c] = (c < na && ee < e_end) ? A.vec(b, c)[ee] : z;
+      sb[l * ld + c] = (c < nbb && ee < e_end) ? Bm.vec(b, c)[ee] : z;
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int tile = threadIdx.x + u * NT;
+      const int tile = tslot + u * tstride;
       if (tile < ntile) {
         const int i0 = 2 * (tile % ta), j0 = 2 * (tile / ta);
         T2 t00 = z, t01 = z, t10 = z, t11 = z;
-#pragma unroll
-        for (int l = 0; l < TK; ++l) {
-          const T2 a0 = sa[l][i0], a1 = sa[l][i0 + 1], b0 = sb[l][j0], b1 = sb[l][j0 + 1];
+        for (int l = q; l < tk; l += Q) {
+          const T2* ra = sa + l * ld;
+          const T2* rb = sb + l * ld;
+          const T2 a0 = ra[i0], a1 = ra[i0 + 1], b0 = rb[j0], b1 = rb[j0 + 1];
           t00 = cadd(t00, cjmul(a0, b0));
           t10 = cadd(t10, cjmul(a1, b0));
           t01 = cadd(t01, cjmul(a0, b1));
@@ -398,19 +431,47 @@ __global__ void __launch_bounds__(NT) k_gram(int N, const int* __restrict__ list
     }
     __syncthreads();
   }
+  // partial sums of the Q threads of a tile (consecutive lanes of one warp)
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int tile = threadIdx.x + u * NT;
-    if (tile < ntile) {
-      const int i0 = 2 * (tile % ta), j0 = 2 * (tile / ta);
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int i = i0 + (v & 1), jj = j0 + (v >> 1);
-        if (i < na && jj < nbb) out[(size_t)b * os + i + (size_t)jj * ldo] = acc[u][v];
+    for (int v = 0; v < 4; ++v)
+      for (int o = Q / 2; o > 0; o >>= 1) {
+        acc[u][v].x += __shfl_xor_sync(0xffffffffu, acc[u][v].x, o);
+        acc[u][v].y += __shfl_xor_sync(0xffffffffu, acc[u][v].y, o);
+      }
+  // this CTA's partial Gram into its shared memory (the staging buffers are free)
+  if (q == 0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int tile = tslot + u * tstride;
+      if (tile < ntile) {
+        const int i0 = 2 * (tile % ta), j0 = 2 * (tile / ta);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int i = i0 + (v & 1), jj = j0 + (v >> 1);
+          if (i < na && jj < nbb) part[i + jj * na] = acc[u][v];
+        }
       }
     }
   }
+  cluster.sync();
+  if (rank == 0) {
+    for (int e = threadIdx.x; e < na * nbb; e += GT) {
+      double2 sum = make_double2(0.0, 0.0);
+      for (int r = 0; r < nsplit; ++r) sum = cadd(sum, cluster.map_shared_rank(part, r)[e]);
+      out[(size_t)b * os + (e % na) + (size_t)(e / na) * ldo] = sum;
+    }
+  }
+  cluster.sync();  // keep every CTA's shared memory alive until rank 0 has read it
 }
+
+// Launch of k_gram for up to B listed systems, of which about `expect` are
+// listed; clusters of GSPLIT CTAs per system when that leaves the GPU
+// underfilled (sets the shared-memory limit once).
+template <typename T2>
+int launch_gram(int N, const int* list, const int* count, int B, int expect, const Seg2<T2>& A,
+                const Seg2<T2>& Bm, double2* out, int ldo, size_t os, cudaStream_t st);
 
 // ------------------------------------- batched tall-skinny times small matrix
 // Out_b[:, c] = sum_i In_b[i] M_b[i, c],  c < ncols (<= 16), i < In.cnt(b).

@@ -263,25 +263,22 @@ __device__ inline int hqr(int m, T2* H, int ldh, T2* Q, int ldq, int maxit) {
       for (int j = j0 + lane(); j < m; j += 32) {
         T2 top = H[kk + (size_t)j * ldh], bot = H[kk + 1 + (size_t)j * ldh];
         H[kk + (size_t)j * ldh] = cadd(cscale(top, c), cmul(s, bot));
-        H[kk + 1 + (size_t)j * ldh] = csub(cscale(bot, c), cjmul(s, top));
+        // the rotation annihilates the bulge H[kk+1, kk-1]: store the exact zero
+        H[kk + 1 + (size_t)j * ldh] = (kk > l && j == kk - 1) ? zero2<T2>() : csub(cscale(bot, c), cjmul(s, top));
       }
       wsync();
       int imax = kk + 2 < hi ? kk + 2 : hi;
-      for (int i = lane(); i <= imax; i += 32) {
-        T2 lft = H[i + (size_t)kk * ldh], rgt = H[i + (size_t)(kk + 1) * ldh];
-        H[i + (size_t)kk * ldh] = cadd(cscale(lft, c), cmul(cconj(s), rgt));
-        H[i + (size_t)(kk + 1) * ldh] = csub(cscale(rgt, c), cmul(s, lft));
-      }
       for (int i = lane(); i < m; i += 32) {
+        if (i <= imax) {
+          T2 lft = H[i + (size_t)kk * ldh], rgt = H[i + (size_t)(kk + 1) * ldh];
+          H[i + (size_t)kk * ldh] = cadd(cscale(lft, c), cmul(cconj(s), rgt));
+          H[i + (size_t)(kk + 1) * ldh] = csub(cscale(rgt, c), cmul(s, lft));
+        }
         T2 lft = Q[i + (size_t)kk * ldq], rgt = Q[i + (size_t)(kk + 1) * ldq];
         Q[i + (size_t)kk * ldq] = cadd(cscale(lft, c), cmul(cconj(s), rgt));
         Q[i + (size_t)(kk + 1) * ldq] = csub(cscale(rgt, c), cmul(s, lft));
       }
       wsync();
-      if (kk > l) {
-        if (lane() == 0) H[kk + 1 + (size_t)(kk - 1) * ldh] = zero2<T2>();
-        wsync();
-      }
     }
   }
   return 0;

@@ -253,7 +253,7 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     // CholQR2: C = AU R^{-1}, U = Ut R^{-1}
     for (int pass = 0; pass < 2; ++pass) {
       auto cseg = seg2(seg(ws.C.p, ss, NS, s), seg(ws.C.p, ss, NS, 0));
-      kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lchunk, cchunk, cseg, cseg, ws.Gs.p, s, (size_t)smax * smax); lyap_count_launch();
+      LY_TRY(kry::launch_gram<T2>(N, Lchunk, cchunk, B, B, cseg, cseg, ws.Gs.p, s, (size_t)smax * smax, st));
       kry::k_chol_rinv<<<(B * 32 + 255) / 256, 256, 0, st>>>(s, Lchunk, cchunk, ws.Gs.p, (size_t)smax * smax,
                                                              ws.Rinv.p, ws.Racc.p, ws.Rtmp.p, pass, ws.ok.p); lyap_count_launch();
       if (pass == 0) {
@@ -335,7 +335,8 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     // ---- cycle end -----------------------------------------------------
     {
       const int ph_ = prof_begin(PK_CYCLE, st);
-      kry::k_cycle_solve<<<g1, 256, 0, st>>>(m, smax, s_cur, Lstart, cstart, ws.H.p, ws.H0.p, ws.Bk.p, ws.g.p,
+      // one thread per system in CTAs of 8: the serial FP64 solves spread over all SMs
+      kry::k_cycle_solve<<<(B + 7) / 8, 8, 0, st>>>(m, smax, s_cur, Lstart, cstart, ws.H.p, ws.H0.p, ws.Bk.p, ws.g.p,
                                            ws.beta.p, ws.jstop.p, ws.coefY.p, ws.coefR.p); lyap_count_launch();
       prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
     }
@@ -348,6 +349,15 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     }
     k_add_iters<<<g1, 256, 0, st>>>(Lstart, cstart, ws.jstop.p, ws.iters.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
+    // ---- next cycle: systems still running (flag > 0). The count is read
+    // here, before the recycle update, so that the update's launches are
+    // sized by it: at most chunk_count + 1 systems (the continuing ones and
+    // the chunk's last system) need harmonic-Ritz vectors.
+    kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.flag.p, Lchunk, cchunk); lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    LY_CUDA(cudaMemcpyAsync(&chunk_count, cchunk, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LY_CUDA(cudaStreamSynchronize(st));
+    const int Bw = std::min(B, chunk_count + 1);
     // ---- recycle update (harmonic Ritz) ----------------------------------
     if (s > 0) {
       auto Vh = seg2(seg(ws.C.p, css, NS, s_cur), segd(ws.V.p, (size_t)(m + 1) * NS, NS, ws.jstop.p, 1));
@@ -360,12 +370,12 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
       lyap_count_launch();
       {
         const int ph_ = prof_begin(PK_GRAM, st);
-        kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lwant, cwant, Vh, Wh, ws.F.p, LD, (size_t)LD * LD); lyap_count_launch();
+        LY_TRY(kry::launch_gram<T2>(N, Lwant, cwant, Bw, Bw, Vh, Wh, ws.F.p, LD, (size_t)LD * LD, st));
         prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
       }
       if (s_cur > 0) {
         auto Us = seg2(seg(ws.U.p, css, NS, s_cur), seg(ws.U.p, css, NS, 0));
-        kry::k_gram<T2><<<B, kry::NT, 0, st>>>(N, Lwant, cwant, Us, Us, ws.UU.p, smax, (size_t)smax * smax); lyap_count_launch();
+        LY_TRY(kry::launch_gram<T2>(N, Lwant, cwant, Bw, Bw, Us, Us, ws.UU.p, smax, (size_t)smax * smax, st));
       }
       {
         const int ph_ = prof_begin(PK_RITZ, st);
@@ -380,7 +390,7 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
         });
         LY_CUDA(rc_attr);
       }
-      kry::k_ritz<<<B, 32, rsm, st>>>(m, smax, s_cur, s, Lwant, cwant, ws.jstop.p, ws.H0.p,
+      kry::k_ritz<<<Bw, 32, rsm, st>>>(m, smax, s_cur, s, Lwant, cwant, ws.jstop.p, ws.H0.p,
                                                         ws.Bk.p, ws.F.p, ws.UU.p, ws.work.p, ws.wstride, ws.Pu.p,
                                                         ws.Qc.p, ws.ok.p); lyap_count_launch();
         prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
@@ -391,19 +401,19 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
         kry::k_compact<<<1, 1024, 0, st>>>(Lwant, cwant, ws.ok.p, Lritz, critz); lyap_count_launch();
         {
           const int ph_ = prof_begin(PK_TSMM, st);
-          kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lritz, critz, Wh, ws.Pu.p, LD,
+          kry::k_tsmm<T2, T2><<<dim3(gx(NS), Bw), kry::NT, 0, st>>>(N, Lritz, critz, Wh, ws.Pu.p, LD,
                                                                  (size_t)LD * 16, s, ws.U.p, css, NS, 0); lyap_count_launch();
           prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
         }
         {
           const int ph_ = prof_begin(PK_TSMM, st);
-          kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lritz, critz, Vh, ws.Qc.p, LD,
+          kry::k_tsmm<T2, T2><<<dim3(gx(NS), Bw), kry::NT, 0, st>>>(N, Lritz, critz, Vh, ws.Qc.p, LD,
                                                                  (size_t)LD * 16, s, ws.C.p, css, NS, 0); lyap_count_launch();
           prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
         }
         k_mark_rec<<<g1, 256, 0, st>>>(Lwant, cwant, ws.ok.p, ws.hasrec.p); lyap_count_launch();
         if (s_cur == 0) {
-          k_zero_failed<T2><<<dim3(gx(NS * s), B), kry::NT, 0, st>>>(NS, s, Lwant, cwant, ws.ok.p, ws.C.p,
+          k_zero_failed<T2><<<dim3(gx(NS * s), Bw), kry::NT, 0, st>>>(NS, s, Lwant, cwant, ws.ok.p, ws.C.p,
                                                                      ws.U.p, css);
           lyap_count_launch();
         }
@@ -411,11 +421,6 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
       }
       s_cur = s;
     }
-    // ---- next cycle: systems still running (flag > 0) ---------------------
-    kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.flag.p, Lchunk, cchunk); lyap_count_launch();
-    LY_CUDA(cudaGetLastError());
-    LY_CUDA(cudaMemcpyAsync(&chunk_count, cchunk, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LY_CUDA(cudaStreamSynchronize(st));
   }
 
   // ---- report and hand the recycle space to the next chunk ----------------
@@ -447,6 +452,36 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
   }
   return LYAP_OK;
 }
+
+namespace kry {
+template <typename T2>
+int launch_gram(int N, const int* list, const int* count, int B, int expect, const Seg2<T2>& A, const Seg2<T2>& Bm,
+                double2* out, int ldo, size_t os, cudaStream_t st) {
+  static std::once_flag once;
+  static cudaError_t rc = cudaSuccess;
+  std::call_once(once, [] {
+    rc = cudaFuncSetAttribute(k_gram<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem_bytes<T2>());
+  });
+  LY_CUDA(rc);
+  // split each system over a cluster of CTAs only while the systems alone leave SMs idle
+  const int split = expect * 4 <= 152 ? GSPLIT : 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(B, split, 1);
+  cfg.blockDim = dim3(GT, 1, 1);
+  cfg.dynamicSmemBytes = gram_smem_bytes<T2>();
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = split;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  LY_CUDA(cudaLaunchKernelEx(&cfg, k_gram<T2>, N, list, count, A, Bm, out, ldo, os));
+  lyap_count_launch();
+  return LYAP_OK;
+}
+}  // namespace kry
 
 template struct KrylovWS<double2>;
 template struct KrylovWS<float2>;
