@@ -34,38 +34,55 @@ __global__ void k_compact(const int* __restrict__ in_list, const int* __restrict
   if (threadIdx.x == blockDim.x - 1) *out_count = sc[threadIdx.x];
 }
 
-__global__ void k_cycle_solve(int m, int smax, int s_cur, const int* __restrict__ list,
-                              const int* __restrict__ count, const double2* __restrict__ H,
-                              const double2* __restrict__ H0, const double2* __restrict__ Bk,
-                              const double2* __restrict__ g, const double* __restrict__ beta,
-                              const int* __restrict__ jstop, double2* __restrict__ coefY, double2* __restrict__ coefR) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= *count) return;
+// One warp per system (CS_WARPS warps per CTA). Back substitution
+// R y2 = g (R = the rotated Hessenberg H, js x js upper triangular) by
+// columns: lane i keeps x_i for rows i and i + 32; once y2[l] is final, every
+// row above it subtracts H[i, l] y2[l] in parallel. Then
+// cy = -Bk y2 (the recycled part) and cr = beta e1 - H0 y2 (the coefficients
+// of the new residual in [C V]).
+__global__ void __launch_bounds__(32 * CS_WARPS) k_cycle_solve(
+    int m, int smax, int s_cur, const int* __restrict__ list, const int* __restrict__ count,
+    const double2* __restrict__ H, const double2* __restrict__ H0, const double2* __restrict__ Bk,
+    const double2* __restrict__ g, const double* __restrict__ beta, const int* __restrict__ jstop,
+    double2* __restrict__ coefY, double2* __restrict__ coefR) {
+  __shared__ double2 ys[CS_WARPS][64];
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slot = blockIdx.x * CS_WARPS + wi;
+  if (slot >= *count) return;  // whole warp
   const int b = list[slot];
   const int js = jstop[b];
+  const size_t ldh = (size_t)(m + 1);
   const double2* Hb = H + (size_t)b * (m + 1) * m;
   const double2* H0b = H0 + (size_t)b * (m + 1) * m;
   const double2* gb = g + (size_t)b * (m + 1);
   double2* cy = coefY + (size_t)b * (m + smax + 1);
   double2* cr = coefR + (size_t)b * (m + 1);
   double2* y2 = cy + s_cur;
-  for (int i = js - 1; i >= 0; --i) {
-    double2 x = gb[i];
-    for (int l = i + 1; l < js; ++l) x = csub(x, cmul(Hb[i + (size_t)l * (m + 1)], y2[l]));
-    double2 d = Hb[i + (size_t)i * (m + 1)];
-    y2[i] = cabs2(d) > 0 ? cdiv(x, d) : make_double2(0.0, 0.0);
+  double2* y = ys[wi];
+  const double2 zero = make_double2(0.0, 0.0);
+  double2 x0 = lane < js ? gb[lane] : zero, x1 = lane + 32 < js ? gb[lane + 32] : zero;
+  for (int l = js - 1; l >= 0; --l) {
+    if (lane == (l & 31)) {
+      const double2 xl = l < 32 ? x0 : x1;
+      const double2 d = Hb[l + l * ldh];
+      y[l] = cabs2(d) > 0 ? cdiv(xl, d) : zero;
+    }
+    __syncwarp();
+    const double2 yl = y[l];
+    if (lane < l) x0 = csub(x0, cmul(Hb[lane + l * ldh], yl));
+    if (lane + 32 < l) x1 = csub(x1, cmul(Hb[lane + 32 + l * ldh], yl));
   }
+  __syncwarp();
+  for (int l = lane; l < js; l += 32) y2[l] = y[l];
   const double2* Bb = Bk + (size_t)b * smax * m;
-  for (int q = 0; q < s_cur; ++q) {
-    double2 x = make_double2(0.0, 0.0);
-    for (int l = 0; l < js; ++l) x = cfma(Bb[q + (size_t)l * smax], y2[l], x);
+  for (int q = lane; q < s_cur; q += 32) {
+    double2 x = zero;
+    for (int l = 0; l < js; ++l) x = cfma(Bb[q + (size_t)l * smax], y[l], x);
     cy[q] = cscale(x, -1.0);
   }
-  for (int i = 0; i <= js; ++i) {
+  for (int i = lane; i <= js; i += 32) {
     double2 x = make_double2(i == 0 ? beta[b] : 0.0, 0.0);
-    for (int l = 0; l < js; ++l) {
-      if (i <= l + 1) x = csub(x, cmul(H0b[i + (size_t)l * (m + 1)], y2[l]));
-    }
+    for (int l = (i > 0 ? i - 1 : 0); l < js; ++l) x = csub(x, cmul(H0b[i + l * ldh], y[l]));
     cr[i] = x;
   }
 }
@@ -213,6 +230,180 @@ __global__ void __launch_bounds__(32) k_ritz(int m, int smax, int s_cur, int s_n
 size_t ritz_smem_bytes(int m, int /*smax*/) {
   const int LS = m + 1;
   return sizeof(float2) * ((size_t)2 * LS * LS + LS + (size_t)2 * LS * 16) + 16 * sizeof(int);
+}
+
+// Recycle start of the FP32 solves in one CTA per system (see krylov.cuh).
+// Shared memory: small FP64 matrices (ld 16), the FP32 copies of the
+// triangular factors, reduction scratch, then C_b (s x N, [c][e]).
+__global__ void __launch_bounds__(RS_T) k_recstart32(int n, int k, int s, const int* __restrict__ list,
+                                                    const int* __restrict__ count, const float2* __restrict__ Ut,
+                                                    const float2* __restrict__ C0Ut, const double* __restrict__ vinv,
+                                                    float2* __restrict__ C, float2* __restrict__ U, size_t ss,
+                                                    float2* __restrict__ X, float2* __restrict__ R,
+                                                    int* __restrict__ ok) {
+  extern __shared__ __align__(16) unsigned char rsm[];
+  double2* G = reinterpret_cast<double2*>(rsm);  // 16 x 16
+  double2* Ri = G + 256;
+  double2* Ra = Ri + 256;
+  double2* Tm = Ra + 256;
+  float2* Rf = reinterpret_cast<float2*>(Tm + 256);  // 16 x 16 FP32 copy
+  float* red = reinterpret_cast<float*>(Rf + 256);   // (RS_T / 32) x 32
+  float2* coef = reinterpret_cast<float2*>(red + (RS_T / 32) * 32);  // 16
+  int* fail = reinterpret_cast<int*>(coef + 16);                     // 4 ints (keeps 16-byte alignment)
+  float2* Cs = reinterpret_cast<float2*>(fail + 4);                  // s x N
+  const int slot = blockIdx.x;
+  if (slot >= *count) return;
+  const int b = list[slot];
+  const int N = n * k;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* vb = vinv + (size_t)b * k;
+  // C = Ut D(v)^{-1} - C0 Ut = T(v) Ut
+  for (int idx = tid; idx < s * N; idx += RS_T) {
+    const int e = idx % N, t = e / n;
+    const float2 u = Ut[idx], cu = C0Ut[idx];
+    const float vi = (float)vb[t];
+    Cs[idx] = make_float2(u.x * vi - cu.x, u.y * vi - cu.y);
+  }
+  if (tid == 0) fail[0] = 0;
+  __syncthreads();
+  const int npair = s * (s + 1) / 2;
+  int Q = 1;
+  while (Q < 32 && npair * Q * 2 <= RS_T) Q *= 2;
+  for (int pass = 0; pass < 2; ++pass) {
+    // Gram G = C^H C (upper pairs i <= j, Q threads per pair over a strided
+    // share of the elements; FP32 partial sums of 32 elements, FP64 total)
+    {
+      const int p = tid / Q, q = tid % Q;
+      double2 acc = make_double2(0.0, 0.0);
+      int i = 0, j = 0;
+      if (p < npair) {
+        int rem = p;
+        while (rem >= s - i) {
+          rem -= s - i;
+          ++i;
+        }
+        j = i + rem;
+        const float2* ci = Cs + (size_t)i * N;
+        const float2* cj = Cs + (size_t)j * N;
+        for (int e0 = q; e0 < N; e0 += 32 * Q) {
+          float2 t = make_float2(0.f, 0.f);
+          const int e1 = min(N, e0 + 32 * Q);
+          for (int e = e0; e < e1; e += Q) t = cadd(t, cjmul(ci[e], cj[e]));
+          acc = cadd(acc, make_double2(t.x, t.y));
+        }
+      }
+      for (int o = Q / 2; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (p < npair && q == 0) {  // G[i][j] = sum conj(C_i) C_j (column-major, ld 16); Hermitian
+        G[i + j * 16] = acc;
+        G[j + i * 16] = cconj(acc);
+      }
+    }
+    __syncthreads();
+    // Cholesky G = L L^H, Ri = L^{-H}, Ra = Ri (first pass) or Ra Ri (second), FP32 copy of Ri
+    if (warp == 0) {
+      if (sd::cholesky(s, G, 16)) {
+        if (lane == 0) fail[0] = 1;
+      } else {
+        for (int e = lane; e < s * s; e += 32) Ri[(e % s) + (e / s) * 16] = make_double2((e % s) == (e / s) ? 1.0 : 0.0, 0.0);
+        sd::wsync();
+        sd::trsm_lower_h_left(s, s, G, 16, Ri, 16);
+        if (pass == 0) {
+          for (int e = lane; e < s * s; e += 32) Ra[(e % s) + (e / s) * 16] = Ri[(e % s) + (e / s) * 16];
+        } else {
+          sd::gemm_nn(s, s, s, Ra, 16, Ri, 16, Tm, 16);
+          for (int e = lane; e < s * s; e += 32) Ra[(e % s) + (e / s) * 16] = Tm[(e % s) + (e / s) * 16];
+        }
+        for (int e = lane; e < s * s; e += 32) {
+          const double2 r = Ri[(e % s) + (e / s) * 16];
+          Rf[(e % s) + (e / s) * 16] = make_float2((float)r.x, (float)r.y);
+        }
+      }
+    }
+    __syncthreads();
+    if (fail[0]) {
+      if (tid == 0) ok[b] = 0;
+      return;
+    }
+    // C := C Ri, element by element (all s values of an element in registers)
+    for (int e = tid; e < N; e += RS_T) {
+      float2 v[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = c < s ? Cs[(size_t)c * N + e] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        if (jj < s) {
+          float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            if (c <= jj) o = cfma(v[c], Rf[c + jj * 16], o);  // Ri is upper triangular
+          Cs[(size_t)jj * N + e] = o;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // write C; coef = C^H r
+  float acc[32];
+#pragma unroll
+  for (int u = 0; u < 32; ++u) acc[u] = 0.f;
+  for (int e = tid; e < N; e += RS_T) {
+    const float2 re = R[(size_t)b * N + e];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      if (c < s) {
+        const float2 ce = Cs[(size_t)c * N + e];
+        C[(size_t)b * ss + (size_t)c * N + e] = ce;
+        acc[2 * c] += ce.x * re.x + ce.y * re.y;
+        acc[2 * c + 1] += ce.x * re.y - ce.y * re.x;
+      }
+    }
+  }
+  warp_reduce_scatter32<float>(acc);
+  red[warp * 32 + lane] = acc[0];
+  // FP32 copy of Ra for U = Ut Ra
+  for (int e = tid; e < 256; e += RS_T) {
+    const double2 r = Ra[e];
+    Rf[e] = make_float2((float)r.x, (float)r.y);
+  }
+  __syncthreads();
+  if (tid < 32) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < RS_T / 32; ++w) v += red[w * 32 + tid];
+    const float im = __shfl_xor_sync(0xffffffffu, v, 1);
+    if ((tid & 1) == 0 && (tid >> 1) < s) coef[tid >> 1] = make_float2(v, im);
+  }
+  __syncthreads();
+  // U = Ut Ra;  x += U coef;  r -= C coef
+  for (int e = tid; e < N; e += RS_T) {
+    float2 ut[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) ut[c] = c < s ? Ut[(size_t)c * N + e] : make_float2(0.f, 0.f);
+    float2 xs = X[(size_t)b * N + e], rs = R[(size_t)b * N + e];
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      if (jj < s) {
+        float2 uj = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (c <= jj) uj = cfma(ut[c], Rf[c + jj * 16], uj);  // Ra is upper triangular
+        U[(size_t)b * ss + (size_t)jj * N + e] = uj;
+        xs = cfma(uj, coef[jj], xs);
+        rs = csub(rs, cmul(Cs[(size_t)jj * N + e], coef[jj]));
+      }
+    }
+    X[(size_t)b * N + e] = xs;
+    R[(size_t)b * N + e] = rs;
+  }
+  if (tid == 0) ok[b] = 1;
+}
+
+size_t recstart32_smem_bytes(int s, int N) {
+  return sizeof(double2) * 4 * 256 + sizeof(float2) * 256 + sizeof(float) * (RS_T / 32) * 32 +
+         sizeof(float2) * 16 + sizeof(int) * 4 + sizeof(float2) * (size_t)s * N;
 }
 
 __global__ void k_chol_rinv(int s, const int* __restrict__ list, const int* __restrict__ count,

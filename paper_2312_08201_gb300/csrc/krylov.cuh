@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(NT) k_cycle_start(int N, int m, const int* __r
 // and the residual coefficients c = beta e1 - H0 y2 (length jstop + 1).
 // Outputs per system: coefY[0..s_cur) = y1, coefY[s_cur..s_cur+jstop) = y2,
 // coefR[0..jstop] = c.
+constexpr int CS_WARPS = 4;  // systems (warps) per CTA of k_cycle_solve
 __global__ void k_cycle_solve(int m, int smax, int s_cur, const int* __restrict__ list,
                               const int* __restrict__ count, const double2* __restrict__ H,
                               const double2* __restrict__ H0, const double2* __restrict__ Bk,
@@ -536,6 +537,21 @@ __global__ void k_chol_rinv(int s, const int* __restrict__ list, const int* __re
                             double2* __restrict__ G, size_t gs, double2* __restrict__ Rinv,
                             double2* __restrict__ Racc, double2* __restrict__ tmp, int accumulate,
                             int* __restrict__ ok);
+
+// Recycle start of the FP32 solves, fused into one CTA per listed system
+// (the FP64 path runs the same steps as separate kernels):
+//   C = T(v_b) Ut = Ut D(v_b)^{-1} - C0Ut,
+//   two CholQR passes (G = C^H C = L L^H, C := C L^{-H}), Ra = product of the
+//   L^{-H} factors, C written out, U = Ut Ra,
+//   c = C^H r, x += U c, r -= C c.
+// C_b stays in shared memory between the steps. ok[b] = 0 when a Cholesky
+// factor fails (the projection is then not applied to that system).
+constexpr int RS_T = 512;
+__global__ void k_recstart32(int n, int k, int s, const int* __restrict__ list, const int* __restrict__ count,
+                             const float2* __restrict__ Ut, const float2* __restrict__ C0Ut,
+                             const double* __restrict__ vinv, float2* __restrict__ C, float2* __restrict__ U,
+                             size_t ss, float2* __restrict__ X, float2* __restrict__ R, int* __restrict__ ok);
+size_t recstart32_smem_bytes(int s, int N);
 
 // AU_b[c] = Ut[c] o (1/v_b per column block) - C0Ut[c]
 template <typename T2>

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "cplx.cuh"
 #include "krylov.cuh"
@@ -248,6 +249,27 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
       rec.c0_valid = true;
     }
     const size_t ss = (size_t)smax * NS;
+    bool fused = false;
+    if constexpr (std::is_same<T2, float2>::value) {
+      // FP32 solves: the whole recycle start in one kernel while C_b fits in shared memory
+      const size_t rsm = kry::recstart32_smem_bytes(s, N);
+      if (rsm <= 200 * 1024) {
+        static std::once_flag once;
+        static cudaError_t rc_attr = cudaSuccess;
+        std::call_once(once, [] {
+          rc_attr = cudaFuncSetAttribute(kry::k_recstart32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        });
+        LY_CUDA(rc_attr);
+        const int ph_ = prof_begin(PK_RECSTART, st);
+        kry::k_recstart32<<<B, kry::RS_T, rsm, st>>>(n, k, s, Lchunk, cchunk, rec.Ut.p, rec.C0Ut.p, op.vinv, ws.C.p,
+                                                     ws.U.p, ss, ws.X.p, ws.R.p, ws.ok.p);
+        lyap_count_launch();
+        prof_end(ph_, st, 0.0, (4.0 * s + 4.0) * N * sizeof(T2), 0, cchunk);
+        LY_CUDA(cudaGetLastError());
+        fused = true;
+      }
+    }
+    if (!fused) {
     kry::k_make_AU<T2><<<dim3(gx(NS * s), B), kry::NT, 0, st>>>(n, k, s, Lchunk, cchunk, rec.Ut.p, rec.C0Ut.p,
                                                                  op.vinv, ws.C.p, ss); lyap_count_launch();
     // CholQR2: C = AU R^{-1}, U = Ut R^{-1}
@@ -270,12 +292,13 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     kry::k_tsmm<T2, T2><<<dim3(gx(NS), B), kry::NT, 0, st>>>(N, Lchunk, cchunk, useg, ws.Racc.p, s,
                                                              (size_t)s * s, s, ws.U.p, ss, NS, 0); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
+    }
     std::vector<int> okh(B);
     LY_CUDA(cudaMemcpyAsync(okh.data(), ws.ok.p, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
     LY_CUDA(cudaStreamSynchronize(st));
     bool all_ok = std::all_of(okh.begin(), okh.end(), [](int v) { return v == 1; });
     if (all_ok) {
-      {
+      if (!fused) {  // the fused kernel has applied the projection already
         const int ph_ = prof_begin(PK_RECSTART, st);
         kry::k_project<T2><<<B, kry::NT, 0, st>>>(N, s, Lchunk, cchunk, ws.C.p, ws.U.p, ss, ws.X.p, ws.R.p); lyap_count_launch();
         prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
@@ -335,8 +358,8 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     // ---- cycle end -----------------------------------------------------
     {
       const int ph_ = prof_begin(PK_CYCLE, st);
-      // one thread per system in CTAs of 8: the serial FP64 solves spread over all SMs
-      kry::k_cycle_solve<<<(B + 7) / 8, 8, 0, st>>>(m, smax, s_cur, Lstart, cstart, ws.H.p, ws.H0.p, ws.Bk.p, ws.g.p,
+      // one warp per system
+      kry::k_cycle_solve<<<(B + kry::CS_WARPS - 1) / kry::CS_WARPS, 32 * kry::CS_WARPS, 0, st>>>(m, smax, s_cur, Lstart, cstart, ws.H.p, ws.H0.p, ws.Bk.p, ws.g.p,
                                            ws.beta.p, ws.jstop.p, ws.coefY.p, ws.coefR.p); lyap_count_launch();
       prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
     }
