@@ -418,6 +418,12 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
       LY_CUDA(cudaStreamSynchronize(st));
     }
   }
+  // the call's stream waits for the recycle updates still running on the
+  // workspaces' side streams, so that work counted after the call includes them
+  if (w.ws64.side) LY_CUDA(cudaStreamWaitEvent(st, w.ws64.side_done, 0));
+  if (w.ws64adj.side) LY_CUDA(cudaStreamWaitEvent(st, w.ws64adj.side_done, 0));
+  if (w.ws32.side) LY_CUDA(cudaStreamWaitEvent(st, w.ws32.side_done, 0));
+  if (w.ws32adj.side) LY_CUDA(cudaStreamWaitEvent(st, w.ws32adj.side_done, 0));
   return LYAP_OK;
 }
 

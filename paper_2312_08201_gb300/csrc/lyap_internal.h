@@ -104,6 +104,12 @@ struct Recycle {
   DevBuf<R2> C0Ut;
   int s = 0;     // columns held (0 = none yet)
   bool c0_valid = false;
+  // An update still running on the producing workspace's side stream: the
+  // solver resolves it (ready, then *ok_host) before the next use.
+  bool pending = false;
+  int pending_s = 0;
+  cudaEvent_t ready = nullptr;
+  const volatile int* ok_host = nullptr;
 };
 
 struct lyap_seed {

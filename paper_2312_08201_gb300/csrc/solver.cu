@@ -101,6 +101,25 @@ __global__ void k_c0_from_relation(int n, int k, int s, const T2* __restrict__ U
   }
 }
 
+// Hand-over of the chunk's recycle space, on the device: when the last
+// system holds a recycle space (hasrec), Ut = its U and C0Ut from the
+// relation T U = C; *ok tells the host whether it happened.
+template <typename T2>
+__global__ void k_handover(int n, int k, int s, const int* __restrict__ hasrec, int last, const T2* __restrict__ U,
+                           const T2* __restrict__ C, const double* __restrict__ vinv_b, T2* __restrict__ Ut,
+                           T2* __restrict__ C0U, int* __restrict__ ok) {
+  const bool have = hasrec[last] != 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ok = have ? 1 : 0;
+  if (!have) return;
+  const size_t N = (size_t)n * k;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N * s; e += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)((e % N) / n);
+    const double2 u = to_d2(U[e]);
+    Ut[e] = U[e];
+    C0U[e] = from_d2<T2>(csub(cscale(u, vinv_b[t]), to_d2(C[e])));
+  }
+}
+
 inline int gx(size_t N) {
   size_t g = (N + kry::NT - 1) / kry::NT;
   if (g > 64) g = 64;
@@ -148,6 +167,30 @@ int lyap_params_from_opts(const lyap_opts& o, SolveParams& p) {
 }
 
 // --------------------------------------------------------------- workspace
+template <typename T2>
+int KrylovWS<T2>::ensure_side() {
+  if (side) return LYAP_OK;
+  LY_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+  LY_CUDA(cudaEventCreateWithFlags(&side_start, cudaEventDisableTiming));
+  LY_CUDA(cudaEventCreateWithFlags(&side_done, cudaEventDisableTiming));
+  LY_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&rec_ok_host), sizeof(int), cudaHostAllocDefault));
+  *rec_ok_host = 0;
+  LY_TRY(rec_ok_dev.alloc(1));
+  LY_TRY(vinv_last.alloc(8));
+  return LYAP_OK;
+}
+
+template <typename T2>
+KrylovWS<T2>::~KrylovWS() {
+  if (side) {
+    cudaStreamSynchronize(side);
+    cudaStreamDestroy(side);
+  }
+  if (side_start) cudaEventDestroy(side_start);
+  if (side_done) cudaEventDestroy(side_done);
+  if (rec_ok_host) cudaFreeHost(rec_ok_host);
+}
+
 template <typename T2>
 int KrylovWS<T2>::ensure(int B_, int N_, int m_, int s_) {
   if (B_ <= B && N_ == N && m_ == m && s_ == smax && V.p) return LYAP_OK;
@@ -212,6 +255,17 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
   const int n = op.sd->n, k = op.sd->k;
   const int N = n * k;
   const int m = prm.m, s = prm.s;
+  // the previous chunk's recycle update on this workspace (side stream) must be
+  // complete before its buffers are reused; it has normally finished long ago
+  if (ws.side) LY_CUDA(cudaEventSynchronize(ws.side_done));
+  if (rec.pending) {
+    LY_CUDA(cudaEventSynchronize(rec.ready));
+    rec.pending = false;
+    if (*rec.ok_host) {
+      rec.s = rec.pending_s;
+      rec.c0_valid = true;
+    }
+  }
   LY_TRY(ws.ensure(B, N, m, s));
   const int smax = ws.smax;
   const int LD = m + smax + 1;
@@ -315,6 +369,7 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
   const size_t css = (size_t)smax * NS;
   int chunk_count = B;
   int guard = 0;
+  bool last_async = false;  // the last cycle's recycle update runs on ws.side
   while (chunk_count > 0 && guard++ < 100000) {
     LY_CUDA(cudaMemcpyAsync(Lstart, Lchunk, sizeof(int) * B, cudaMemcpyDeviceToDevice, st));
     LY_CUDA(cudaMemcpyAsync(cstart, cchunk, sizeof(int), cudaMemcpyDeviceToDevice, st));
@@ -382,26 +437,39 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     LY_CUDA(cudaStreamSynchronize(st));
     const int Bw = std::min(B, chunk_count + 1);
     // ---- recycle update (harmonic Ritz) ----------------------------------
+    // After the chunk's last cycle only the last system is updated, and only
+    // the next chunk uses the result: run it on the side stream.
+    const bool async_update = s > 0 && chunk_count == 0;
+    last_async = async_update;
+    cudaStream_t us = st;
+    if (async_update) {
+      LY_TRY(ws.ensure_side());
+      LY_CUDA(cudaMemcpyAsync(ws.vinv_last.p, op.vinv + (size_t)(B - 1) * k, sizeof(double) * k,
+                              cudaMemcpyDeviceToDevice, st));
+      LY_CUDA(cudaEventRecord(ws.side_start, st));
+      LY_CUDA(cudaStreamWaitEvent(ws.side, ws.side_start, 0));
+      us = ws.side;
+    }
     if (s > 0) {
       auto Vh = seg2(seg(ws.C.p, css, NS, s_cur), segd(ws.V.p, (size_t)(m + 1) * NS, NS, ws.jstop.p, 1));
       auto Wh = seg2(seg(ws.U.p, css, NS, s_cur), segd(ws.Z.p, (size_t)m * NS, NS, ws.jstop.p, 0));
       int* Lwant = L + 5 * B;
       int* cwant = cnt + 5;
-      k_want_ritz<<<g1, 256, 0, st>>>(Lstart, cstart, ws.flag.p, ws.jstop.p, B - 1, ws.rflag.p);
+      k_want_ritz<<<g1, 256, 0, us>>>(Lstart, cstart, ws.flag.p, ws.jstop.p, B - 1, ws.rflag.p);
       lyap_count_launch();
-      kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.rflag.p, Lwant, cwant);
+      kry::k_compact<<<1, 1024, 0, us>>>(Lstart, cstart, ws.rflag.p, Lwant, cwant);
       lyap_count_launch();
       {
-        const int ph_ = prof_begin(PK_GRAM, st);
-        LY_TRY(kry::launch_gram<T2>(N, Lwant, cwant, Bw, Bw, Vh, Wh, ws.F.p, LD, (size_t)LD * LD, st));
-        prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+        const int ph_ = prof_begin(PK_GRAM, us);
+        LY_TRY(kry::launch_gram<T2>(N, Lwant, cwant, Bw, Bw, Vh, Wh, ws.F.p, LD, (size_t)LD * LD, us));
+        prof_end(ph_, us, 0.0, 0.0, 0, nullptr);
       }
       if (s_cur > 0) {
         auto Us = seg2(seg(ws.U.p, css, NS, s_cur), seg(ws.U.p, css, NS, 0));
-        LY_TRY(kry::launch_gram<T2>(N, Lwant, cwant, Bw, Bw, Us, Us, ws.UU.p, smax, (size_t)smax * smax, st));
+        LY_TRY(kry::launch_gram<T2>(N, Lwant, cwant, Bw, Bw, Us, Us, ws.UU.p, smax, (size_t)smax * smax, us));
       }
       {
-        const int ph_ = prof_begin(PK_RITZ, st);
+        const int ph_ = prof_begin(PK_RITZ, us);
         const size_t rsm = kry::ritz_smem_bytes(m, smax);
       if (rsm > 48 * 1024) {
         // the largest size any call needs (m <= 60, s <= 16), set once for all threads
@@ -413,30 +481,30 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
         });
         LY_CUDA(rc_attr);
       }
-      kry::k_ritz<<<Bw, 32, rsm, st>>>(m, smax, s_cur, s, Lwant, cwant, ws.jstop.p, ws.H0.p,
+      kry::k_ritz<<<Bw, 32, rsm, us>>>(m, smax, s_cur, s, Lwant, cwant, ws.jstop.p, ws.H0.p,
                                                         ws.Bk.p, ws.F.p, ws.UU.p, ws.work.p, ws.wstride, ws.Pu.p,
                                                         ws.Qc.p, ws.ok.p); lyap_count_launch();
-        prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+        prof_end(ph_, us, 0.0, 0.0, 0, nullptr);
       }
       // systems whose update succeeded: new U = [U Z] Pu, C = [C V] Qc (in place)
       {
         // list of systems with ok = 1 (flag-like compaction on ok)
-        kry::k_compact<<<1, 1024, 0, st>>>(Lwant, cwant, ws.ok.p, Lritz, critz); lyap_count_launch();
+        kry::k_compact<<<1, 1024, 0, us>>>(Lwant, cwant, ws.ok.p, Lritz, critz); lyap_count_launch();
         {
-          const int ph_ = prof_begin(PK_TSMM, st);
-          kry::k_tsmm<T2, T2><<<dim3(gx(NS), Bw), kry::NT, 0, st>>>(N, Lritz, critz, Wh, ws.Pu.p, LD,
+          const int ph_ = prof_begin(PK_TSMM, us);
+          kry::k_tsmm<T2, T2><<<dim3(gx(NS), Bw), kry::NT, 0, us>>>(N, Lritz, critz, Wh, ws.Pu.p, LD,
                                                                  (size_t)LD * 16, s, ws.U.p, css, NS, 0); lyap_count_launch();
-          prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+          prof_end(ph_, us, 0.0, 0.0, 0, nullptr);
         }
         {
-          const int ph_ = prof_begin(PK_TSMM, st);
-          kry::k_tsmm<T2, T2><<<dim3(gx(NS), Bw), kry::NT, 0, st>>>(N, Lritz, critz, Vh, ws.Qc.p, LD,
+          const int ph_ = prof_begin(PK_TSMM, us);
+          kry::k_tsmm<T2, T2><<<dim3(gx(NS), Bw), kry::NT, 0, us>>>(N, Lritz, critz, Vh, ws.Qc.p, LD,
                                                                  (size_t)LD * 16, s, ws.C.p, css, NS, 0); lyap_count_launch();
-          prof_end(ph_, st, 0.0, 0.0, 0, nullptr);
+          prof_end(ph_, us, 0.0, 0.0, 0, nullptr);
         }
-        k_mark_rec<<<g1, 256, 0, st>>>(Lwant, cwant, ws.ok.p, ws.hasrec.p); lyap_count_launch();
+        k_mark_rec<<<g1, 256, 0, us>>>(Lwant, cwant, ws.ok.p, ws.hasrec.p); lyap_count_launch();
         if (s_cur == 0) {
-          k_zero_failed<T2><<<dim3(gx(NS * s), Bw), kry::NT, 0, st>>>(NS, s, Lwant, cwant, ws.ok.p, ws.C.p,
+          k_zero_failed<T2><<<dim3(gx(NS * s), Bw), kry::NT, 0, us>>>(NS, s, Lwant, cwant, ws.ok.p, ws.C.p,
                                                                      ws.U.p, css);
           lyap_count_launch();
         }
@@ -452,7 +520,7 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
   std::vector<int> fl(B), hr(B);
   LY_CUDA(cudaMemcpyAsync(iters.data(), ws.iters.p, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
   LY_CUDA(cudaMemcpyAsync(fl.data(), ws.flag.p, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
-  LY_CUDA(cudaMemcpyAsync(hr.data(), ws.hasrec.p, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  if (!last_async) LY_CUDA(cudaMemcpyAsync(hr.data(), ws.hasrec.p, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
   LY_CUDA(cudaStreamSynchronize(st));
   for (int b = 0; b < B; ++b) {
     int f = fl[b];
@@ -461,6 +529,23 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
                 : code == 2 ? LYAP_ENOCONV
                 : code == 3 ? LYAP_EBREAKDOWN
                             : LYAP_ENONFINITE;
+  }
+  if (last_async) {
+    // hand-over on the side stream, resolved by the next chunk on this workspace
+    if (rec.Ut.count < (size_t)s * NS) LY_TRY(rec.Ut.alloc((size_t)s * NS));
+    if (rec.C0Ut.count < (size_t)s * NS) LY_TRY(rec.C0Ut.alloc((size_t)s * NS));
+    const size_t off = (size_t)(B - 1) * css;
+    k_handover<T2><<<gx(NS * s), kry::NT, 0, ws.side>>>(n, k, s, ws.hasrec.p, B - 1, ws.U.p + off, ws.C.p + off,
+                                                         ws.vinv_last.p, rec.Ut.p, rec.C0Ut.p, ws.rec_ok_dev.p);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    LY_CUDA(cudaMemcpyAsync(ws.rec_ok_host, ws.rec_ok_dev.p, sizeof(int), cudaMemcpyDeviceToHost, ws.side));
+    LY_CUDA(cudaEventRecord(ws.side_done, ws.side));
+    rec.pending = true;
+    rec.pending_s = s;
+    rec.ready = ws.side_done;
+    rec.ok_host = ws.rec_ok_host;
+    return LYAP_OK;
   }
   if (s > 0 && hr[B - 1]) {
     LY_TRY(rec.Ut.alloc((size_t)s * NS));

@@ -37,8 +37,21 @@ struct KrylovWS {
   DevBuf<double2> H, H0, Bk, g, sn, coefY, coefR, F, UU, work, Pu, Qc, Gs, Rinv, Racc, Rtmp;
   DevBuf<double> cs, beta, tolabs, tmpd;
   DevBuf<int> jstop, flag, iters, lists, counts, ok, hasrec, rflag;
+  // The recycle update of a chunk's last cycle (harmonic Ritz of the last
+  // system, hand-over to the Recycle) runs on a side stream, overlapping
+  // the caller's next work; the next chunk on this workspace waits for it.
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_start = nullptr, side_done = nullptr;
+  int* rec_ok_host = nullptr;  // pinned
+  DevBuf<int> rec_ok_dev;
+  DevBuf<double> vinv_last;
   int ensure(int B, int N, int m, int s);
+  int ensure_side();
   size_t bytes() const;
+  KrylovWS() = default;
+  KrylovWS(const KrylovWS&) = delete;
+  KrylovWS& operator=(const KrylovWS&) = delete;
+  ~KrylovWS();
 };
 
 // Solve op(v_b) x_b = rhs_b for the B systems of one chunk, starting from
