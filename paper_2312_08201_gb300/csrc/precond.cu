@@ -378,52 +378,70 @@ __global__ void __launch_bounds__(WT) k_prec_b(int n, const int* __restrict__ li
   const int s0 = blockIdx.y * PST;
   if (s0 >= nact) return;
   const int j0 = blockIdx.x * RT;
-  for (int e = threadIdx.x; e < r * PST; e += WT) {
-    const int sl = e % PST, l = e / PST;
-    float2 c = make_float2(0.f, 0.f);
-    if (s0 + sl < nact)
-      for (int tx = 0; tx < ntx; ++tx) c = cadd(c, Cp[((size_t)tx * nslots + s0 + sl) * r + l]);
-    cs[sl][l] = c;
-  }
-  __syncthreads();
-  // y = Cap^{-1} c, or Cap^{-T} c for the adjoint
-  for (int e = threadIdx.x; e < r * PST; e += WT) {
-    const int sl = e % PST, l = e / PST;
-    float2 y = make_float2(0.f, 0.f);
-    if (s0 + sl < nact) {
-      const float2* Ci = cinv + (size_t)list[s0 + sl] * r * r;
-      for (int q = 0; q < r; ++q) y = cfma(adj ? Ci[q + (size_t)l * r] : Ci[l + (size_t)q * r], cs[sl][q], y);
+  // one warp per system of the tile, lanes over the rank index: the partial
+  // sums and Cap^{-1} are read with coalesced, independent loads
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int sl = warp; sl < PST; sl += WT / 32) {
+    const bool live = s0 + sl < nact;
+    for (int l = lane; l < r; l += 32) {
+      float2 c = make_float2(0.f, 0.f);
+      if (live)
+        for (int tx = 0; tx < ntx; ++tx) c = cadd(c, Cp[((size_t)tx * nslots + s0 + sl) * r + l]);
+      cs[sl][l] = c;
     }
-    ys[sl][l] = y;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < RT * PST; e += WT) {
-    const int row = e % RT, sl = e / RT;
-    const int j = j0 + row;
-    if (s0 + sl >= nact || j >= n) continue;
-    const int b = list[s0 + sl];
-    float2 x[K];
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-      const float2* arow = Aop + (size_t)t * n + j;
-      float2 s0v = make_float2(0.f, 0.f), s1v = make_float2(0.f, 0.f);
-      int l = 0;
-      for (; l + 1 < r; l += 2) {
-        s0v = cfma(arow[(size_t)l * ldr], ys[sl][l], s0v);
-        s1v = cfma(arow[(size_t)(l + 1) * ldr], ys[sl][l + 1], s1v);
+    __syncwarp();
+    // y = Cap^{-1} c, or Cap^{-T} c for the adjoint
+    for (int l = lane; l < r; l += 32) {
+      float2 y = make_float2(0.f, 0.f);
+      if (live) {
+        const float2* Ci = cinv + (size_t)list[s0 + sl] * r * r;
+        if (adj) {
+          for (int q = 0; q < r; ++q) y = cfma(Ci[q + (size_t)l * r], cs[sl][q], y);
+        } else {
+          for (int q = 0; q < r; ++q) y = cfma(Ci[l + (size_t)q * r], cs[sl][q], y);
+        }
       }
-      if (l < r) s0v = cfma(arow[(size_t)l * ldr], ys[sl][l], s0v);
-      x[t] = cadd(s0v, s1v);
+      ys[sl][l] = y;
     }
-    double vb[K];
-    load_vb<K>(vinv, b, vb);
-    bsolve<K>(n, j, Gd, adj, vb, x);
-    T2* out = Out + (size_t)b * out_ss;
+  }
+  __syncthreads();
+  // thread = (row, group of PG systems): each entry of the row of A is
+  // loaded once and serves PG systems
+  constexpr int PG = K <= 2 ? 4 : (K <= 4 ? 2 : 1);
+  for (int e = threadIdx.x; e < RT * (PST / PG); e += WT) {
+    const int row = e % RT, g0 = (e / RT) * PG;
+    const int j = j0 + row;
+    if (j >= n || s0 + g0 >= nact) continue;
+    float2 x[PG][K];
 #pragma unroll
-    for (int t = 0; t < K; ++t) {
-      const size_t e2 = (size_t)t * n + j;
-      const double2 zd = to_d2(out[e2]);
-      out[e2] = from_d2<T2>(make_double2(zd.x + x[t].x, zd.y + x[t].y));
+    for (int u = 0; u < PG; ++u)
+#pragma unroll
+      for (int t = 0; t < K; ++t) x[u][t] = make_float2(0.f, 0.f);
+    for (int l = 0; l < r; ++l) {
+      float2 a[K];
+#pragma unroll
+      for (int t = 0; t < K; ++t) a[t] = Aop[(size_t)t * n + j + (size_t)l * ldr];
+#pragma unroll
+      for (int u = 0; u < PG; ++u) {
+        const float2 y = ys[g0 + u][l];
+#pragma unroll
+        for (int t = 0; t < K; ++t) x[u][t] = cfma(a[t], y, x[u][t]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PG; ++u) {
+      if (s0 + g0 + u >= nact) break;
+      const int b = list[s0 + g0 + u];
+      double vb[K];
+      load_vb<K>(vinv, b, vb);
+      bsolve<K>(n, j, Gd, adj, vb, x[u]);
+      T2* out = Out + (size_t)b * out_ss;
+#pragma unroll
+      for (int t = 0; t < K; ++t) {
+        const size_t e2 = (size_t)t * n + j;
+        const double2 zd = to_d2(out[e2]);
+        out[e2] = from_d2<T2>(make_double2(zd.x + x[u][t].x, zd.y + x[u][t].y));
+      }
     }
   }
 }
