@@ -96,9 +96,10 @@ typedef struct lyap_server lyap_server;
  * linear functional of the capacitance solution and is wanted to 1e-10),
  * at most 300 iterations, s = 10 recycled vectors. The cycle length m is
  * not given in the paper; the default 40 is the fastest of 24..60 for both
- * paths on the 800-state benchmark. The TSVD rank defaults to 30 (the paper
- * uses 50 and 5 in its examples; 30 is the fastest setting of the mixed path
- * on that benchmark). The mixed path's inner tolerance defaults to 1e-4:
+ * paths on the 800-state benchmark. The TSVD rank defaults to 50, the
+ * paper's Ex. 1 value (it uses 5 in Ex. 3); on the 800-state benchmark 50 is
+ * within 2% of the fastest rank (64). The mixed path's inner tolerance
+ * defaults to 1e-4:
  * the tensor-core operator is accurate to about 1e-5, so a tighter inner
  * solve does not save refinement steps, and 1e-4 minimised the time. */
 typedef struct {
@@ -110,7 +111,7 @@ typedef struct {
   int s;             /* recycled vectors (harmonic Ritz, smallest |theta|)    */
   int pbar;          /* rank of the truncated SVD of the off-diagonal coupling
                         kept in the preconditioner (eq. (prec)); 0 = block
-                        diagonal only; at most 64; default 30            */
+                        diagonal only; at most 64; default 50            */
   int batch;         /* systems solved in lockstep (0 = library's choice)    */
   int precision;     /* LYAP_FP64 or LYAP_BF16_IR                              */
   int max_refine;    /* mixed path: max refinement steps                      */

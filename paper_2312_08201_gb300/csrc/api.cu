@@ -83,7 +83,7 @@ extern "C" void lyap_opts_default(lyap_opts* o) {
   o->maxit = 300;
   o->m = 40;
   o->s = 10;
-  o->pbar = 30;
+  o->pbar = 50;
   o->batch = 0;
   o->precision = LYAP_FP64;
   o->max_refine = 10;

@@ -31,8 +31,8 @@ def test_binding_covers_header(lib):
 
 def test_opts_defaults_follow_paper_settings(lib):
     o = ly.default_opts()
-    assert o.maxit == 300 and o.s == 10  # §4, Ex. 1 settings
-    assert o.m == 40 and o.precision == ly.FP64 and o.pbar == 30 and o.inner_tol == 1e-4
+    assert o.maxit == 300 and o.s == 10  # §4, Ex. 1 settings (also p̄ = 50)
+    assert o.m == 40 and o.precision == ly.FP64 and o.pbar == 50 and o.inner_tol == 1e-4
     assert 0 < o.tol <= 1e-10
 
 
