@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--precision", choices=["best", "fp64", "bf16_ir"], default="best")
     ap.add_argument("--batch", type=int, default=0, help="systems solved in lockstep (0: library default)")
     ap.add_argument("--pbar", type=int, default=-1, help="TSVD rank of the preconditioner coupling (-1: library default)")
-    ap.add_argument("--residual", choices=["ff", "fp64"], default="ff",
+    ap.add_argument("--residual", choices=["ff", "fp64", "tc"], default="tc",
                     help="arithmetic of the mixed path's refinement residual")
     ap.add_argument("--nv", type=int, default=0, help="parameter vectors of the sweep (0: all 1000)")
     ap.add_argument("--profile-sweep", action="store_true",
@@ -246,7 +246,8 @@ def run_serving(args, local):
                                 p99_ms=1e3 * float(np.percentile(lat, 99)), requests=len(reqs))
     line = dict(metric=METRIC, value=rates["0.95"]["evals_per_s"], unit="evals/s", n_gpus=1, steps=args.requests,
                 warmup=16, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="bf16x3-gemm/f32-krylov/ff-refine" if prec == ly.BF16_IR else "f64", data="synthetic",
+                dtype="bf16x3-gemm/f32-krylov/int-sliced-bf16-refine (ff-refine for n > 1023)" if prec == ly.BF16_IR
+                else "f64", data="synthetic",
                 config=dict(workload=f"serving: 8 chain seeds {sizes} masses x2, k in {{2,3,4}}, 64 v per request, "
                                      "Poisson arrivals", n=[p.n for p in probs], k=[p.k for p in probs]),
                 saturation_evals_per_s=sat, rates=rates, seed_factor_s=t_factor,
@@ -354,7 +355,7 @@ def main():
     if args.pbar >= 0:
         opts["pbar"] = args.pbar
     if precision == "bf16_ir":
-        opts["residual"] = ly.RESID_FF if args.residual == "ff" else ly.RESID_FP64
+        opts["residual"] = {"ff": ly.RESID_FF, "fp64": ly.RESID_FP64, "tc": ly.RESID_TC}[args.residual]
 
     # reference values of the FP64 GPU path (outside the timed region)
     f64 = seed.trace_EX(v_dev, precision=ly.FP64).cpu().numpy()
@@ -468,7 +469,8 @@ def main():
         metric=METRIC, value=value, unit="evals/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="f64" if precision == "fp64" else
-        "bf16x3-gemm/f32-krylov/" + ("ff-refine" if args.residual == "ff" else "f64-refine"), data="synthetic",
+        "bf16x3-gemm/f32-krylov/" + {"ff": "ff-refine", "fp64": "f64-refine", "tc": "int-sliced-bf16-refine"}[args.residual],
+        data="synthetic",
         config=dict(workload=WORKLOAD, n=int(p.n), k=int(k), nv=int(nv), precision=precision, batch=args.batch,
                     pbar=int(ly.default_opts(**opts).pbar),
                     residual=args.residual if precision == "bf16_ir" else "fp64",

@@ -75,11 +75,15 @@ extern "C" {
 #define LYAP_BF16_IR 2
 
 /* Arithmetic of the mixed path's refinement residual (lyap_opts.residual).
- * Both evaluate P - T(v) W with an error of the order of FP64 rounding:
+ * All evaluate P - T(v) W with an error of the order of FP64 rounding:
  * FF pairs two FP32 values per number (about 48 significant bits, exact
- * products by FMA) and runs on the FP32 pipes; FP64 uses the FP64 pipes. */
+ * products by FMA) and runs on the FP32 pipes; FP64 uses the FP64 pipes;
+ * TC (the default) splits both operands into 8 exact 6-bit integer digits
+ * (48 bits, scaled per row/column) whose products the BF16 tensor cores sum
+ * without rounding; it needs n <= 1023, and FF is used above. */
 #define LYAP_RESID_FF 0
 #define LYAP_RESID_FP64 1
+#define LYAP_RESID_TC 2
 
 /* Fault-injection bits for lyap_opts.inject (host-side only; no GPU fault). */
 #define LYAP_INJECT_ALLOC_FAIL 0x1u   /* next workspace allocation fails     */
@@ -118,7 +122,7 @@ typedef struct {
   size_t hbm_budget; /* serving: admission budget in bytes (0 = 80% of free)  */
   void* stream;      /* cudaStream_t to run on (NULL = the context's stream)  */
   unsigned inject;   /* LYAP_INJECT_* bits (tests only)                       */
-  int residual;      /* mixed path: LYAP_RESID_FF (default) or LYAP_RESID_FP64 */
+  int residual;      /* mixed path: LYAP_RESID_TC (default), _FF or _FP64      */
 } lyap_opts;
 
 /* Per-result report. */

@@ -21,6 +21,9 @@ extern "C" {
  * out, float-float products). Synchronises. Returns LYAP_EDEVICE_TIMEOUT if
  * a bounded device wait expired. */
 #define LYAP_TEST_FF 3
+/* precision for lyap_test_apply: the integer-sliced tensor-core product of the
+ * mixed path's TC residual (FP64 in and out; n <= 1023) */
+#define LYAP_TEST_TC 4
 int lyap_test_apply(lyap_seed* seed, int nsys, const double* v, const double* w, int precision, int adjoint,
                     double* out);
 

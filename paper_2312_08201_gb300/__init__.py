@@ -43,7 +43,9 @@ INJECT_FORCE_MAXIT = 0x2
 INJECT_DEVICE_WAIT = 0x4
 RESID_FF = 0
 RESID_FP64 = 1
+RESID_TC = 2
 TEST_FF = 3  # lyap_test_apply: float-float residual kernel
+TEST_TC = 4  # lyap_test_apply: integer-sliced tensor-core residual kernel
 
 
 class LyapOpts(ctypes.Structure):

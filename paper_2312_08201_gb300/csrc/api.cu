@@ -90,7 +90,7 @@ extern "C" void lyap_opts_default(lyap_opts* o) {
   o->hbm_budget = 0;
   o->stream = nullptr;
   o->inject = 0;
-  o->residual = LYAP_RESID_FF;
+  o->residual = LYAP_RESID_TC;
 }
 
 extern "C" const char* lyap_strerror(int code) {

@@ -10,8 +10,9 @@
 //  * FP32 recycled Krylov inner solves (same batched GCRO-DR, float vectors,
 //    FP64 small matrices);
 //  * iterative refinement on the capacitance residual r = P - T(v) W,
-//    evaluated to FP64 accuracy (float-float kernel on the FP32 pipes, or
-//    the FP64 kernel), W += ||r|| * solve(T~, r/||r||), until
+//    evaluated to FP64 accuracy (integer-sliced product on the BF16 tensor
+//    cores, float-float kernel on the FP32 pipes, or the FP64 kernel),
+//    W += ||r|| * solve(T~, r/||r||), until
 //    ||r|| <= refine_tol ||P||. The trace and the update stay in FP64.
 #include <cuda_bf16.h>
 
@@ -23,6 +24,7 @@
 #include "krylov.cuh"
 #include "mixed.h"
 #include "prof.h"
+#include "oz_gemm.cuh"
 #include "tc_gemm.cuh"
 #include "lyap_testing.h"
 
@@ -48,6 +50,15 @@ struct MixedState {
   double lc_scale = 1.0, p_scale = 1.0;
   DevBuf<double> sw;   // bcap
   DevBuf<float4> panel_ff;  // bcap x k^2 n
+  // integer-sliced tensor-core residual (oz_gemm.cu), when 2n <= oz::KMAX
+  bool oz_ok = false;
+  DevBuf<__nv_bfloat16> ozA;  // NS x mpad x kpad digits of the Cauchy matrix
+  DevBuf<int> ozEA;           // mpad
+  CUtensorMap ozMapA;
+  DevBuf<__nv_bfloat16> ozB;  // NS x ncap x kpad digits of the panel
+  DevBuf<int> ozEB;           // ncap
+  DevBuf<float2> ozD;         // ncap x mpad
+  oz::Panel ozPanel;
 };
 
 namespace {
@@ -230,6 +241,17 @@ int ensure_refine(lyap_seed* sd, int Bc) {
   LY_TRY(ms.cnt.alloc(1));
   LY_TRY(ms.sw.alloc(Bc));
   LY_TRY(ms.panel_ff.alloc((size_t)Bc * sd->k * sd->k * sd->n));
+  if (ms.oz_ok) {
+    const int ncap = ((Bc * sd->k * sd->k + oz::BN - 1) / oz::BN) * oz::BN;
+    LY_TRY(ms.ozB.alloc((size_t)oz::NS * ncap * ms.kpad));
+    LY_TRY(ms.ozEB.alloc(ncap));
+    LY_TRY(ms.ozD.alloc((size_t)ncap * ms.mpad));
+    LY_TRY(oz::make_map(&ms.ozPanel.mapB, ms.ozB.p, oz::NS * ncap, ms.kpad, oz::BN));
+    ms.ozPanel.S = ms.ozB.p;
+    ms.ozPanel.eB = ms.ozEB.p;
+    ms.ozPanel.D = ms.ozD.p;
+    ms.ozPanel.ncap = ncap;
+  }
   ms.bcap = Bc;
   return LYAP_OK;
 }
@@ -279,6 +301,8 @@ int refine(lyap_seed* sd, int Bc, const double* vinv, const double2* rhs, double
       a.count = ms.cnt.p;
       a.nsys = nact;
       if (o.residual == LYAP_RESID_FP64) LY_TRY(capmv64_launch(a, st));
+      else if (o.residual == LYAP_RESID_TC && ms.oz_ok)
+        LY_TRY(oz::residual(a, ms.ozMapA, ms.ozEA.p, ms.mpad, ms.kpad, ms.ozPanel, ms.err.p, st));
       else LY_TRY(capmv_df_launch(a, ms.Lff.p, ms.lc_scale, ms.p_scale, ms.sw.p, ms.panel_ff.p, st));
       kry::k_norms<double2><<<Bc, kry::NT, 0, st>>>(N, Bc, ms.R64.p, N, ms.norms.p);
       lyap_count_launch();
@@ -380,13 +404,20 @@ int lyap_mixed_prepare(lyap_seed* sd, cudaStream_t st) {
     LY_TRY(ms->Lff.alloc((size_t)n * n));
     LY_TRY(capmv_df_build_lc(n, sd->lam.p, ms->lc_scale, ms->Lff.p, st));
   }
+  if (2 * n <= oz::KMAX) {
+    LY_TRY(ms->ozA.alloc((size_t)oz::NS * ms->mpad * ms->kpad));
+    LY_TRY(ms->ozEA.alloc(ms->mpad));
+    LY_TRY(oz::slice_A(n, sd->lam.p, ms->mpad, ms->kpad, ms->ozA.p, ms->ozEA.p, st));
+    LY_TRY(oz::make_map(&ms->ozMapA, ms->ozA.p, oz::NS * ms->mpad, ms->kpad, oz::BM));
+    ms->oz_ok = true;
+  }
   LY_TRY(tc::make_map(&ms->maps.a_hi, ms->Ahi.p, ms->mpad, ms->kpad, tc::BM));
   LY_TRY(tc::make_map(&ms->maps.a_lo, ms->Alo.p, ms->mpad, ms->kpad, tc::BM));
   LY_TRY(ms->err.alloc(1));
   LY_CUDA(cudaMemsetAsync(ms->err.p, 0, sizeof(int), st));
   LY_CUDA(cudaStreamSynchronize(st));
   sd->resident_bytes += ms->Ahi.bytes() + ms->Alo.bytes() + ms->Ub32.bytes() + ms->Vb32.bytes() + ms->Gd32.bytes() +
-                        ms->Lff.bytes();
+                        ms->Lff.bytes() + ms->ozA.bytes() + ms->ozEA.bytes();
   sd->mixed = ms.release();
   return LYAP_OK;
 }
@@ -468,7 +499,7 @@ extern "C" int lyap_test_apply(lyap_seed* sd, int nsys, const double* v, const d
   LY_CUDA(cudaStreamSynchronize(st));
   for (double& x : hv) x = 1.0 / x;
   LY_CUDA(cudaMemcpyAsync(vinv.p, hv.data(), sizeof(double) * hv.size(), cudaMemcpyHostToDevice, st));
-  if (precision == LYAP_FP64 || precision == LYAP_TEST_FF) {
+  if (precision == LYAP_FP64 || precision == LYAP_TEST_FF || precision == LYAP_TEST_TC) {
     CapArgs64 a{};
     a.n = sd->n;
     a.k = k;
@@ -486,6 +517,24 @@ extern "C" int lyap_test_apply(lyap_seed* sd, int nsys, const double* v, const d
     a.nsys = nsys;
     if (precision == LYAP_FP64) {
       LY_TRY(capmv64_launch(a, st));
+    } else if (precision == LYAP_TEST_TC) {
+      MixedState& ms = *sd->mixed;
+      if (!ms.oz_ok) return LYAP_EINVAL;
+      const int ncap = ((nsys * k * k + oz::BN - 1) / oz::BN) * oz::BN;
+      DevBuf<__nv_bfloat16> Bd;
+      DevBuf<int> eB;
+      DevBuf<float2> Dd;
+      LY_TRY(Bd.alloc((size_t)oz::NS * ncap * ms.kpad));
+      LY_TRY(eB.alloc(ncap));
+      LY_TRY(Dd.alloc((size_t)ncap * ms.mpad));
+      oz::Panel pn;
+      pn.S = Bd.p;
+      pn.eB = eB.p;
+      pn.D = Dd.p;
+      pn.ncap = ncap;
+      LY_TRY(oz::make_map(&pn.mapB, Bd.p, oz::NS * ncap, ms.kpad, oz::BN));
+      LY_TRY(oz::residual(a, ms.ozMapA, ms.ozEA.p, ms.mpad, ms.kpad, pn, ms.err.p, st));
+      LY_CUDA(cudaStreamSynchronize(st));
     } else {
       DevBuf<double> sw;
       DevBuf<float4> panel;

@@ -10,7 +10,7 @@
 namespace {
 
 const char* kNames[PK_COUNT] = {"capmv64", "tc_gemm", "ortho", "precond", "gram", "tsmm",
-                                "ritz",    "epi32",   "lsq",   "cycle",   "panel", "recstart", "capmv_ff", "cap_build"};
+                                "ritz",    "epi32",   "lsq",   "cycle",   "panel", "recstart", "capmv_ff", "cap_build", "oz_gemm"};
 
 struct Rec {
   int kernel;

@@ -24,7 +24,8 @@ enum ProfKernel {
   PK_CAPMV_FF = 12, // float-float capacitance matvec (mixed-path residual);
                     // its "flops" are FP32 lane instructions
   PK_CAPBUILD = 13, // Woodbury capacitance Cap(v)^{-1} per system
-  PK_COUNT = 14
+  PK_OZGEMM = 14,   // integer-sliced tensor-core residual product (mixed path)
+  PK_COUNT = 15
 };
 
 void lyap_count_launch(int n = 1);

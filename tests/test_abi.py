@@ -34,6 +34,7 @@ def test_opts_defaults_follow_paper_settings(lib):
     assert o.maxit == 300 and o.s == 10  # §4, Ex. 1 settings (also p̄ = 50)
     assert o.m == 40 and o.precision == ly.FP64 and o.pbar == 50 and o.inner_tol == 1e-4
     assert 0 < o.tol <= 1e-10
+    assert o.residual == ly.RESID_TC
 
 
 def test_strerror(lib):

@@ -8,6 +8,8 @@ Tolerances:
   * float-float residual kernel: ||T_ff w - T w|| <= 1e-12 ||T w|| per
     system (about 48 significant bits per product; the sums run over n
     terms), unchanged under power-of-two rescaling of w;
+  * integer-sliced tensor-core residual kernel: the same bound (8 digits of
+    6 bits per operand, exact integer sums; about 2^-47 of |A||B|^T);
   * traces after refinement: 1e-8 relative to the oracle;
   * gradients after refinement: 1e-6 relative to the largest component.
 """
@@ -177,3 +179,51 @@ def test_mixed_residual_arithmetic_options_agree(ctx):
         f, info = seed.trace_EX(vs[::4], return_info=True, precision=ly.BF16_IR, residual=resid)
         assert rel_err(f, ref).max() <= TOL_MIXED
         assert all(i["status"] == 0 and i["rel_resid"] <= 1e-11 for i in info)
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_sliced_tensor_core_operator_matches_fp64_operator(ctx, adjoint):
+    import torch
+
+    p, vs = workload_small_fp64()
+    A0, U, V, G, E, vs2 = random_problem(56, 70, 8, 3)
+    for A0_, U_, V_, G_, E_, vv in ((p.A0, p.U, p.V, p.G, p.E, vs), (A0, U, V, G, E, vs2)):
+        seed = ly.Seed(ctx, A0_, U_, V_, G_, E_)
+        n, k = U_.shape
+        rng = np.random.default_rng(3)
+        w = rng.standard_normal((9, k, n, 2))
+        v = torch.tensor(vv[:9], dtype=torch.float64, device="cuda")
+        for scale in (1.0, 2.0**-700, 2.0**400, 1e-30):
+            wt = torch.tensor(w * scale, dtype=torch.float64, device="cuda")
+            y64 = ly.test_apply(seed, v, wt, ly.FP64, adjoint).cpu().numpy()
+            ytc = ly.test_apply(seed, v, wt, ly.TEST_TC, adjoint).cpu().numpy()
+            assert np.isfinite(ytc).all()
+            for b in range(9):
+                assert np.linalg.norm(ytc[b] - y64[b]) <= 1e-12 * np.linalg.norm(y64[b]), (scale, b)
+
+
+def test_sliced_tensor_core_operator_at_converged_solution(ctx):
+    import torch
+
+    p, vs = workload_precision()
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    W, _ = seed.param_solve(vs[:70], precision=ly.FP64)
+    v = torch.tensor(vs[:70], dtype=torch.float64, device="cuda")
+    wt = torch.tensor(np.stack([W.real, W.imag], axis=-1), dtype=torch.float64, device="cuda")
+    y64 = ly.test_apply(seed, v, wt, ly.FP64, False).cpu().numpy()
+    ytc = ly.test_apply(seed, v, wt, ly.TEST_TC, False).cpu().numpy()
+    # the digits are scaled per row of the Cauchy matrix: an entry 2^j times
+    # smaller than its row's largest keeps 48 - j bits. On this chain the
+    # rows span about 2^5, so the bound is 5e-13, still 20x below the
+    # refinement tolerance 1e-11 that the residual is compared with.
+    for b in range(70):
+        assert np.linalg.norm(ytc[b] - y64[b]) <= 5e-13 * np.linalg.norm(y64[b])
+
+
+def test_mixed_with_sliced_residual(ctx):
+    p, vs = workload_small_fp64()
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    ref = oracle.sweep(p, vs[::4])
+    f, info = seed.trace_EX(vs[::4], return_info=True, precision=ly.BF16_IR, residual=ly.RESID_TC)
+    assert rel_err(f, ref).max() <= TOL_MIXED
+    assert all(i["status"] == 0 and i["rel_resid"] <= 1e-11 for i in info)
