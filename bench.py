@@ -259,9 +259,10 @@ def run_serving(args, local):
 def run_kernel_probe(args, local):
     """The capacitance operators on a full batch: T(v) applied to 1000
     random inputs of the 800-state seed with the tensor-core operator (panel,
-    tcgen05 GEMM, epilogue), the float-float kernel and the FP64 kernel;
-    CUDA-event timing per kernel for the roofline, and the float-float
-    operator's error against the FP64 one. One more application of each
+    tcgen05 GEMM, epilogue), the float-float kernel, the integer-sliced
+    tensor-core kernel and the FP64 kernel; CUDA-event timing per kernel for
+    the roofline, and the errors of the two FP64-accurate operators against
+    the FP64 one. One more application of each
     operator runs between cudaProfilerStart/Stop, for ncu captures of full
     launches (--profile-from-start off)."""
     import numpy as np
@@ -282,19 +283,26 @@ def run_kernel_probe(args, local):
     for _ in range(2):
         ly.test_apply(seed, v, w, ly.BF16_IR)
         ly.test_apply(seed, v, w, ly.TEST_FF)
+        ly.test_apply(seed, v, w, ly.TEST_TC)
         y64 = ly.test_apply(seed, v, w, ly.FP64)
     ly.prof_enable(True)
     for _ in range(max(1, args.steps)):
         ly.test_apply(seed, v, w, ly.BF16_IR)
         yff = ly.test_apply(seed, v, w, ly.TEST_FF)
+        ytc = ly.test_apply(seed, v, w, ly.TEST_TC)
     ly.test_apply(seed, v, w, ly.FP64)
     prof, launches = ly.prof_read()
     ly.prof_enable(False)
-    ff_err = float(((yff - y64).flatten(1).norm(dim=1) / y64.flatten(1).norm(dim=1)).max())
+
+    def rel(y):
+        return float(((y - y64).flatten(1).norm(dim=1) / y64.flatten(1).norm(dim=1)).max())
+
+    ff_err, tc_err = rel(yff), rel(ytc)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     ly.test_apply(seed, v, w, ly.BF16_IR)
     ly.test_apply(seed, v, w, ly.TEST_FF)
+    ly.test_apply(seed, v, w, ly.TEST_TC)
     ly.test_apply(seed, v, w, ly.FP64)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
@@ -306,7 +314,8 @@ def run_kernel_probe(args, local):
                          tflops=d["flops"] / sec / 1e12 if d["flops"] else None,
                          gbs=d["bytes"] / sec / 1e9 if d["bytes"] else None)
     print(json.dumps(dict(probe="operators on 1000 systems, 800-state seed", kernels=out,
-                          ff_max_rel_err_vs_fp64=ff_err, bf16_peak_tflops=pk["bf16_tflops"],
+                          ff_max_rel_err_vs_fp64=ff_err, tc_max_rel_err_vs_fp64=tc_err,
+                          bf16_peak_tflops=pk["bf16_tflops"],
                           peak_source=how)), flush=True)
 
 
@@ -443,7 +452,7 @@ def main():
                         peak_source="FP32 pipe: 152 SMs x 128 lane-instructions/clk x max SM clock "
                                     "(achieved: 49.5 FP32 instructions per float-float complex MAC)",
                         launches=d["launches"], avg_launch_ms=d["total_ms"] / d["launches"])
-        elif dom_name == "tc_gemm":
+        elif dom_name in ("tc_gemm", "oz_gemm"):
             peak = float(pk["bf16_tflops_sustained"])
             ach = d["flops"] / sec / 1e12
             roof = dict(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=None,

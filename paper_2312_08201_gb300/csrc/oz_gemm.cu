@@ -86,10 +86,25 @@ __global__ void __launch_bounds__(256) k_slice_A(int n, const double2* __restric
     write_digits(val(c) * sc, S + (size_t)r * kpad + c, (size_t)mpad * kpad);
 }
 
+// NS balanced base-64 digits of q = x 2^48 (|q| <= 2^47), top digit first,
+// by integer arithmetic (round to nearest at every digit, as write_digits).
+__device__ __forceinline__ void write_digits_int(long long q, __nv_bfloat16* S, size_t slice_stride) {
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int b = 6 * (NS - 1 - s);
+    const long long d = b > 0 ? ((q + (1LL << (b - 1))) >> b) : q;
+    q -= d << b;
+    S[(size_t)s * slice_stride] = __float2bfloat16_rn((float)d);
+  }
+}
+
 // Panel digits of the listed systems: column slot * k^2 + p k + t holds
-// W_b[:, p] o P2[:, t], real-split along K.
+// W_b[:, p] o P2[:, t], real-split along K. The column is formed once in
+// shared memory; its digits come from one rounding to 48 bits and integer
+// digit extraction (GB300's FP64 pipe is narrow).
 __global__ void __launch_bounds__(256) k_slice_B(CapArgs64 a, int ncap, int kpad, __nv_bfloat16* __restrict__ S,
                                                  int* __restrict__ eB) {
+  extern __shared__ double zcol[];  // kpad
   __shared__ double red[256];
   const int nsys = a.count ? *a.count : a.nsys;
   const int slot = blockIdx.x;
@@ -100,19 +115,23 @@ __global__ void __launch_bounds__(256) k_slice_B(CapArgs64 a, int ncap, int kpad
   for (int pt = 0; pt < kk; ++pt) {
     const int p = pt / k, t = pt % k;
     const int col = slot * kk + pt;
-    auto val = [&](int c) -> double {
-      if (c >= rows) return 0.0;
-      const int j = c >> 1;
-      const double2 z = cmul(Wb[(size_t)p * n + j], a.P2[(size_t)t * n + j]);
-      return (c & 1) ? z.y : z.x;
-    };
     double mx = 0.0;
-    for (int c = threadIdx.x; c < kpad; c += blockDim.x) mx = fmax(mx, fabs(val(c)));
-    const int e = scale_exp(block_max(mx, red));
+    for (int c = threadIdx.x; c < kpad; c += blockDim.x) {
+      double v = 0.0;
+      if (c < rows) {
+        const int j = c >> 1;
+        const double2 z = cmul(Wb[(size_t)p * n + j], a.P2[(size_t)t * n + j]);
+        v = (c & 1) ? z.y : z.x;
+      }
+      zcol[c] = v;
+      mx = fmax(mx, fabs(v));
+    }
+    const int e = scale_exp(block_max(mx, red));  // its barriers also publish zcol
     if (threadIdx.x == 0) eB[col] = e;
-    const double sc = ldexp(1.0, -e);
+    const double sc = ldexp(1.0, 48 - e);
     for (int c = threadIdx.x; c < kpad; c += blockDim.x)
-      write_digits(val(c) * sc, S + (size_t)col * kpad + c, (size_t)ncap * kpad);
+      write_digits_int(__double2ll_rn(zcol[c] * sc), S + (size_t)col * kpad + c, (size_t)ncap * kpad);
+    __syncthreads();  // zcol is rewritten by the next column
   }
 }
 
@@ -332,7 +351,8 @@ int residual(const CapArgs64& a, const CUtensorMap& mapA, const int* eA, int mpa
     attr_rc = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
   });
   LY_CUDA(attr_rc);
-  k_slice_B<<<a.nsys, 256, 0, st>>>(a, pn.ncap, kpad, reinterpret_cast<__nv_bfloat16*>(pn.S), pn.eB);
+  k_slice_B<<<a.nsys, 256, sizeof(double) * kpad, st>>>(a, pn.ncap, kpad, reinterpret_cast<__nv_bfloat16*>(pn.S),
+                                                         pn.eB);
   lyap_count_launch();
   LY_CUDA(cudaGetLastError());
   // tensor work per system: NS (NS + 1) / 2 BF16 products of the (2n x 2n) x (2n x k^2) real-split GEMM

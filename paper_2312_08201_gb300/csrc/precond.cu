@@ -187,9 +187,16 @@ __global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const double2* _
   double vb[K];
   load_vb<K>(vinv, b, vb);
   const int nout = r * r;
-  float2 acc[16];
+  // each thread owns a 4 x 4 tile of Cap (rows l0.., columns l20..): one pair
+  // of shared loads per row of the tile feeds 16 multiply-adds
+  const int tr = (r + 3) / 4, ntile = tr * tr;  // <= 256 = WT for r <= 64
+  const int tile = threadIdx.x;
+  const int l0 = 4 * (tile % tr), l20 = 4 * (tile / tr);
+  float2 acc[4][4];
 #pragma unroll
-  for (int u = 0; u < 16; ++u) acc[u] = make_float2(0.f, 0.f);
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
   for (int j0 = 0; j0 < n; j0 += J) {
     for (int e = threadIdx.x; e < J * r; e += WT) {
       const int jj = e / r, l = e % r, j = j0 + jj;
@@ -206,28 +213,35 @@ __global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const double2* _
       }
     }
     __syncthreads();
+    if (tile < ntile) {
+      for (int q = 0; q < J * K; ++q) {
+        float2 mv[4], wv[4];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-      const int o = threadIdx.x + u * WT;
-      if (o < nout) {
-        const int l = o % r, l2 = o / r;
-        float2 a = acc[u];
-        for (int q = 0; q < J * K; ++q) a = cfma(sm[(size_t)q * r + l], sw[(size_t)q * r + l2], a);
-        acc[u] = a;
+        for (int u = 0; u < 4; ++u) {
+          mv[u] = l0 + u < r ? sm[(size_t)q * r + l0 + u] : make_float2(0.f, 0.f);
+          wv[u] = l20 + u < r ? sw[(size_t)q * r + l20 + u] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = cfma(mv[u], wv[v], acc[u][v]);
       }
     }
     __syncthreads();
   }
   float2* C = sw;            // r x r, column-major: C[i + q r]
   float2* Inv = sw + nout;   // r x r
+  if (tile < ntile) {
 #pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int o = threadIdx.x + u * WT;
-    if (o < nout) {
-      const int l = o % r, l2 = o / r;
-      C[o] = make_float2((l == l2 ? 1.f : 0.f) - acc[u].x, -acc[u].y);
-      Inv[o] = make_float2(l == l2 ? 1.f : 0.f, 0.f);
-    }
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int l = l0 + u, l2 = l20 + v;
+        if (l < r && l2 < r) {
+          C[l + l2 * r] = make_float2((l == l2 ? 1.f : 0.f) - acc[u][v].x, -acc[u][v].y);
+          Inv[l + l2 * r] = make_float2(l == l2 ? 1.f : 0.f, 0.f);
+        }
+      }
   }
   __syncthreads();
   for (int c = 0; c < r; ++c) {
