@@ -103,9 +103,10 @@ typedef struct lyap_server lyap_server;
  * paths on the 800-state benchmark. The TSVD rank defaults to 50, the
  * paper's Ex. 1 value (it uses 5 in Ex. 3); on the 800-state benchmark 50 is
  * within 2% of the fastest rank (64). The mixed path's inner tolerance
- * defaults to 1e-4:
- * the tensor-core operator is accurate to about 1e-5, so a tighter inner
- * solve does not save refinement steps, and 1e-4 minimised the time. */
+ * defaults to 1e-3: the tensor-core operator is accurate to about 1e-5, so a
+ * tighter inner solve does not save refinement steps, and with the
+ * residual on the tensor cores a refinement step is cheap; 1e-3 (about 4
+ * steps) minimised the time. */
 typedef struct {
   double tol;        /* FP64 path: stop when ||r|| <= tol ||b||               */
   double refine_tol; /* mixed path: outer stop on the FP64 residual           */

@@ -79,7 +79,7 @@ extern "C" void lyap_opts_default(lyap_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->tol = 1e-12;
   o->refine_tol = 1e-11;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 1e-3;
   o->maxit = 300;
   o->m = 40;
   o->s = 10;
