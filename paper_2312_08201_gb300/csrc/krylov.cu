@@ -10,7 +10,8 @@ __global__ void k_iota(int B, int* list, int* count) {
 
 // single CTA of 1024 threads; order-preserving
 __global__ void k_compact(const int* __restrict__ in_list, const int* __restrict__ in_count,
-                          const int* __restrict__ flag, int* __restrict__ out_list, int* __restrict__ out_count) {
+                          const int* __restrict__ flag, int* __restrict__ out_list, int* __restrict__ out_count,
+                          int* host_count) {
   __shared__ int sc[1024];
   const int n = *in_count;
   const int per = (n + blockDim.x - 1) / blockDim.x;
@@ -31,7 +32,10 @@ __global__ void k_compact(const int* __restrict__ in_list, const int* __restrict
     int b = in_list[i];
     if (flag[b] > 0) out_list[pos++] = b;
   }
-  if (threadIdx.x == blockDim.x - 1) *out_count = sc[threadIdx.x];
+  if (threadIdx.x == blockDim.x - 1) {
+    *out_count = sc[threadIdx.x];
+    if (host_count) *host_count = sc[threadIdx.x];
+  }
 }
 
 // One warp per system (CS_WARPS warps per CTA). Back substitution
@@ -233,8 +237,66 @@ size_t ritz_smem_bytes(int m, int /*smax*/) {
 }
 
 // Recycle start of the FP32 solves in one CTA per system (see krylov.cuh).
-// Shared memory: small FP64 matrices (ld 16), the FP32 copies of the
-// triangular factors, reduction scratch, then C_b (s x N, [c][e]).
+// Everything runs in FP32: the Gram matrices of C are those of nearly
+// orthonormal columns (C = T(v) Ut with T(v') Ut orthonormal for the
+// previous v'), and the second CholQR pass removes what the first leaves.
+// Shared memory: 16 x 16 Gram, Cholesky factor, this pass's L^{-H} and the
+// accumulated product (column-major, ld 16), reduction scratch, D(v)^{-1},
+// then C_b (s rows of N, row stride N + 1).
+
+// Lower Cholesky factor of the 16 x 16 Hermitian matrix Gf (the leading
+// s x s block; identity beyond it) in one warp: lane i keeps row i in
+// registers, and column j's entries reach the other rows by shuffles.
+// Writes L to Lf and 1 / L[j][j] to rdiag; returns nonzero when a pivot is
+// not positive.
+__device__ __forceinline__ int chol16_warp(int s, const float2* Gf, float2* Lf, float* rdiag) {
+  const int lane = threadIdx.x & 31;
+  float2 g[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c)
+    g[c] = (lane < s && c < s) ? Gf[lane + c * 16] : make_float2(lane == c ? 1.f : 0.f, 0.f);
+  int bad = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float d = __shfl_sync(0xffffffffu, g[j].x, j);
+    bad |= !(d > 0.f) || !isfinite(d);
+    const float rs = rsqrtf(d);
+    const float2 lij = lane == j ? make_float2(d * rs, 0.f)
+                                 : (lane > j ? make_float2(g[j].x * rs, g[j].y * rs) : make_float2(0.f, 0.f));
+    g[j] = lij;
+    if (lane == 0) rdiag[j] = rs;
+#pragma unroll
+    for (int q = j + 1; q < 16; ++q) {
+      const float2 lq = make_float2(__shfl_sync(0xffffffffu, lij.x, q), __shfl_sync(0xffffffffu, lij.y, q));
+      g[q] = csub(g[q], cmul(lij, cconj(lq)));  // G(i, q) -= L(i, j) conj(L(q, j))
+    }
+  }
+  if (lane < 16) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) Lf[lane + c * 16] = g[c];
+  }
+  __syncwarp();
+  return bad;
+}
+
+// Rf = L^{-H} (upper triangular): lane c solves L x = e_c by forward
+// substitution and writes conj(x) as row c of Rf.
+__device__ __forceinline__ void linvh16_warp(const float2* Lf, const float* rdiag, float2* Rf) {
+  const int lane = threadIdx.x & 31;
+  if (lane >= 16) return;
+  float2 x[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    float2 acc = make_float2(i == lane ? 1.f : 0.f, 0.f);
+#pragma unroll
+    for (int p = 0; p < i; ++p) acc = csub(acc, cmul(Lf[i + p * 16], x[p]));
+    const float r = rdiag[i];
+    x[i] = make_float2(acc.x * r, acc.y * r);
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) Rf[lane + i * 16] = cconj(x[i]);
+}
+
 __global__ void __launch_bounds__(RS_T) k_recstart32(int n, int k, int s, const int* __restrict__ list,
                                                     const int* __restrict__ count, const float2* __restrict__ Ut,
                                                     const float2* __restrict__ C0Ut, const double* __restrict__ vinv,
@@ -242,39 +304,43 @@ __global__ void __launch_bounds__(RS_T) k_recstart32(int n, int k, int s, const 
                                                     float2* __restrict__ X, float2* __restrict__ R,
                                                     int* __restrict__ ok) {
   extern __shared__ __align__(16) unsigned char rsm[];
-  double2* G = reinterpret_cast<double2*>(rsm);  // 16 x 16
-  double2* Ri = G + 256;
-  double2* Ra = Ri + 256;
-  double2* Tm = Ra + 256;
-  float2* Rf = reinterpret_cast<float2*>(Tm + 256);  // 16 x 16 FP32 copy
-  float* red = reinterpret_cast<float*>(Rf + 256);   // (RS_T / 32) x 32
-  float2* coef = reinterpret_cast<float2*>(red + (RS_T / 32) * 32);  // 16
-  int* fail = reinterpret_cast<int*>(coef + 16);                     // 4 ints (keeps 16-byte alignment)
-  float2* Cs = reinterpret_cast<float2*>(fail + 4);                  // s x N
+  float2* Gf = reinterpret_cast<float2*>(rsm);                           // 16 x 16
+  float2* Lf = Gf + 256;                                                 // 16 x 16
+  float2* Rf = Lf + 256;                                                 // 16 x 16, this pass's L^{-H}
+  float2* Raf = Rf + 256;                                                // 16 x 16, product of the L^{-H}
+  float* red = reinterpret_cast<float*>(Raf + 256);                      // (RS_T / 32) x 32
+  float2* coef = reinterpret_cast<float2*>(red + (RS_T / 32) * 32);      // 16
+  float* vf = reinterpret_cast<float*>(coef + 16);                       // 16: D(v_b)^{-1}
+  float* rdiag = vf + 16;                                                // 16
+  int* fail = reinterpret_cast<int*>(rdiag + 16);                        // 4 ints (keeps 16-byte alignment)
+  float2* Cs = reinterpret_cast<float2*>(fail + 4);                      // s x N
   const int slot = blockIdx.x;
   if (slot >= *count) return;
   const int b = list[slot];
   const int N = n * k;
+  const int LDC = N + 1;  // padded row of C in shared memory
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double* vb = vinv + (size_t)b * k;
-  // C = Ut D(v)^{-1} - C0 Ut = T(v) Ut
-  for (int idx = tid; idx < s * N; idx += RS_T) {
-    const int e = idx % N, t = e / n;
-    const float2 u = Ut[idx], cu = C0Ut[idx];
-    const float vi = (float)vb[t];
-    Cs[idx] = make_float2(u.x * vi - cu.x, u.y * vi - cu.y);
-  }
+  if (tid < k) vf[tid] = (float)vinv[(size_t)b * k + tid];
   if (tid == 0) fail[0] = 0;
+  __syncthreads();
+  // C = Ut D(v)^{-1} - C0 Ut = T(v) Ut
+  for (int e = tid; e < N; e += RS_T) {
+    const float vi = vf[e / n];
+    for (int c = 0; c < s; ++c) {
+      const float2 u = Ut[(size_t)c * N + e], cu = C0Ut[(size_t)c * N + e];
+      Cs[(size_t)c * LDC + e] = make_float2(u.x * vi - cu.x, u.y * vi - cu.y);
+    }
+  }
   __syncthreads();
   const int npair = s * (s + 1) / 2;
   int Q = 1;
   while (Q < 32 && npair * Q * 2 <= RS_T) Q *= 2;
   for (int pass = 0; pass < 2; ++pass) {
     // Gram G = C^H C (upper pairs i <= j, Q threads per pair over a strided
-    // share of the elements; FP32 partial sums of 32 elements, FP64 total)
+    // share of the elements)
     {
       const int p = tid / Q, q = tid % Q;
-      double2 acc = make_double2(0.0, 0.0);
+      float2 acc = make_float2(0.f, 0.f);
       int i = 0, j = 0;
       if (p < npair) {
         int rem = p;
@@ -283,67 +349,61 @@ __global__ void __launch_bounds__(RS_T) k_recstart32(int n, int k, int s, const 
           ++i;
         }
         j = i + rem;
-        const float2* ci = Cs + (size_t)i * N;
-        const float2* cj = Cs + (size_t)j * N;
-        for (int e0 = q; e0 < N; e0 += 32 * Q) {
-          float2 t = make_float2(0.f, 0.f);
-          const int e1 = min(N, e0 + 32 * Q);
-          for (int e = e0; e < e1; e += Q) t = cadd(t, cjmul(ci[e], cj[e]));
-          acc = cadd(acc, make_double2(t.x, t.y));
-        }
+        const float2* ci = Cs + (size_t)i * LDC;
+        const float2* cj = Cs + (size_t)j * LDC;
+        for (int e = q; e < N; e += Q) acc = cadd(acc, cjmul(ci[e], cj[e]));
       }
       for (int o = Q / 2; o > 0; o >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
       }
       if (p < npair && q == 0) {  // G[i][j] = sum conj(C_i) C_j (column-major, ld 16); Hermitian
-        G[i + j * 16] = acc;
-        G[j + i * 16] = cconj(acc);
+        if (i == j) acc.y = 0.f;
+        Gf[i + j * 16] = acc;
+        Gf[j + i * 16] = cconj(acc);
       }
     }
     __syncthreads();
-    // Cholesky G = L L^H, Ri = L^{-H}, Ra = Ri (first pass) or Ra Ri (second), FP32 copy of Ri
+    // G = L L^H, Rf = L^{-H}
     if (warp == 0) {
-      if (sd::cholesky(s, G, 16)) {
-        if (lane == 0) fail[0] = 1;
-      } else {
-        for (int e = lane; e < s * s; e += 32) Ri[(e % s) + (e / s) * 16] = make_double2((e % s) == (e / s) ? 1.0 : 0.0, 0.0);
-        sd::wsync();
-        sd::trsm_lower_h_left(s, s, G, 16, Ri, 16);
-        if (pass == 0) {
-          for (int e = lane; e < s * s; e += 32) Ra[(e % s) + (e / s) * 16] = Ri[(e % s) + (e / s) * 16];
-        } else {
-          sd::gemm_nn(s, s, s, Ra, 16, Ri, 16, Tm, 16);
-          for (int e = lane; e < s * s; e += 32) Ra[(e % s) + (e / s) * 16] = Tm[(e % s) + (e / s) * 16];
-        }
-        for (int e = lane; e < s * s; e += 32) {
-          const double2 r = Ri[(e % s) + (e / s) * 16];
-          Rf[(e % s) + (e / s) * 16] = make_float2((float)r.x, (float)r.y);
-        }
-      }
+      const int bad = chol16_warp(s, Gf, Lf, rdiag);
+      linvh16_warp(Lf, rdiag, Rf);
+      if (bad && lane == 0) fail[0] = 1;
     }
     __syncthreads();
     if (fail[0]) {
       if (tid == 0) ok[b] = 0;
       return;
     }
-    // C := C Ri, element by element (all s values of an element in registers)
+    // Ra := Rf (first pass) or Ra Rf (second); both upper triangular
+    float2 ra = make_float2(0.f, 0.f);
+    if (tid < 256) {
+      const int ri = tid & 15, rj = tid >> 4;
+      if (pass == 0) {
+        ra = Rf[tid];
+      } else {
+#pragma unroll
+        for (int p = 0; p < 16; ++p) ra = cfma(Raf[ri + p * 16], Rf[p + rj * 16], ra);
+      }
+    }
+    // C := C Rf, element by element (all s values of an element in registers)
     for (int e = tid; e < N; e += RS_T) {
       float2 v[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) v[c] = c < s ? Cs[(size_t)c * N + e] : make_float2(0.f, 0.f);
+      for (int c = 0; c < 16; ++c) v[c] = c < s ? Cs[(size_t)c * LDC + e] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int jj = 0; jj < 16; ++jj) {
         if (jj < s) {
           float2 o = make_float2(0.f, 0.f);
 #pragma unroll
           for (int c = 0; c < 16; ++c)
-            if (c <= jj) o = cfma(v[c], Rf[c + jj * 16], o);  // Ri is upper triangular
-          Cs[(size_t)jj * N + e] = o;
+            if (c <= jj) o = cfma(v[c], Rf[c + jj * 16], o);  // Rf is upper triangular
+          Cs[(size_t)jj * LDC + e] = o;
         }
       }
     }
     __syncthreads();
+    if (tid < 256) Raf[tid] = ra;
   }
   // write C; coef = C^H r
   float acc[32];
@@ -354,7 +414,7 @@ __global__ void __launch_bounds__(RS_T) k_recstart32(int n, int k, int s, const 
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       if (c < s) {
-        const float2 ce = Cs[(size_t)c * N + e];
+        const float2 ce = Cs[(size_t)c * LDC + e];
         C[(size_t)b * ss + (size_t)c * N + e] = ce;
         acc[2 * c] += ce.x * re.x + ce.y * re.y;
         acc[2 * c + 1] += ce.x * re.y - ce.y * re.x;
@@ -363,11 +423,6 @@ __global__ void __launch_bounds__(RS_T) k_recstart32(int n, int k, int s, const 
   }
   warp_reduce_scatter32<float>(acc);
   red[warp * 32 + lane] = acc[0];
-  // FP32 copy of Ra for U = Ut Ra
-  for (int e = tid; e < 256; e += RS_T) {
-    const double2 r = Ra[e];
-    Rf[e] = make_float2((float)r.x, (float)r.y);
-  }
   __syncthreads();
   if (tid < 32) {
     float v = 0.f;
@@ -389,10 +444,10 @@ __global__ void __launch_bounds__(RS_T) k_recstart32(int n, int k, int s, const 
         float2 uj = make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 16; ++c)
-          if (c <= jj) uj = cfma(ut[c], Rf[c + jj * 16], uj);  // Ra is upper triangular
+          if (c <= jj) uj = cfma(ut[c], Raf[c + jj * 16], uj);  // Ra is upper triangular
         U[(size_t)b * ss + (size_t)jj * N + e] = uj;
         xs = cfma(uj, coef[jj], xs);
-        rs = csub(rs, cmul(Cs[(size_t)jj * N + e], coef[jj]));
+        rs = csub(rs, cmul(Cs[(size_t)jj * LDC + e], coef[jj]));
       }
     }
     X[(size_t)b * N + e] = xs;
@@ -402,8 +457,8 @@ __global__ void __launch_bounds__(RS_T) k_recstart32(int n, int k, int s, const 
 }
 
 size_t recstart32_smem_bytes(int s, int N) {
-  return sizeof(double2) * 4 * 256 + sizeof(float2) * 256 + sizeof(float) * (RS_T / 32) * 32 +
-         sizeof(float2) * 16 + sizeof(int) * 4 + sizeof(float2) * (size_t)s * N;
+  return sizeof(float2) * 4 * 256 + sizeof(float) * (RS_T / 32) * 32 + sizeof(float2) * 16 + sizeof(float) * 32 +
+         sizeof(int) * 4 + sizeof(float2) * (size_t)s * (N + 1);
 }
 
 __global__ void k_chol_rinv(int s, const int* __restrict__ list, const int* __restrict__ count,

@@ -71,8 +71,11 @@ struct Seg2 {
 
 // ----------------------------------------------------------------- lists
 // Rebuild an ordered list of systems: out = [b in in_list : flag[b] > 0].
+// host_count (optional, mapped pinned memory) receives a copy of the count
+// that the host may read once the kernel has completed.
 __global__ void k_compact(const int* __restrict__ in_list, const int* __restrict__ in_count,
-                          const int* __restrict__ flag, int* __restrict__ out_list, int* __restrict__ out_count);
+                          const int* __restrict__ flag, int* __restrict__ out_list, int* __restrict__ out_count,
+                          int* host_count = nullptr);
 __global__ void k_iota(int B, int* list, int* count);
 
 // ------------------------------------------------------ Givens least squares
@@ -541,8 +544,9 @@ __global__ void k_chol_rinv(int s, const int* __restrict__ list, const int* __re
 // Recycle start of the FP32 solves, fused into one CTA per listed system
 // (the FP64 path runs the same steps as separate kernels):
 //   C = T(v_b) Ut = Ut D(v_b)^{-1} - C0Ut,
-//   two CholQR passes (G = C^H C = L L^H, C := C L^{-H}), Ra = product of the
-//   L^{-H} factors, C written out, U = Ut Ra,
+//   two CholQR passes (G = C^H C = L L^H, C := C L^{-H}; the 16 x 16 factor
+//   and its inverse in one warp's registers), Ra = product of the L^{-H}
+//   factors, C written out, U = Ut Ra,
 //   c = C^H r, x += U c, r -= C c.
 // C_b stays in shared memory between the steps. ok[b] = 0 when a Cholesky
 // factor fails (the projection is then not applied to that system).

@@ -181,6 +181,16 @@ int KrylovWS<T2>::ensure_side() {
 }
 
 template <typename T2>
+int KrylovWS<T2>::ensure_poll() {
+  if (poll_host) return LYAP_OK;
+  for (int i = 0; i < POLL_RING; ++i) LY_CUDA(cudaEventCreateWithFlags(&poll_ev[i], cudaEventDisableTiming));
+  LY_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&poll_host), sizeof(int) * POLL_RING, cudaHostAllocMapped));
+  for (int i = 0; i < POLL_RING; ++i) poll_host[i] = 1;
+  LY_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&poll_dev), poll_host, 0));
+  return LYAP_OK;
+}
+
+template <typename T2>
 KrylovWS<T2>::~KrylovWS() {
   if (side) {
     cudaStreamSynchronize(side);
@@ -189,6 +199,9 @@ KrylovWS<T2>::~KrylovWS() {
   if (side_start) cudaEventDestroy(side_start);
   if (side_done) cudaEventDestroy(side_done);
   if (rec_ok_host) cudaFreeHost(rec_ok_host);
+  for (int i = 0; i < POLL_RING; ++i)
+    if (poll_ev[i]) cudaEventDestroy(poll_ev[i]);
+  if (poll_host) cudaFreeHost(poll_host);
 }
 
 template <typename T2>
@@ -366,6 +379,7 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
   }
 
   const int maxit = (prm.inject & LYAP_INJECT_FORCE_MAXIT) ? 1 : prm.maxit;
+  LY_TRY(ws.ensure_poll());
   const size_t css = (size_t)smax * NS;
   int chunk_count = B;
   int guard = 0;
@@ -386,7 +400,15 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     int* Lnext = Lb;
     int* cnext = cb;
     const int mc = m - s_cur;
+    constexpr int LAG = KrylovWS<T2>::POLL_LAG, RING = KrylovWS<T2>::POLL_RING;
     for (int j = 0; j < mc; ++j) {
+      if (j >= LAG) {
+        // once every system of the chunk has stopped, the cycle's remaining
+        // steps would launch on empty lists: stop queueing them
+        const int q = (j - LAG) % RING;
+        LY_CUDA(cudaEventSynchronize(ws.poll_ev[q]));
+        if (*static_cast<volatile int*>(ws.poll_host + q) == 0) break;
+      }
       T2* Vj = ws.V.p;  // slot j of each system: V + b*(m+1)*N + j*N
       T2* Zj = ws.Z.p;
       LY_TRY(op.precond(Lcur, ccur, B, Vj + (size_t)j * NS, (size_t)(m + 1) * NS, Zj + (size_t)j * NS,
@@ -405,8 +427,10 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
         lyap_count_launch();
         prof_end(ph, st, 2.0 * 2.0 * 8.0 * nb * N, (3.0 * nb + 7.0) * N * sizeof(T2), 0, ccur);
       }
-      kry::k_compact<<<1, 1024, 0, st>>>(Lcur, ccur, ws.flag.p, Lnext, cnext); lyap_count_launch();
+      kry::k_compact<<<1, 1024, 0, st>>>(Lcur, ccur, ws.flag.p, Lnext, cnext, ws.poll_dev + j % RING);
+      lyap_count_launch();
       LY_CUDA(cudaGetLastError());
+      LY_CUDA(cudaEventRecord(ws.poll_ev[j % RING], st));
       std::swap(Lcur, Lnext);
       std::swap(ccur, cnext);
     }

@@ -45,8 +45,17 @@ struct KrylovWS {
   int* rec_ok_host = nullptr;  // pinned
   DevBuf<int> rec_ok_dev;
   DevBuf<double> vinv_last;
+  // Early exit from an Arnoldi cycle: each step's active count is written to
+  // a ring of mapped pinned slots, with an event per step; the host reads
+  // the count of a step POLL_LAG steps back before queueing the next one.
+  static constexpr int POLL_LAG = 2;
+  static constexpr int POLL_RING = POLL_LAG + 1;
+  int* poll_host = nullptr;  // POLL_RING ints, pinned and mapped
+  int* poll_dev = nullptr;   // device view of poll_host
+  cudaEvent_t poll_ev[POLL_RING] = {};
   int ensure(int B, int N, int m, int s);
   int ensure_side();
+  int ensure_poll();
   size_t bytes() const;
   KrylovWS() = default;
   KrylovWS(const KrylovWS&) = delete;
