@@ -77,6 +77,19 @@ __host__ __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return
 template <>
 __host__ __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
 
+// FP32 arithmetic on vectors stored in either precision (no FP64 work when
+// the storage is FP32)
+__host__ __device__ __forceinline__ float2 to_f2(float2 a) { return a; }
+__host__ __device__ __forceinline__ float2 to_f2(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <typename T2>
+__host__ __device__ __forceinline__ T2 from_f2(float2 a);
+template <>
+__host__ __device__ __forceinline__ float2 from_f2<float2>(float2 a) { return a; }
+template <>
+__host__ __device__ __forceinline__ double2 from_f2<double2>(float2 a) { return make_double2(a.x, a.y); }
+__host__ __device__ __forceinline__ float2 add_f2(float2 o, float2 x) { return make_float2(o.x + x.x, o.y + x.y); }
+__host__ __device__ __forceinline__ double2 add_f2(double2 o, float2 x) { return make_double2(o.x + x.x, o.y + x.y); }
+
 // Convert a double2 coefficient to the vector type T2.
 template <typename T2>
 __host__ __device__ __forceinline__ T2 cvt(double2 a) {

@@ -126,6 +126,7 @@ struct lyap_seed {
   DevBuf<double2> Ub, Vb;
   // Gd[(p*k + t)*n + i] = [Lc (Ub_p o Vb_t)]_i: diagonal blocks of N^T L0^{-1} M.
   DevBuf<double2> Gd;
+  DevBuf<float2> Gdf;  // FP32 copy of Gd: the preconditioner's block solves run in FP32
   // Capacitance right-hand side of the shifted system T(v) W' = Ph (n x k).
   DevBuf<double2> Ph;
   // Trace vector: f(v) = f0 + Re sum(h o W').

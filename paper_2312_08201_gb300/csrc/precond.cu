@@ -87,6 +87,7 @@ int orth(cusolverDnHandle_t sol, int m, int L, double2* Y, cudaStream_t st) {
 
 // Solve K_j x = x in place for the k x k block of row j,
 //   K_j[t][p] = delta_tp / v_t - Gd[j, p, t]   (transposed when gT),
+// in FP32 throughout (Gd: the seed's FP32 copy, 1/v_t rounded to FP32),
 // by Gaussian elimination with partial pivoting. k is a template argument and
 // each elimination step is its own instantiation (Elim<K, C>), so every index
 // is a compile-time constant and the block stays in registers; rows are
@@ -141,7 +142,7 @@ struct Elim<K, K> {
 };
 
 template <int K>
-__device__ __forceinline__ void bsolve(int n, int j, const double2* __restrict__ Gd, int gT, const double (&vb)[K],
+__device__ __forceinline__ void bsolve(int n, int j, const float2* __restrict__ Gd, int gT, const float (&vb)[K],
                                        float2 (&x)[K]) {
   float Ar[K][K], Ai[K][K];
 #pragma unroll
@@ -149,9 +150,9 @@ __device__ __forceinline__ void bsolve(int n, int j, const double2* __restrict__
 #pragma unroll
     for (int p = 0; p < K; ++p) {
       const size_t gi = gT ? ((size_t)(t * K + p) * n + j) : ((size_t)(p * K + t) * n + j);
-      const double2 g = Gd[gi];
-      Ar[t][p] = (float)((t == p ? vb[t] : 0.0) - g.x);
-      Ai[t][p] = (float)(-g.y);
+      const float2 g = Gd[gi];
+      Ar[t][p] = (t == p ? vb[t] : 0.f) - g.x;
+      Ai[t][p] = -g.y;
     }
   Elim<K, 0>::run(Ar, Ai, x);
 #pragma unroll
@@ -166,16 +167,17 @@ __device__ __forceinline__ void bsolve(int n, int j, const double2* __restrict__
 }
 
 template <int K>
-__device__ __forceinline__ void load_vb(const double* __restrict__ vinv, int b, double (&vb)[K]) {
+__device__ __forceinline__ void load_vb(const double* __restrict__ vinv, int b, float (&vb)[K]) {
 #pragma unroll
-  for (int t = 0; t < K; ++t) vb[t] = vinv[(size_t)b * K + t];
+  for (int t = 0; t < K; ++t) vb[t] = (float)vinv[(size_t)b * K + t];
 }
+
 
 // Cap_b^{-1} with Cap_b = I - Ml^T K_b^{-1} Nl (r x r, column-major), one CTA
 // per system: the product accumulates over chunks of J rows, then
 // Gauss-Jordan elimination with partial pivoting inverts it in shared memory.
 template <int K>
-__global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const double2* __restrict__ Gd,
+__global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const float2* __restrict__ Gd,
                                                   const double* __restrict__ vinv, const float2* __restrict__ Nl,
                                                   const float2* __restrict__ Ml, int ldr, float2* __restrict__ cinv) {
   extern __shared__ float2 sw[];  // [J x K x r] K^{-1} Nl rows, [J x K x r] Ml rows; then C, Inv (r x r each)
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const double2* _
   constexpr int J = 8;
   float2* sm = sw + (size_t)J * K * r;
   const int b = blockIdx.x;
-  double vb[K];
+  float vb[K];
   load_vb<K>(vinv, b, vb);
   const int nout = r * r;
   // each thread owns a 4 x 4 tile of Cap (rows l0.., columns l20..): one pair
@@ -318,7 +320,7 @@ struct PrecTile {
 
 template <typename T2, int K>
 __global__ void __launch_bounds__(WT) k_prec_a(int n, const int* __restrict__ list, const int* __restrict__ count,
-                                               const double2* __restrict__ Gd, int adj,
+                                               const float2* __restrict__ Gd, int adj,
                                                const double* __restrict__ vinv, const T2* __restrict__ In,
                                                size_t in_ss, T2* __restrict__ Out, size_t out_ss, int r,
                                                const float2* __restrict__ Bop, int ldr, float2* __restrict__ Cp,
@@ -335,18 +337,15 @@ __global__ void __launch_bounds__(WT) k_prec_a(int n, const int* __restrict__ li
     float2 x[K];
     if (s0 + sl < nact && j < n) {
       const int b = list[s0 + sl];
-      double vb[K];
+      float vb[K];
       load_vb<K>(vinv, b, vb);
       const T2* in = In + (size_t)b * in_ss;
 #pragma unroll
-      for (int t = 0; t < K; ++t) {
-        const double2 v = to_d2(in[(size_t)t * n + j]);
-        x[t] = make_float2((float)v.x, (float)v.y);
-      }
+      for (int t = 0; t < K; ++t) x[t] = to_f2(in[(size_t)t * n + j]);
       bsolve<K>(n, j, Gd, adj, vb, x);
       T2* out = Out + (size_t)b * out_ss;
 #pragma unroll
-      for (int t = 0; t < K; ++t) out[(size_t)t * n + j] = from_d2<T2>(make_double2(x[t].x, x[t].y));
+      for (int t = 0; t < K; ++t) out[(size_t)t * n + j] = from_f2<T2>(x[t]);
     } else {
 #pragma unroll
       for (int t = 0; t < K; ++t) x[t] = make_float2(0.f, 0.f);
@@ -380,7 +379,7 @@ __global__ void __launch_bounds__(WT) k_prec_a(int n, const int* __restrict__ li
 
 template <typename T2, int K>
 __global__ void __launch_bounds__(WT) k_prec_b(int n, const int* __restrict__ list, const int* __restrict__ count,
-                                               const double2* __restrict__ Gd, int adj,
+                                               const float2* __restrict__ Gd, int adj,
                                                const double* __restrict__ vinv, T2* __restrict__ Out, size_t out_ss,
                                                int r, const float2* __restrict__ Aop, int ldr,
                                                const float2* __restrict__ cinv, const float2* __restrict__ Cp,
@@ -446,15 +445,14 @@ __global__ void __launch_bounds__(WT) k_prec_b(int n, const int* __restrict__ li
     for (int u = 0; u < PG; ++u) {
       if (s0 + g0 + u >= nact) break;
       const int b = list[s0 + g0 + u];
-      double vb[K];
+      float vb[K];
       load_vb<K>(vinv, b, vb);
       bsolve<K>(n, j, Gd, adj, vb, x[u]);
       T2* out = Out + (size_t)b * out_ss;
 #pragma unroll
       for (int t = 0; t < K; ++t) {
         const size_t e2 = (size_t)t * n + j;
-        const double2 zd = to_d2(out[e2]);
-        out[e2] = from_d2<T2>(make_double2(zd.x + x[u][t].x, zd.y + x[u][t].y));
+        out[e2] = add_f2(out[e2], x[u][t]);
       }
     }
   }
@@ -474,7 +472,7 @@ int launch_cap_build(lyap_seed* sd, int r, int B, const double* vinv, const Wood
                                    (int)cap_smem<K>(RMAX));
   });
   LY_CUDA(attr_rc);
-  k_cap_build<K><<<B, WT, cap_smem<K>(r), st>>>(sd->n, r, sd->Gd.p, vinv, ws.Nl, ws.Ml, ws.ldr, ws.cinv);
+  k_cap_build<K><<<B, WT, cap_smem<K>(r), st>>>(sd->n, r, sd->Gdf.p, vinv, ws.Nl, ws.Ml, ws.ldr, ws.cinv);
   return LYAP_OK;
 }
 
@@ -488,10 +486,10 @@ void launch_prec(lyap_seed* sd, const WoodState* ws, bool adjoint, const double*
   const dim3 grid(ntx, (B + PST - 1) / PST);
   const float2* A = ws ? (adjoint ? ws->Ml : ws->Nl) : nullptr;
   const float2* Bm = ws ? (adjoint ? ws->Nl : ws->Ml) : nullptr;
-  k_prec_a<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv, In, in_ss, Out, out_ss, r, Bm,
+  k_prec_a<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, In, in_ss, Out, out_ss, r, Bm,
                                        ws ? ws->ldr : 0, ws ? ws->cpart : nullptr, B);
   if (r > 0)
-    k_prec_b<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gd.p, adjoint ? 1 : 0, vinv, Out, out_ss, r, A, ws->ldr,
+    k_prec_b<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, Out, out_ss, r, A, ws->ldr,
                                          ws->cinv, ws->cpart, B, ntx);
 }
 

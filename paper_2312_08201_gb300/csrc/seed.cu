@@ -112,6 +112,12 @@ __global__ void k_fill_cauchy(int n, const double2* __restrict__ lam, double2* _
   }
 }
 
+// out = in rounded to FP32
+__global__ void k_round_f32(size_t count, const double2* __restrict__ in, float2* __restrict__ out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
 // Y[:, p*k + t] = Ub[:, p] o Vb[:, t]
 __global__ void k_panel_products(int n, int k, const double2* __restrict__ Ub, const double2* __restrict__ Vb,
                                  double2* __restrict__ Y) {
@@ -429,9 +435,13 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
     LY_CUDA(cudaGetLastError());
     LY_TRY(sd->Gd.alloc((size_t)n * k * k));
     LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k * k, n, one, W1.p, n, Y.p, n, zero, sd->Gd.p, n));
+    LY_TRY(sd->Gdf.alloc((size_t)n * k * k));
+    k_round_f32<<<grid_for((size_t)n * k * k), 256, 0, st>>>((size_t)n * k * k, sd->Gd.p, sd->Gdf.p);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
   }
   LY_CUDA(cudaStreamSynchronize(st));
   sd->resident_bytes = sd->lam.bytes() + sd->Qp.bytes() + sd->Qi.bytes() + sd->Ub.bytes() + sd->Vb.bytes() +
-                       sd->Gd.bytes() + sd->Ph.bytes() + sd->h.bytes();
+                       sd->Gd.bytes() + sd->Gdf.bytes() + sd->Ph.bytes() + sd->h.bytes();
   return LYAP_OK;
 }
