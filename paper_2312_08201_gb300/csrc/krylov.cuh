@@ -99,37 +99,42 @@ struct LsqArgs {
 // new rotation zeroes H[j+1, j]. |g[j+1]| is the residual norm of the
 // projected problem; when it reaches tolabs, or H[j+1, j] vanishes
 // (breakdown: exact solution in the space), the system stops this cycle.
-// Run by one thread per system, right after the column is complete.
-__device__ __forceinline__ void lsq_column(int b, int j, int m, double2* __restrict__ H, const LsqArgs& L) {
-  double2* h = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
-  double2* h0 = L.H0 + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
-  for (int i = 0; i <= j + 1; ++i) h0[i] = h[i];
-  double* c = L.cs + (size_t)b * m;
-  double2* s = L.sn + (size_t)b * m;
-  double2* gb = L.g + (size_t)b * (m + 1);
+// Run by one thread per system, right after the column is complete: the
+// column (h, j + 2 entries) and the previous rotations (cs_s, sn_s) are in
+// shared memory, and gj = g[j], tolabs, iterations done were loaded before
+// the column was; only stores go to global memory.
+__device__ __forceinline__ void lsq_column(int b, int j, int m, double2* __restrict__ H, const double2* h,
+                                           const double* cs_s, const double2* sn_s, double2 gj, double tola,
+                                           int iters_done, const LsqArgs& L) {
+  double2* hg = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
+  double2 top = h[0];
   for (int i = 0; i < j; ++i) {
-    const double2 top = h[i], bot = h[i + 1];
-    h[i] = cadd(cscale(top, c[i]), cmul(s[i], bot));
-    h[i + 1] = csub(cscale(bot, c[i]), cjmul(s[i], top));
+    const double2 bot = h[i + 1];
+    const double ci = cs_s[i];
+    const double2 si = sn_s[i];
+    hg[i] = cadd(cscale(top, ci), cmul(si, bot));
+    top = csub(cscale(bot, ci), cjmul(si, top));
   }
+  const double2 low = h[j + 1];
   double cj;
   double2 sj;
-  sd::givens<double2, double>(h[j], h[j + 1], cj, sj);
-  const double2 rho = cadd(cscale(h[j], cj), cmul(sj, h[j + 1]));
-  const double sub = h0[j + 1].x;
-  h[j] = rho;
-  h[j + 1] = make_double2(0.0, 0.0);
-  c[j] = cj;
-  s[j] = sj;
-  const double2 gj = gb[j];
+  sd::givens<double2, double>(top, low, cj, sj);
+  const double2 rho = cadd(cscale(top, cj), cmul(sj, low));
+  const double sub = low.x;
+  hg[j] = rho;
+  hg[j + 1] = make_double2(0.0, 0.0);
+  L.cs[(size_t)b * m + j] = cj;
+  L.sn[(size_t)b * m + j] = sj;
+  double2* gb = L.g + (size_t)b * (m + 1);
   gb[j] = cscale(gj, cj);
-  gb[j + 1] = cscale(cjmul(sj, gj), -1.0);
-  const double res = sqrt(cabs2(gb[j + 1]));
+  const double2 gn = cscale(cjmul(sj, gj), -1.0);
+  gb[j + 1] = gn;
+  const double res = sqrt(cabs2(gn));
   int st = ST_RUN;
   if (!isfinite(res) || !isfinite(rho.x) || !isfinite(rho.y)) st = ST_NONFINITE;
-  else if (res <= L.tolabs[b]) st = ST_CONV;
+  else if (res <= tola) st = ST_CONV;
   else if (!(sub > 1e-14 * sqrt(cabs2(rho)))) st = ST_CONV;  // invariant subspace: exact in the space
-  else if (L.iters_done[b] + j + 1 >= L.maxit) st = ST_MAXIT;
+  else if (iters_done + j + 1 >= L.maxit) st = ST_MAXIT;
   L.jstop[b] = j + 1;  // provisional when still running (the cycle may end here)
   if (st != ST_RUN) L.flag[b] = -st;  // negative: stopped this cycle with a final status
 }
@@ -171,6 +176,9 @@ __global__ void __launch_bounds__(OT, sizeof(T2) == 8 ? 2 : 1) k_ortho(int N, in
   constexpr int NW = OT / 32;
   __shared__ R red[NW][32];
   __shared__ T2 coef[2][64];
+  __shared__ double2 hcol[64];  // new column of H (m + 1 <= 61 entries)
+  __shared__ double cs_s[64];   // previous Givens rotations
+  __shared__ double2 sn_s[64];
   const int slot = blockIdx.x;
   if (slot >= *count) return;
   const int b = list[slot];
@@ -259,19 +267,37 @@ __global__ void __launch_bounds__(OT, sizeof(T2) == 8 ? 2 : 1) k_ortho(int N, in
   R tot = R(0);
 #pragma unroll
   for (int w2 = 0; w2 < NW; ++w2) tot += red[w2][0];
-  const double nrm = sqrt((double)tot);
-  double2* Hc = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
+  double2* H0c = L.H0 + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
   double2* Bc = Bk + (size_t)b * smax * m + (size_t)j * smax;
   if (threadIdx.x < nb) {
     const int q = threadIdx.x;
     const double2 cval = cadd(to_d2(coef[0][q]), to_d2(coef[1][q]));
-    if (q < s_cur) Bc[q] = cval;
-    else Hc[q - s_cur] = cval;
+    if (q < s_cur) {
+      Bc[q] = cval;
+    } else {
+      H0c[q - s_cur] = cval;
+      hcol[q - s_cur] = cval;
+    }
   }
-  if (threadIdx.x == 0) Hc[j + 1] = make_double2(nrm, 0.0);
+  if (threadIdx.x >= 32 && threadIdx.x < 32 + j) {  // the previous rotations
+    cs_s[threadIdx.x - 32] = L.cs[(size_t)b * m + threadIdx.x - 32];
+    sn_s[threadIdx.x - 32] = L.sn[(size_t)b * m + threadIdx.x - 32];
+  }
+  double2 gj = make_double2(0.0, 0.0);
+  double tola = 0.0;
+  int itd = 0;
+  if (threadIdx.x == 0) {
+    gj = L.g[(size_t)b * (m + 1) + j];
+    tola = L.tolabs[b];
+    itd = L.iters_done[b];
+    const double nrm = sqrt((double)tot);
+    H0c[j + 1] = make_double2(nrm, 0.0);
+    hcol[j + 1] = make_double2(nrm, 0.0);
+  }
   __syncthreads();
-  if (threadIdx.x == 0) lsq_column(b, j, m, H, L);  // while the others normalise w
-  const R inv = nrm > 0.0 ? (R)(1.0 / nrm) : R(0);
+  if (threadIdx.x == 0) lsq_column(b, j, m, H, hcol, cs_s, sn_s, gj, tola, itd, L);  // while the others normalise w
+  const R rn = sqrt(tot);
+  const R inv = rn > R(0) ? R(1) / rn : R(0);
   for (int e = threadIdx.x; e < N; e += OT) w[e] = cscale(w[e], inv);
 }
 
@@ -293,11 +319,12 @@ __global__ void __launch_bounds__(NT) k_cycle_start(int N, int m, const int* __r
   RT s[1] = {RT(0)};
   for (int e = threadIdx.x; e < N; e += NT) s[0] += cabs2(r[e]);
   block_sum<1, RT>(s, red);
-  double beta = sqrt((double)s[0]);
+  const RT rn = sqrt(s[0]);
   T2* v0 = V + (size_t)b * (m + 1) * N;
-  const RT inv = beta > 0 ? (RT)(1.0 / beta) : RT(0);
+  const RT inv = rn > RT(0) ? RT(1) / rn : RT(0);
   for (int e = threadIdx.x; e < N; e += NT) v0[e] = cscale(r[e], inv);
   if (threadIdx.x == 0) {
+    const double beta = sqrt((double)s[0]);
     double2* gb = g + (size_t)b * (m + 1);
     gb[0] = make_double2(beta, 0.0);
     beta_out[b] = beta;

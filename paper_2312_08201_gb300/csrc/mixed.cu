@@ -131,10 +131,7 @@ __global__ void k_epi(int n, int k, const int* __restrict__ list, const int* __r
   const float2* D2 = reinterpret_cast<const float2*>(D);
   const int ld2 = ldd / 2;
   float2 w[8];
-  for (int p = 0; p < k; ++p) {
-    const double2 x = to_d2(In[(size_t)b * in_ss + (size_t)p * n + i]);
-    w[p] = make_float2((float)x.x, (float)x.y);
-  }
+  for (int p = 0; p < k; ++p) w[p] = to_f2(In[(size_t)b * in_ss + (size_t)p * n + i]);
   for (int t = 0; t < k; ++t) {
     float2 o = make_float2(0.f, 0.f);
     for (int p = 0; p < k; ++p) {
@@ -144,7 +141,7 @@ __global__ void k_epi(int n, int k, const int* __restrict__ list, const int* __r
     }
     float2 y = o;
     if (mode == CAP_T) y = csub(cscale(w[t], (float)vinv[(size_t)b * k + t]), o);
-    Out[(size_t)b * out_ss + (size_t)t * n + i] = from_d2<T2>(to_d2(y));
+    Out[(size_t)b * out_ss + (size_t)t * n + i] = from_f2<T2>(y);
   }
 }
 

@@ -173,6 +173,13 @@ __device__ __forceinline__ void load_vb(const double* __restrict__ vinv, int b, 
 }
 
 
+// Rows of Nl and Ml staged per step of the capacitance product: J K r
+// entries of each, about 32 K-blocks' worth of rows.
+template <int K>
+struct CapRows {
+  static constexpr int J = K <= 2 ? 32 : (K <= 4 ? 16 : 8);
+};
+
 // Cap_b^{-1} with Cap_b = I - Ml^T K_b^{-1} Nl (r x r, column-major), one CTA
 // per system: the product accumulates over chunks of J rows, then
 // Gauss-Jordan elimination with partial pivoting inverts it in shared memory.
@@ -180,11 +187,12 @@ template <int K>
 __global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const float2* __restrict__ Gd,
                                                   const double* __restrict__ vinv, const float2* __restrict__ Nl,
                                                   const float2* __restrict__ Ml, int ldr, float2* __restrict__ cinv) {
-  extern __shared__ float2 sw[];  // [J x K x r] K^{-1} Nl rows, [J x K x r] Ml rows; then C, Inv (r x r each)
+  extern __shared__ float2 sw[];  // [J x K x rp] K^{-1} Nl rows, [J x K x rp] Ml rows; then C, Inv (r x r each)
   __shared__ float2 fcol[RMAX];
   __shared__ int piv_s;
-  constexpr int J = 8;
-  float2* sm = sw + (size_t)J * K * r;
+  constexpr int J = CapRows<K>::J;
+  const int rp = r | 1;  // odd row length: the fill's stores spread over the banks
+  float2* sm = sw + (size_t)J * K * rp;
   const int b = blockIdx.x;
   float vb[K];
   load_vb<K>(vinv, b, vb);
@@ -200,8 +208,9 @@ __global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const float2* __
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
   for (int j0 = 0; j0 < n; j0 += J) {
+    // consecutive threads take consecutive rows j of a column l (coalesced)
     for (int e = threadIdx.x; e < J * r; e += WT) {
-      const int jj = e / r, l = e % r, j = j0 + jj;
+      const int jj = e % J, l = e / J, j = j0 + jj;
       float2 x[K];
       if (j < n) {
 #pragma unroll
@@ -210,8 +219,8 @@ __global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const float2* __
       }
 #pragma unroll
       for (int t = 0; t < K; ++t) {
-        sw[((size_t)jj * K + t) * r + l] = j < n ? x[t] : make_float2(0.f, 0.f);
-        sm[((size_t)jj * K + t) * r + l] = j < n ? Ml[(size_t)t * n + j + (size_t)l * ldr] : make_float2(0.f, 0.f);
+        sw[((size_t)jj * K + t) * rp + l] = j < n ? x[t] : make_float2(0.f, 0.f);
+        sm[((size_t)jj * K + t) * rp + l] = j < n ? Ml[(size_t)t * n + j + (size_t)l * ldr] : make_float2(0.f, 0.f);
       }
     }
     __syncthreads();
@@ -220,8 +229,8 @@ __global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const float2* __
         float2 mv[4], wv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          mv[u] = l0 + u < r ? sm[(size_t)q * r + l0 + u] : make_float2(0.f, 0.f);
-          wv[u] = l20 + u < r ? sw[(size_t)q * r + l20 + u] : make_float2(0.f, 0.f);
+          mv[u] = l0 + u < r ? sm[(size_t)q * rp + l0 + u] : make_float2(0.f, 0.f);
+          wv[u] = l20 + u < r ? sw[(size_t)q * rp + l20 + u] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -460,7 +469,7 @@ __global__ void __launch_bounds__(WT) k_prec_b(int n, const int* __restrict__ li
 
 template <int K>
 size_t cap_smem(int r) {
-  return sizeof(float2) * std::max<size_t>((size_t)2 * 8 * K * r, (size_t)2 * r * r);
+  return sizeof(float2) * std::max<size_t>((size_t)2 * CapRows<K>::J * K * (r | 1), (size_t)2 * r * r);
 }
 
 template <int K>
