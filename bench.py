@@ -36,7 +36,8 @@ SMS = 152
 # `bench.py --steps 1 --warmup 3 --no-cpu-baseline --profile-sweep` (cold caches: ncu
 # flushes them before every launch). Valid for the kernels as they stand; a kernel
 # change invalidates its entry.
-MEASURED_TRAFFIC_PER_LAUNCH = {"ortho": 71.23e6, "tc_gemm": 14.11e6, "precond": 15.10e6, "oz_gemm": 215.09e6}
+# "precond" counts one k_prec_a + k_prec_b pair as a launch.
+MEASURED_TRAFFIC_PER_LAUNCH = {"ortho": 113.99e6, "tc_gemm": 23.02e6, "precond": 26.74e6, "oz_gemm": 271.95e6}
 FP32_LANES_PER_SM = 128.0  # FP32 lane-instructions per clock per SM
 L2_FLUSH_BYTES = 256 << 20
 
