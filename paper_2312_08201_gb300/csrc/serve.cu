@@ -77,7 +77,8 @@ struct SeedSlot {
 // workspace (basis, preconditioned basis, recycled pairs, iterate, residual),
 // the small dense matrices, the FP64 solution/residual vectors, and for the
 // mixed path the float-float residual panel (k^2 n pairs of float2) and the
-// Woodbury capacitance inverses. Gradients double the solve part.
+// Woodbury capacitance inverses and partial sums. Gradients double the solve
+// part.
 size_t request_bytes(const lyap_seed* sd, const lyap_opts& o, int nv, bool grad) {
   const size_t n = (size_t)sd->n, k = (size_t)sd->k, N = n * k;
   const size_t vec = o.precision == LYAP_FP64 ? 16 : 8;
@@ -85,7 +86,7 @@ size_t request_bytes(const lyap_seed* sd, const lyap_opts& o, int nv, bool grad)
   size_t per = (size_t)(2 * o.m + 2 * o.s + 6) * N * vec + LD * LD * 8 * 16 + (size_t)4 * N * 16;
   if (grad) per *= 2;
   if (o.precision != LYAP_FP64) per += k * k * n * 16;
-  if (o.pbar > 0) per += (size_t)2 * o.pbar * o.pbar * 8;
+  if (o.pbar > 0) per += (size_t)2 * o.pbar * o.pbar * 8 + (n / 32 + 2) * (size_t)o.pbar * 8;  // Cap^{-1}, partials
   return per * (size_t)nv;
 }
 
