@@ -320,6 +320,24 @@ def run_kernel_probe(args, local):
                           peak_source=how)), flush=True)
 
 
+def whole_job_rate(local_ms: float, units_per_rank: int, steps: int, dist=None, device=None):
+    """Units per second over all ranks and the time it is taken over.
+
+    Every rank processes units_per_rank units per step (independent replicas,
+    weak scaling); the time is the slowest rank's (max over ranks).
+    """
+    total_ms = float(local_ms)
+    world = 1
+    if dist is not None:
+        import torch
+
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        world = dist.get_world_size()
+    return world * units_per_rank * steps / (total_ms / 1000.0), total_ms
+
+
 # -------------------------------------------------------------------- ours
 def main():
     args = parse()
@@ -406,12 +424,7 @@ def main():
     prof_step_ms, _, _ = timed_steps()
     prof, launches = ly.prof_read()
     ly.prof_enable(False)
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * nv * args.steps / (total_ms / 1000.0)
+    value, total_ms = whole_job_rate(sum(step_ms), nv, args.steps, dist, dev)
 
     f_last = outs[-1].cpu().numpy()
     acc = np.abs(f_last - f64) / np.abs(f64)
