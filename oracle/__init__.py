@@ -1,4 +1,4 @@
-"""CPU oracle (test infrastructure only; see lyap_oracle's docstring)."""
+"""CPU oracle (test infrastructure only; see the docstrings of lyap_oracle and projection)."""
 from .lyap_oracle import (  # noqa: F401
     param_matrix,
     lyap_kron,
