@@ -58,14 +58,20 @@ from .lyap_oracle import lyap_bartels_stewart, lyap_solve, trace_product
 RANK_TOL = 1e-13
 
 
-def seed_quantities(A0, U, V, G, E):
-    """A0p, B_l, B_r, X0, P and f(X0) in the convention of §2.2."""
+def seed_quantities(A0, U, V, G, E, X0=None):
+    """A0p, B_l, B_r, X0, P and f(X0) in the convention of §2.2.
+
+    X0 may be given when it is already known (a closed form pinned
+    separately); otherwise Bartels-Stewart solves the seed equation.
+    """
     A0 = np.asarray(A0, dtype=np.float64)
     A0p = A0.T.copy()
     Bl = np.asarray(V, dtype=np.float64)
     Br = np.asarray(U, dtype=np.float64)
     G = np.asarray(G, dtype=np.float64)
-    X0 = lyap_solve(A0, G @ G.T)  # A0^T X0 + X0 A0 = -G G^T, i.e. A0p X0 + X0 A0p^T = -G G^T
+    if X0 is None:
+        X0 = lyap_solve(A0, G @ G.T)  # A0^T X0 + X0 A0 = -G G^T, i.e. A0p X0 + X0 A0p^T = -G G^T
+    X0 = np.asarray(X0, dtype=np.float64)
     P = np.hstack([X0 @ Br, Bl])
     return dict(A0p=A0p, Bl=Bl, Br=Br, X0=X0, P=P, f0=trace_product(E, X0))
 
@@ -194,7 +200,7 @@ def trace_value(sq: dict, pm: dict, Y, E):
     return sq["f0"] + trace_product(Vm.T @ np.asarray(E) @ Vm, Y)
 
 
-def eksm_sweep(A0, U, V, G, E, vs, eps: float, m_max: int):
+def eksm_sweep(A0, U, V, G, E, vs, eps: float, m_max: int, X0=None):
     """Algorithm 1 over the ordered parameter set ``vs``.
 
     For m = 1, 2, ... (while m < m_max): build the next block, then go
@@ -203,7 +209,7 @@ def eksm_sweep(A0, U, V, G, E, vs, eps: float, m_max: int):
     and the space grows. Returns (f, m_used, delta) per v; v that never met
     eps keep f = nan and m_used = 0.
     """
-    sq = seed_quantities(A0, U, V, G, E)
+    sq = seed_quantities(A0, U, V, G, E, X0)
     off = offline_norms(sq["A0p"], sq["Bl"], sq["Br"])
     ek = ExtendedKrylov(sq["A0p"], sq["P"])
     vs = np.asarray(vs, dtype=np.float64)

@@ -89,6 +89,32 @@ def test_paper_seed_closed_form_X0():
         assert np.abs(off).max() < 1e-12 * np.abs(X).max()
 
 
+def test_paper_seed_closed_form_X0_partial_modes():
+    """Paper §3.1's closed-form X0 for Q = eq. (matrix Z) (the first s modes);
+    the same (1,1) correction as for Q = I/n, and zero on the other modes."""
+    spec = json.load(open(os.path.join(GOLDEN, "modal_seed_X0_Z.json")))
+    for case in spec["cases"]:
+        alpha, s = case["alpha"], case["s"]
+        om = np.array(case["omega"])
+        m = om.size
+        n = 2 * m
+        A0p = np.zeros((n, n))
+        A0p[:m, m:] = np.diag(om)
+        A0p[m:, :m] = -np.diag(om)
+        A0p[m:, m:] = -alpha * np.diag(om)
+        Q = np.zeros((n, n))
+        Q[np.arange(s), np.arange(s)] = Q[m + np.arange(s), m + np.arange(s)] = 1.0 / (2 * s)
+        X = ol.lyap_bartels_stewart(A0p.T, Q)
+        Xc = np.zeros((n, n))
+        i = np.arange(s)
+        Xc[i, i] = (1 / alpha + alpha / 2) / om[:s]
+        Xc[i, m + i] = Xc[m + i, i] = -0.5 / om[:s]
+        Xc[m + i, m + i] = 1 / (alpha * om[:s])
+        Xc /= 2 * s
+        assert np.abs(X - Xc).max() <= 1e-12 * np.abs(Xc).max()
+        assert not np.isclose(X[0, 0] * 2 * s * om[0], 1.5 * alpha)  # the printed entry
+
+
 def test_modal_chain_seed_trace_full_size():
     """f(X0) = sum_i (2/alpha + alpha/2)/omega_i for the decoupled modal seed
     (G = E = I), at the full 100-state chain; and continuity as v -> 0+."""

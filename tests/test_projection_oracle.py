@@ -15,14 +15,19 @@ own formulas:
 * Algorithm 1 accepts v in order with non-decreasing m, meets its bound, and
   its traces agree with the exact ones within a small multiple of the bound;
 * for symmetric A(v) and E = I the trace is exact on EK_1 (trace(X) =
-  trace(A^-1 C) / 2 and A(v)^-1 P lies in EK_1).
+  trace(A^-1 C) / 2 and A(v)^-1 P lies in EK_1);
+* Ex. 1 case b): the dimension of the space that meets eps for the first
+  equation, against the values the paper prints (tests/golden).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 from oracle import projection as pj
-from workloads import generic_dense, mass_spring_chain, multi_agent
+from workloads import generic_dense, mass_spring_chain, multi_agent, two_row_system
 
 
 def chain_problem(masses: int, dampers, seed: int = 3, alpha: float = 0.04):
@@ -188,3 +193,31 @@ def test_symmetric_trace_is_exact_on_the_first_space():
         assert pj.backward_error_cheap(pm, Y, ek.G, v, off) > 1e-8
         exact = oracle.trace_EX(p.A0, p.U, p.V, p.G, p.E, v)
         assert pj.trace_value(sq, pm, Y, p.E) == pytest.approx(exact, rel=1e-12)
+
+
+def two_row_x0(p, s):
+    """Closed-form seed solution for Q = eq. (matrix Z) (pinned against
+    Bartels-Stewart in test_oracle.py's partial-mode closed-form test)."""
+    om, a, nm = p.meta["omega"], p.meta["alpha"], p.meta["omega"].size
+    X = np.zeros((p.n, p.n))
+    i = np.arange(s)
+    X[i, i] = (1 / a + a / 2) / om[:s]
+    X[i, nm + i] = X[nm + i, i] = -0.5 / om[:s]
+    X[nm + i, nm + i] = 1 / (a * om[:s])
+    return X / (2 * s)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case", [0, 1])
+def test_ex1b_extended_krylov_dimension(case):
+    """Ex. 1 case b): the space that meets eps = 1e-8 for the first equation
+    has the dimension the paper prints, within two blocks of 12."""
+    spec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "ex1b_eksm_dimensions.json")))
+    mod, ref = spec["model"], spec["printed"][case]
+    p = two_row_system(mod["d"], ref["i1"], ref["i2"], 21, alpha=mod["alpha"], stiffness=tuple(mod["stiffness"]))
+    X0 = two_row_x0(p, 21)
+    f, m_used, delta = pj.eksm_sweep(p.A0, p.U, p.V, p.G, p.E, np.array([mod["v0"]]), eps=mod["eps"],
+                                     m_max=mod["m_max"], X0=X0)
+    k4 = 4 * p.k
+    assert delta[0] <= mod["eps"] and np.isfinite(f[0])
+    assert abs(m_used[0] * k4 - ref["dim"]) <= spec["tolerance_blocks"] * k4

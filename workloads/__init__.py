@@ -8,6 +8,8 @@ tests and benchmark can draw their inputs from it.
 from .generators import (  # noqa: F401
     Problem,
     mass_spring_chain,
+    two_row_masses,
+    two_row_system,
     multi_agent,
     haar_orthogonal,
     generic_dense,

@@ -20,6 +20,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.linalg as sla
 
 
 @dataclass
@@ -141,6 +142,79 @@ def mass_spring_chain(
         G=np.eye(n),
         E=E,
         meta=dict(omega=omega, alpha=alpha, dampers=list(dampers), masses=m),
+    )
+
+
+def two_row_masses(d: int) -> np.ndarray:
+    """Masses of Ex. 1's two-row system, eq. (mass-Config), as printed for
+    d = 1000: m_i = (2d + 1 - 2i)/10 for i <= 500, (i - 500)/10 + 100 for
+    501 <= i <= 1000, 160 for 1001 <= i <= 2d (the printed range starts at
+    1000, which the second range already covers), and m_{2d+1} = 175."""
+    i = np.arange(1, 2 * d + 1, dtype=np.float64)
+    m = np.where(i <= 500, (2 * d + 1 - 2 * i) / 10.0, np.where(i <= 1000, (i - 500) / 10.0 + 100.0, 160.0))
+    m = np.append(m, 175.0)
+    if np.any(m <= 0):
+        raise ValueError("eq. (mass-Config) gives non-positive masses for this d")
+    return m
+
+
+def two_row_system(d: int, i1: int, i2: int, s: int, alpha: float = 0.04,
+                   stiffness=(40.0, 20.0, 30.0)) -> Problem:
+    """Ex. 1: two rows of d masses joined to a last mass (2d + 1 masses).
+
+    * K: row r has springs of stiffness k_r, with the first mass of the row
+      tied to the wall and the last tied to mass 2d + 1, which a spring k_3
+      ties to the wall (the block matrix printed with the example).
+    * Critical internal damping (eq. (Ccrit)), modal state of eq. (MatrixA):
+      A_p = [[0, Omega], [-Omega, -alpha Omega]].
+    * Dampers, eq. (damping-geometry): B = [e_i1, e_(i1+d/10) - e_(i1+d/10+d),
+      e_i2] (1-based mass indices), B_l = B_r = [0; Phi^T B].
+    * Q = eq. (matrix Z) with s modes: 1/(2s) on the first s modal
+      displacements and velocities. E = I (average total energy = trace X).
+
+    The paper writes A_p X + X A_p^T = -Q; the API's A(v)^T X + X A(v) = -G G^T
+    takes A0 = A_p^T, U = B_r, V = B_l and G G^T = Q.
+    """
+    if d % 10:
+        raise ValueError("d must be a multiple of 10 (damper offset d/10)")
+    k1, k2, k3 = stiffness
+    masses = two_row_masses(d)
+    nm = 2 * d + 1
+    K = np.zeros((nm, nm))
+    for r, kr in ((0, k1), (1, k2)):
+        o = r * d
+        for i in range(d):
+            K[o + i, o + i] = 2.0 * kr
+            if i + 1 < d:
+                K[o + i, o + i + 1] = K[o + i + 1, o + i] = -kr
+        K[o + d - 1, nm - 1] = K[nm - 1, o + d - 1] = -kr
+    K[nm - 1, nm - 1] = k1 + k2 + k3
+    w2, Phi = sla.eigh(K, np.diag(masses))  # Phi^T K Phi = Omega^2, Phi^T M Phi = I, ascending
+    omega = np.sqrt(w2)
+    n = 2 * nm
+    Ap = np.zeros((n, n))
+    Ap[:nm, nm:] = np.diag(omega)
+    Ap[nm:, :nm] = -np.diag(omega)
+    Ap[nm:, nm:] = -alpha * np.diag(omega)
+    B = np.zeros((nm, 3))
+    B[i1 - 1, 0] = 1.0
+    B[i1 + d // 10 - 1, 1] = 1.0
+    B[i1 + d // 10 + d - 1, 1] = -1.0
+    B[i2 - 1, 2] = 1.0
+    Bm = np.zeros((n, 3))
+    Bm[nm:, :] = Phi.T @ B
+    G = np.zeros((n, 2 * s))
+    G[np.arange(s), np.arange(s)] = 1.0
+    G[nm + np.arange(s), s + np.arange(s)] = 1.0
+    G /= np.sqrt(2.0 * s)
+    return Problem(
+        name=f"tworow{d}_{i1}_{i2}",
+        A0=Ap.T.copy(),
+        U=Bm,
+        V=Bm.copy(),
+        G=G,
+        E=np.eye(n),
+        meta=dict(omega=omega, alpha=alpha, d=d, i1=i1, i2=i2, s=s),
     )
 
 
