@@ -17,7 +17,7 @@ import scipy.linalg as sla
 
 import oracle
 import oracle.lyap_oracle as ol
-from workloads import mass_spring_chain, haar_orthogonal, workload_small_fp64
+from workloads import haar_orthogonal, workload_small_fp64
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 

@@ -7,7 +7,6 @@ to the path's tolerance (1e-8 relative for the mixed path, 1e-10 for FP64):
 batching changes the recycled space and the iteration counts, not the
 answer. A few results are also checked against the CPU oracle.
 """
-import math
 
 import numpy as np
 import pytest
