@@ -115,6 +115,37 @@ def test_paper_seed_closed_form_X0_partial_modes():
         assert not np.isclose(X[0, 0] * 2 * s * om[0], 1.5 * alpha)  # the printed entry
 
 
+def test_rayleigh_seed_closed_form_X0():
+    """Paper §3.1's closed-form X0 for Rayleigh damping in physical
+    coordinates with Q = diag(K^-1, M^-1); the printed blocks are corrected
+    (see the fixture), and the printed form is shown not to solve the equation."""
+    spec = json.load(open(os.path.join(GOLDEN, "rayleigh_seed_X0.json")))
+    for case in spec["cases"]:
+        m, a, b = case["m"], case["alpha"], case["beta"]
+        rng = np.random.default_rng(case["seed"])
+        F = rng.standard_normal((m, m))
+        K = F @ F.T + m * np.eye(m)
+        F = rng.standard_normal((m, m))
+        M = F @ F.T + m * np.eye(m)
+        Ki, Mi = np.linalg.inv(K), np.linalg.inv(M)
+        Z = np.zeros((2 * m, 2 * m))
+        Z[:m, :m], Z[m:, m:] = Ki, Mi
+        A0p = np.block([[np.zeros((m, m)), np.eye(m)], [-Mi @ K, -a * np.eye(m) - b * Mi @ K]])
+        X = ol.lyap_bartels_stewart(A0p.T, Z)  # paper convention A0 X + X A0^T = -Z
+        S = np.linalg.inv(a * K + b * K @ Mi @ K)
+        X11 = S + 0.5 * a * Ki @ M @ Ki + 0.5 * b * Ki
+        X22 = np.linalg.inv(a * M + b * K)
+        Xc = np.block([[X11, -0.5 * Ki], [-0.5 * Ki, X22]])
+        assert np.abs(X - Xc).max() <= 1e-12 * np.abs(Xc).max()
+        Xp = np.block([[S + a * Ki @ Mi @ Ki + b * Ki, -0.5 * Ki], [-0.5 * Ki, S]])  # as printed
+        assert np.abs(X - Xp).max() > 1e-2 * np.abs(Xc).max()
+    # one mass: X11 = 1/(c k) + c/(2 k^2), X22 = 1/c with c = alpha + beta k
+    k, a, b = 2.5, 0.3, 0.05
+    c = a + b * k
+    X = ol.lyap_bartels_stewart(np.array([[0.0, 1.0], [-k, -c]]).T, np.diag([1 / k, 1.0]))
+    np.testing.assert_allclose(X, [[1 / (c * k) + c / (2 * k * k), -0.5 / k], [-0.5 / k, 1 / c]], rtol=1e-13)
+
+
 def test_modal_chain_seed_trace_full_size():
     """f(X0) = sum_i (2/alpha + alpha/2)/omega_i for the decoupled modal seed
     (G = E = I), at the full 100-state chain; and continuity as v -> 0+."""
