@@ -31,7 +31,8 @@ Steps, in the paper's order:
 * The projected equation (param_projected)
       (T_m - B_{l,m} D B_{r,m}^T) Y + Y (T_m - B_{l,m} D B_{r,m}^T)^T
           = E_1 G (I2 (x) D) G^T E_1^T
-  by the Bartels-Stewart solver of lyap_oracle (a library step here).
+  by LAPACK's Bartels-Stewart solver (a library step; lyap_oracle's own
+  solver is pinned against it).
 * The backward error Delta_{m,v} by the backward error proposition (cheap:
   no n-sized work per v) and by its definition (the full n x n residual).
 * f(v) = trace(E X0) + trace((V_m^T E V_m) Y_m(v)); for E = I the second
@@ -51,7 +52,7 @@ import math
 import numpy as np
 import scipy.linalg as sla
 
-from .lyap_oracle import lyap_bartels_stewart, lyap_solve, trace_product
+from .lyap_oracle import lyap_solve, trace_product
 
 # Directions of a new block whose norm after orthogonalisation falls below
 # this fraction of the largest candidate column are already in the space.
@@ -165,8 +166,9 @@ def solve_projected(pm: dict, G, v):
     E1G = np.zeros((d, G.shape[1]))
     E1G[: G.shape[0], :] = G
     Q = E1G @ i2_kron(v) @ E1G.T
-    # M Y + Y M^T = Q  <=>  (M^T)^T Y + Y (M^T) = -(-Q)
-    return lyap_bartels_stewart(M.T, -Q)
+    # M Y + Y M^T = Q: LAPACK's Bartels-Stewart (real Schur form, trsyl),
+    # which lyap_oracle's own solver is pinned against
+    return sla.solve_continuous_lyapunov(M, Q)
 
 
 def offline_norms(A0p, Bl, Br):
