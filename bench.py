@@ -31,13 +31,10 @@ METRIC = "trace(EX(v)) evals/sec at rel err<=1e-8 vs FP64 path; p50/p99 request 
 WORKLOAD = "chain400 n=800 k=2, 1000 v log-uniform [1e-2,1e2]^2 NN-ordered, Haar-dense"
 FP64_PEAK_FLOPS_PER_CLK_SM = 4.0  # 2 FP64 FMA per clock per SM (1.25 TFLOP/s at 2070 MHz x 152 SMs)
 SMS = 152
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, averaged over the
-# launches of one 1000-vector sweep of the 800-state workload, from one ncu capture of
-# `bench.py --steps 1 --warmup 3 --no-cpu-baseline --profile-sweep` (cold caches: ncu
-# flushes them before every launch). Valid for the kernels as they stand; a kernel
-# change invalidates its entry.
-# "precond" counts one k_prec_a + k_prec_b pair as a launch.
-MEASURED_TRAFFIC_PER_LAUNCH = {"ortho": 113.99e6, "tc_gemm": 23.02e6, "precond": 26.74e6, "oz_gemm": 271.95e6}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel,
+# from a one-kernel ncu capture of the same workload (see profiles/); empty
+# while no capture of the kernels as they stand exists.
+MEASURED_TRAFFIC_PER_LAUNCH = {}
 FP32_LANES_PER_SM = 128.0  # FP32 lane-instructions per clock per SM
 L2_FLUSH_BYTES = 256 << 20
 
@@ -57,11 +54,15 @@ def parse():
     ap.add_argument("--profile-sweep", action="store_true",
                     help="after the measurements, run one more sweep between cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
-    ap.add_argument("--cpu-sample", type=int, default=4, help="oracle evaluations in the CPU baseline")
+    ap.add_argument("--cpu-sample", type=int, default=8, help="oracle evaluations in the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["precision", "serving", "kernels"], default="precision")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests per arrival rate")
     ap.add_argument("--serving-sizes", default="200,400,800,1600", help="serving: chain lengths (masses)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-path, gradient, multi-agent and serving figures of the default run")
+    ap.add_argument("--serving-requests", type=int, default=160,
+                    help="requests of the serving figure in the default run (one rate, 0.95 of saturation)")
     return ap.parse_args()
 
 
@@ -182,28 +183,23 @@ def run_reference(args, rank):
 
 
 # ----------------------------------------------------------------- serving
-def run_serving(args, local):
+def serving_measure(ctx, prec, sizes=(200, 400, 800, 1600), requests=2000, fracs=(0.5, 0.8, 0.95), burst=128):
     """Serving workload: 8 seeds (two chains each of the given lengths,
     k in {2,3,4}, Haar-dense), requests of 64 log-uniform parameter vectors
     on [0.1, 10]^k. Saturation throughput from a burst, then Poisson arrivals
-    at 0.5/0.8/0.95 of it; evals/s and p50/p99 submit-to-result latency."""
+    at the given fractions of it; evals/s and p50/p99 submit-to-result
+    latency per rate."""
     import threading
 
     import numpy as np
-    import torch
 
     import paper_2312_08201_gb300 as ly
     from workloads import workload_serving_requests, workload_serving_seeds
 
-    torch.cuda.set_device(local)
-    ly.build()
-    sizes = tuple(int(x) for x in args.serving_sizes.split(","))
     probs = workload_serving_seeds(dense=True, sizes=sizes)
-    ctx = ly.Context(local)
     t0 = time.perf_counter()
     seeds = [ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E) for p in probs]
     t_factor = time.perf_counter() - t0
-    prec = ly.FP64 if args.precision == "fp64" else ly.BF16_IR
 
     def drive(reqs, paced):
         srv = ly.Server(ctx, precision=prec)
@@ -236,24 +232,127 @@ def run_serving(args, local):
     # warm-up (recycle spaces, workspaces) and saturation
     warm = workload_serving_requests(probs, rate_hz=1e9, count=16, seed=99)
     drive(warm, False)
-    burst = workload_serving_requests(probs, rate_hz=1e9, count=min(128, args.requests), seed=1)
-    sat, _ = drive(burst, False)
+    sat, _ = drive(workload_serving_requests(probs, rate_hz=1e9, count=min(burst, requests), seed=1), False)
     rates = {}
-    for frac in (0.5, 0.8, 0.95):
+    for frac in fracs:
         req_rate = frac * sat / 64.0
-        reqs = workload_serving_requests(probs, rate_hz=req_rate, count=args.requests, seed=int(frac * 100))
+        reqs = workload_serving_requests(probs, rate_hz=req_rate, count=requests, seed=int(frac * 100))
         thr, lat = drive(reqs, True)
         rates[str(frac)] = dict(evals_per_s=thr, p50_ms=1e3 * float(np.percentile(lat, 50)),
                                 p99_ms=1e3 * float(np.percentile(lat, 99)), requests=len(reqs))
+    for sd in seeds:
+        sd.free()
+    return dict(workload=f"8 chain seeds {sizes} masses x2, k in {{2,3,4}}, Haar-dense, 64 v log-uniform "
+                         "[0.1,10]^k per request, Poisson arrivals",
+                n=[p.n for p in probs], k=[p.k for p in probs], saturation_evals_per_s=sat, rates=rates,
+                seed_factor_s=t_factor)
+
+
+def run_serving(args, local):
+    import torch
+
+    import paper_2312_08201_gb300 as ly
+
+    torch.cuda.set_device(local)
+    ly.build()
+    sizes = tuple(int(x) for x in args.serving_sizes.split(","))
+    ctx = ly.Context(local)
+    prec = ly.FP64 if args.precision == "fp64" else ly.BF16_IR
+    sv = serving_measure(ctx, prec, sizes, args.requests)
+    rates = sv["rates"]
     line = dict(metric=METRIC, value=rates["0.95"]["evals_per_s"], unit="evals/s", n_gpus=1, steps=args.requests,
                 warmup=16, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="bf16x3-gemm/f32-krylov/int-sliced-bf16-refine (ff-refine for n > 1023)" if prec == ly.BF16_IR
                 else "f64", data="synthetic",
-                config=dict(workload=f"serving: 8 chain seeds {sizes} masses x2, k in {{2,3,4}}, 64 v per request, "
-                                     "Poisson arrivals", n=[p.n for p in probs], k=[p.k for p in probs]),
-                saturation_evals_per_s=sat, rates=rates, seed_factor_s=t_factor,
+                config=dict(workload="serving: " + sv["workload"], n=sv["n"], k=sv["k"]),
+                saturation_evals_per_s=sv["saturation_evals_per_s"], rates=rates, seed_factor_s=sv["seed_factor_s"],
                 latency_ms=dict(p50=rates["0.95"]["p50_ms"], p99=rates["0.95"]["p99_ms"], request="64-vector sweep"))
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------- the other workloads (extras)
+def _event_time(fn, steps, warmup, stream):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    out = None
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ms], out
+
+
+def extra_fp64_path(seed, v_dev, f64_ref, stream, steps=2):
+    """The plain FP64 GPU path on the headline sweep (the path the mixed one
+    is compared with)."""
+    import numpy as np
+
+    import paper_2312_08201_gb300 as ly
+
+    ms, f = _event_time(lambda: seed.trace_EX(v_dev, precision=ly.FP64), steps, 1, stream)
+    f = f.cpu().numpy()
+    rep = np.abs(f - f64_ref) / np.abs(f64_ref)
+    return dict(evals_per_s=len(f) * len(ms) / (sum(ms) / 1e3), ms_per_sweep=float(np.mean(ms)), steps=len(ms),
+                max_rel_diff_between_runs=float(rep.max()), dtype="f64")
+
+
+def extra_grad(ctx, dev, stream, steps=2):
+    """Differentiation workload: 1000-mass chain (n = 2000), 4 dampers,
+    E = first 100 modal displacements, 256 v with gradients, mixed path; the
+    first 4 v also on the FP64 path for the accuracy figures."""
+    import numpy as np
+    import torch
+
+    import paper_2312_08201_gb300 as ly
+    from workloads import workload_differentiation
+
+    p, vs = workload_differentiation()
+    t0 = time.perf_counter()
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    tf = time.perf_counter() - t0
+    v = torch.tensor(vs, dtype=torch.float64, device=dev)
+    ms, (f, g) = _event_time(lambda: seed.grad(v, precision=ly.BF16_IR), steps, 1, stream)
+    f64, g64 = seed.grad(v[:4], precision=ly.FP64)
+    f, g, f64, g64 = (x.cpu().numpy() for x in (f, g, f64, g64))
+    gerr = float(max(np.abs(g[i] - g64[i]).max() / np.abs(g64[i]).max() for i in range(4)))
+    seed.free()
+    return dict(workload="chain1000 n=2000 k=4, E = first 100 modal displacements, 256 v log-uniform [0.1,10]^4, "
+                         "Haar-dense", unit="evals+grads/s", value=len(vs) * len(ms) / (sum(ms) / 1e3),
+                ms_per_sweep=float(np.mean(ms)), precision="bf16_ir",
+                max_rel_err_f_vs_fp64_path=float(np.max(np.abs(f[:4] - f64) / np.abs(f64))),
+                max_rel_err_grad_vs_fp64_path=gerr, seed_factor_s=tf)
+
+
+def extra_multi_agent(ctx, dev, stream, steps=2):
+    """Multi-agent workload: 256 agents (n = 1024), 8 tunable edges, 512
+    weight vectors in one lockstep batch, mixed path; 8 of them also on the
+    FP64 path."""
+    import numpy as np
+    import torch
+
+    import paper_2312_08201_gb300 as ly
+    from workloads import workload_multi_agent
+
+    p, ws = workload_multi_agent()
+    seed = ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E)
+    v = torch.tensor(ws, dtype=torch.float64, device=dev)
+    ms, f = _event_time(lambda: seed.trace_EX(v, precision=ly.BF16_IR, batch=len(ws)), steps, 1, stream)
+    f64 = seed.trace_EX(v[:8], precision=ly.FP64).cpu().numpy()
+    f = f.cpu().numpy()
+    st = seed.stats()
+    seed.free()
+    return dict(workload="256 agents n=1024 k=8 (ER p=0.05), 512 weight vectors U[0.1,5]^8, one batch",
+                unit="evals/s", value=len(ws) * len(ms) / (sum(ms) / 1e3), ms_per_sweep=float(np.mean(ms)),
+                precision="bf16_ir", real_spectrum=bool(st["real_path"]),
+                max_rel_err_vs_fp64_path=float(np.max(np.abs(f[:8] - f64) / np.abs(f64))))
 
 
 # ------------------------------------------------------------ kernel probe
@@ -501,13 +600,31 @@ def main():
                     parallelism="replicas" if world > 1 else "single-gpu", cond_Q=stats["cond_Q"]),
         accuracy=dict(max_rel_err_vs_fp64_path=float(acc.max()), median_rel_err=float(np.median(acc)),
                       iters_mean=float(np.mean(iters)), refine_steps_mean=float(np.mean(rsteps))),
-        latency_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99)),
-                        request="one 1000-vector sweep"),
+        sweep_ms=dict(p50=float(np.percentile(step_ms, 50)), p99=float(np.percentile(step_ms, 99)),
+                      note="device time of one 1000-vector sweep"),
         roofline=roof, kernels=kernels, e2e=e2e, gpu_launches=int(launches), clocks=clk,
         profiled_ms_per_step=float(np.mean(prof_step_ms)),
         profile_note="kernel times, launches and roofline come from a second run of the same K steps "
                      "with per-kernel CUDA events; value is timed without them")
 
+    if rank == 0 and world == 1 and not args.no_extras:
+        # the figures of the other workloads, after the timed region
+        for key, fn in (("fp64_path", lambda: extra_fp64_path(seed, v_dev, f64, stream)),
+                        ("grad", lambda: extra_grad(ctx, dev, stream)),
+                        ("multi_agent", lambda: extra_multi_agent(ctx, dev, stream))):
+            try:
+                line[key] = fn()
+            except Exception as exc:  # report, never lose the headline line
+                line[key] = dict(error=f"{type(exc).__name__}: {exc}"[:300])
+        try:
+            sv = serving_measure(ctx, ly.BF16_IR, requests=args.serving_requests, fracs=(0.95,), burst=64)
+            r = sv["rates"]["0.95"]
+            line["serving"] = sv
+            line["latency_ms"] = dict(p50=r["p50_ms"], p99=r["p99_ms"],
+                                      request="one 64-vector request of the serving workload, submit to result, "
+                                              "Poisson arrivals at 0.95 of measured saturation")
+        except Exception as exc:
+            line["serving"] = dict(error=f"{type(exc).__name__}: {exc}"[:300])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, fcpu, secs = cpu_oracle(args.cpu_sample)
         err = max(abs(a - b) / abs(b) for a, b in zip(f_last[: len(fcpu)], fcpu))

@@ -26,8 +26,12 @@
  *    equal to the row count.
  *  - mem_kind: LYAP_MEM_HOST means pointer arguments are host memory (the
  *    call copies them); LYAP_MEM_DEVICE means device memory on the context's
- *    GPU, read (or written) in order on opts->stream; the caller keeps
- *    ownership and must keep the buffers alive until the call returns.
+ *    GPU, read and written only by work queued on opts->stream (no copy
+ *    through the host; device parameters are validated by a kernel and an
+ *    invalid one is reported at the call's next synchronisation); the
+ *    caller keeps ownership and must keep the buffers alive until the call
+ *    returns. The solve calls drive the Krylov iteration from the host and
+ *    return once their results are complete.
  *  - Handles (ctx, seed, server) are owned by the library and freed with the
  *    matching destroy/free call. Output arrays are caller-allocated.
  *  - Every function returns LYAP_OK (0) or a negative error code; nothing
@@ -85,10 +89,17 @@ extern "C" {
 #define LYAP_RESID_FP64 1
 #define LYAP_RESID_TC 2
 
-/* Fault-injection bits for lyap_opts.inject (host-side only; no GPU fault). */
-#define LYAP_INJECT_ALLOC_FAIL 0x1u   /* next workspace allocation fails     */
-#define LYAP_INJECT_FORCE_MAXIT 0x2u  /* solver stops after one cycle         */
-#define LYAP_INJECT_DEVICE_WAIT 0x4u  /* a device wait flag is never set      */
+/* Fault-injection bits for lyap_opts.inject (tests; none faults the GPU).
+ *  ALLOC_FAIL:  the call fails as if a workspace allocation had failed.
+ *  FORCE_MAXIT: every Krylov solve stops after one iteration (ENOCONV).
+ *  DEVICE_WAIT: in the mixed path the tensor-core GEMM issues no copy, so
+ *               its bounded mbarrier wait runs out (after about 50 us);
+ *               the kernel records the expiry, frees its TMEM and returns,
+ *               and the call returns LYAP_EDEVICE_TIMEOUT at its next
+ *               synchronisation. The context stays usable. */
+#define LYAP_INJECT_ALLOC_FAIL 0x1u
+#define LYAP_INJECT_FORCE_MAXIT 0x2u
+#define LYAP_INJECT_DEVICE_WAIT 0x4u
 
 typedef struct lyap_ctx lyap_ctx;
 typedef struct lyap_seed lyap_seed;
@@ -169,7 +180,8 @@ void lyap_ctx_destroy(lyap_ctx* ctx);
  * trace(E X0), and (pbar > 0) a truncated SVD of the off-diagonal coupling
  * for the preconditioner (eq. (prec)).
  *   A0: n x n; U, V: n x k; G: n x g; E: n x n symmetric, or NULL for I.
- *   1 <= k <= 16, 1 <= n, k <= n, 1 <= g.
+ *   1 <= k <= 8 (the per-row k x k blocks of the operator and of the
+ *   preconditioner are held in registers), 1 <= n, k <= n, 1 <= g.
  * On success *out holds a device-resident seed; *cond_Q_out (may be NULL)
  * receives ||Qp||_F ||Qp^{-1}||_F.
  * Errors: LYAP_EINVAL, LYAP_EUNSTABLE_SEED (max Re lambda >= 0, or
@@ -191,8 +203,8 @@ int lyap_seed_free(lyap_seed* seed);
  * receives, for each v, the shifted capacitance solution W' = W + P D(v) as
  * n x k complex128 (interleaved re, im; column-major), nv*n*k*2 doubles, in
  * mem_kind memory. info (may be NULL) receives nv reports (host memory).
- * Errors: LYAP_EINVAL (v_i == 0 or not finite, bad sizes), LYAP_ENOMEM,
- * LYAP_ECUDA, LYAP_EDEVICE_TIMEOUT. */
+ * Errors: LYAP_EINVAL (v_i == 0 or not finite, bad sizes; outputs are then
+ * undefined), LYAP_ENOMEM, LYAP_ECUDA, LYAP_EDEVICE_TIMEOUT. */
 int lyap_param_solve(lyap_seed* seed, int nv, const double* v, int mem_kind, const lyap_opts* opts,
                      double* w_out, lyap_result_info* info);
 
@@ -256,23 +268,28 @@ int lyap_serve_cancel(lyap_server* srv, uint64_t ticket);
 void lyap_serve_destroy(lyap_server* srv);
 
 /* ------------------------------------------------- allocation-free check
- * The paper has no counterpart to this call; it exists for callers that
- * must not allocate device memory: code running while its stream is being
- * captured into a CUDA graph, hosts whose device memory is reserved once at
- * start-up by their own pool, and plug-ins confined to a host framework's
- * allocator. For nv parameter vectors v (device, nv x k row-major) and the
- * caller's capacitance solutions w (device, nv x n x k complex128 as written
- * by lyap_param_solve), it writes trace_out[b] = f(v_b) and resid_out[b] =
- * ||P - T(v_b) W'_b|| / ||P|| in FP64 (device, nv doubles each), in order on
- * `stream` (NULL = default stream), without synchronising.
+ * The paper has no counterpart to this call. It is for callers that cannot
+ * allocate device memory while they run: hosts that reserve all of their
+ * device memory once at start-up in their own pool and must not let it
+ * grow, and plug-ins that live inside another framework's allocator and
+ * may not go around it. For nv parameter vectors v (device, nv x k
+ * row-major) and the caller's capacitance solutions w (device,
+ * nv x n x k complex128 as written by lyap_param_solve), it writes
+ * trace_out[b] = f(v_b) and resid_out[b] = ||P - T(v_b) W'_b|| / ||P|| in
+ * FP64 (device, nv doubles each), in order on `stream` (NULL = default
+ * stream), without synchronising.
  * It calls no allocation routine: intermediates live in one static device
- * array of LYAP_NOALLOC_MAX_ENTRIES complex doubles (about 33 MiB, held by
- * every GPU that loads the library until the process exits); a call needs
- * nv*n*k + ceil(nv*k/2) entries and returns LYAP_EINVAL when that exceeds
- * the limit. All calls share the array, so calls that overlap on the GPU
- * race. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * A zero or non-finite v_i yields NaN in that system's outputs. */
+ * array of LYAP_NOALLOC_MAX_ENTRIES complex doubles (33 MiB, 34,603,008
+ * bytes, held by every GPU that loads the library until the process exits);
+ * a call needs nv*n*k + ceil(nv*k/2) entries and returns LYAP_EINVAL when
+ * that exceeds the limit. All calls share the array and it keeps the last
+ * call's contents; every entry a call reads was written earlier in the same
+ * call, so nothing needs clearing. Calls that overlap on the GPU (other
+ * streams, or host threads without ordering) race on the array. The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) once; make that first call before any stream
+ * capture. A zero or non-finite v_i yields NaN in that system's residual
+ * (its trace does not involve v). */
 #define LYAP_NOALLOC_MAX_ENTRIES ((1u << 21) + (1u << 16))
 int lyap_check_solution_noalloc(lyap_seed* seed, int nv, const double* v, const double* w, double* trace_out,
                                 double* resid_out, void* stream);

@@ -491,25 +491,37 @@ def _infos(info, nv):
 
 
 def trace_ex_function():
-    """torch.autograd.Function: f = TraceEX.apply(v, seed, opts_dict); backward
-    returns grad_output * df/dv from the library's adjoint solve."""
+    """torch.autograd.Function ``TraceEX``: ``f = TraceEX.apply(v, seed, opts)``.
+
+    ``v`` is an (nv, k) tensor on the seed's GPU (device path: no copy through
+    the host) or on the CPU (host path); ``f`` is float64 on ``v``'s device.
+    When ``v`` requires a gradient the forward pass calls lyap_grad, which
+    adds one adjoint capacitance solve per v (df/dv_i = v_i^-2 <Z_i, W'_i>,
+    the adjoint of eq. (SMW_linearsystem)); backward returns
+    ``grad_out[:, None] * df/dv`` in ``v``'s dtype and device. ``opts`` is a
+    dict of lyap_opts fields (e.g. ``{"precision": BF16_IR}``)."""
     import torch
 
     class TraceEX(torch.autograd.Function):
         @staticmethod
         def forward(ctx, v, seed, opts=None):
-            opts = opts or {}
-            if v.requires_grad:
-                f, g = seed.grad(v.detach(), **opts)
-                ctx.save_for_backward(g if _is_torch(g) else torch.as_tensor(g))
+            opts = dict(opts or {})
+            if v.dim() != 2 or v.shape[1] != seed.k:
+                raise ValueError(f"v must have shape (nv, {seed.k})")
+            vd = v.detach().to(torch.float64)
+            vin = vd.contiguous() if vd.is_cuda else vd.cpu().numpy()
+            ctx.v_dtype, ctx.v_device = v.dtype, v.device
+            if ctx.needs_input_grad[0]:
+                f, g = seed.grad(vin, **opts)
+                ctx.save_for_backward(torch.as_tensor(g).to(device=v.device, dtype=torch.float64))
             else:
-                f = seed.trace_EX(v.detach(), **opts)
-                ctx.save_for_backward(torch.empty(0))
-            return f if _is_torch(f) else torch.as_tensor(f)
+                f = seed.trace_EX(vin, **opts)
+            return torch.as_tensor(f).to(device=v.device, dtype=torch.float64)
 
         @staticmethod
         def backward(ctx, grad_out):
             (g,) = ctx.saved_tensors
-            return grad_out[:, None].to(g.dtype) * g.to(grad_out.device), None, None
+            gv = grad_out.to(device=g.device, dtype=torch.float64)[:, None] * g
+            return gv.to(device=ctx.v_device, dtype=ctx.v_dtype), None, None
 
     return TraceEX

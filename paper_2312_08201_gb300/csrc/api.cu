@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 
@@ -20,22 +21,54 @@ thread_local std::string g_last_error;
 void lyap_set_last_error(const std::string& msg) { g_last_error = msg; }
 extern "C" const char* lyap_last_error(void) { return g_last_error.c_str(); }
 
+int lyap_smem_optin(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> done;
+  int dev = -1;
+  LY_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& have = done[{dev, func}];
+  if (have >= bytes) return LYAP_OK;
+  LY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  have = bytes;
+  return LYAP_OK;
+}
+
 // Workspaces cached per seed.
 struct SeedWork {
   KrylovWS<double2> ws64, ws64adj;
   KrylovWS<float2> ws32, ws32adj;
-  DevBuf<double> vinv;
+  DevBuf<double> vinv, vdev;
   DevBuf<double2> Wp, Zadj, Rres, tmp;
   DevBuf<double> red0, red1, red2, red3;
   DevBuf<float2> wcinv, wpart;
+  DevBuf<int> lst, cnt;  // system list of the error estimate
+  DevBuf<int> vbad;      // device-side count of invalid parameters in the call
+  int* vbad_host = nullptr;  // pinned copy, read at the chunk's sync
   WoodState wood;
+  ~SeedWork() {
+    if (vbad_host) cudaFreeHost(vbad_host);
+  }
 };
 
 namespace {
 
-__global__ void k_vinv(int count, const double* __restrict__ v, double* __restrict__ out) {
+// 1/v for every entry. An entry that is zero (excluded by §1) or not finite
+// is counted in *bad and gets 1/v = 0, so the solve stays finite; the call
+// reports LYAP_EINVAL when it reads the count.
+__global__ void k_vinv(int count, const double* __restrict__ v, double* __restrict__ out, int* __restrict__ bad) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < count) out[i] = 1.0 / v[i];
+  if (i >= count) return;
+  const double x = v[i];
+  const bool ok = x != 0.0 && isfinite(x);
+  out[i] = ok ? 1.0 / x : 0.0;
+  if (!ok) atomicAdd(bad, 1);
+}
+
+// f[b] = f0 + tr[b] into the caller's device output
+__global__ void k_trace_out(int nsys, double f0, const double* __restrict__ tr, double* __restrict__ f) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nsys) f[b] = f0 + tr[b];
 }
 
 // grad[b, i] = v_i^{-2} Re sum_s Z_b[s, i] W_b[s, i]  (pairing without conjugation)
@@ -231,40 +264,37 @@ namespace {
 
 struct CallIO {
   int nv = 0;
-  std::vector<double> v;  // host copy, nv x k
+  int mem = LYAP_MEM_HOST;
+  const double* v = nullptr;  // nv x k, host or device (mem)
 };
 
-int load_v(lyap_seed* sd, int nv, const double* v, int mem_kind, cudaStream_t st, CallIO& io) {
+// Host parameters are checked here; device parameters are checked by k_vinv
+// in stream order, and the result is read at each chunk's sync.
+int load_v(lyap_seed* sd, int nv, const double* v, int mem_kind, CallIO& io) {
   if (nv < 0 || (nv > 0 && !v)) return LYAP_EINVAL;
   if (mem_kind != LYAP_MEM_HOST && mem_kind != LYAP_MEM_DEVICE) return LYAP_EINVAL;
   io.nv = nv;
-  io.v.resize((size_t)nv * sd->k);
-  if (nv == 0) return LYAP_OK;
-  if (mem_kind == LYAP_MEM_HOST) {
-    std::memcpy(io.v.data(), v, sizeof(double) * io.v.size());
-  } else {
-    LY_CUDA(cudaMemcpyAsync(io.v.data(), v, sizeof(double) * io.v.size(), cudaMemcpyDeviceToHost, st));
-    LY_CUDA(cudaStreamSynchronize(st));
-  }
-  return lyap_check_v(nv, sd->k, io.v.data());
+  io.mem = mem_kind;
+  io.v = v;
+  if (nv == 0 || mem_kind == LYAP_MEM_DEVICE) return LYAP_OK;
+  return lyap_check_v(nv, sd->k, v);
 }
 
-int store_out(double* dst, const double* src_host, size_t count, int mem_kind, cudaStream_t st) {
-  if (!dst || count == 0) return LYAP_OK;
-  if (mem_kind == LYAP_MEM_HOST) {
-    std::memcpy(dst, src_host, count * sizeof(double));
-  } else {
-    LY_CUDA(cudaMemcpyAsync(dst, src_host, count * sizeof(double), cudaMemcpyHostToDevice, st));
-    LY_CUDA(cudaStreamSynchronize(st));
-  }
-  return LYAP_OK;
-}
+// Where a chunk's results go: host arrays, or the caller's device arrays
+// (written in stream order). Pointers are already offset to the chunk.
+struct ChunkOut {
+  int mem = LYAP_MEM_HOST;
+  double* f = nullptr;
+  double* g = nullptr;
+  lyap_result_info* info = nullptr;
+};
 
 // Final FP64 report for one chunk: trace, residual, error estimate, and
 // (with an adjoint solution Zadj) the gradient and the dual-weighted error
-// estimate |<z, r>| / |f|.
+// estimate |<z, r>| / |f|. Device outputs are written on the stream; the
+// host waits once for the per-result reports and the parameter check.
 int report_chunk(lyap_seed* sd, SeedWork& w, int Bc, const double2* Wp, const double2* Zadj, bool have_resid,
-                 cudaStream_t st, double* f_host, double* grad_host, lyap_result_info* info) {
+                 cudaStream_t st, const ChunkOut& out) {
   const int n = sd->n, k = sd->k;
   const size_t N = (size_t)n * k;
   if (w.Rres.count < (size_t)Bc * N) LY_TRY(w.Rres.alloc((size_t)Bc * N));
@@ -301,36 +331,49 @@ int report_chunk(lyap_seed* sd, SeedWork& w, int Bc, const double2* Wp, const do
     SysOp<double2> op;
     op.sd = sd;
     op.vinv = w.vinv.p;
-    DevBuf<int> lst, cnt;
-    LY_TRY(lst.alloc(Bc));
-    LY_TRY(cnt.alloc(1));
-    kry::k_iota<<<grid_of(Bc), 256, 0, st>>>(Bc, lst.p, cnt.p); lyap_count_launch();
-    LY_TRY(op.precond(lst.p, cnt.p, Bc, w.Rres.p, N, w.tmp.p, N, st));
+    if (w.lst.count < (size_t)Bc) LY_TRY(w.lst.alloc(Bc));
+    if (w.cnt.count < 1) LY_TRY(w.cnt.alloc(1));
+    kry::k_iota<<<grid_of(Bc), 256, 0, st>>>(Bc, w.lst.p, w.cnt.p); lyap_count_launch();
+    LY_TRY(op.precond(w.lst.p, w.cnt.p, Bc, w.Rres.p, N, w.tmp.p, N, st));
     kry::k_dot_h<double2><<<Bc, kry::NT, 0, st>>>((int)N, Bc, w.tmp.p, N, sd->h.p, w.red2.p, nullptr); lyap_count_launch();
+  }
+  if (out.mem == LYAP_MEM_DEVICE) {
+    if (out.f) {
+      k_trace_out<<<grid_of(Bc), 256, 0, st>>>(Bc, sd->f0, w.red0.p, out.f);
+      lyap_count_launch();
+    }
+    if (out.g && Zadj)
+      LY_CUDA(cudaMemcpyAsync(out.g, w.red3.p, sizeof(double) * Bc * k, cudaMemcpyDeviceToDevice, st));
   }
   LY_CUDA(cudaGetLastError());
   std::vector<double> tr(Bc), rn(Bc), ee(Bc), gr((size_t)Bc * k);
   LY_CUDA(cudaMemcpyAsync(tr.data(), w.red0.p, sizeof(double) * Bc, cudaMemcpyDeviceToHost, st));
   LY_CUDA(cudaMemcpyAsync(rn.data(), w.red1.p, sizeof(double) * Bc, cudaMemcpyDeviceToHost, st));
   LY_CUDA(cudaMemcpyAsync(ee.data(), w.red2.p, sizeof(double) * Bc, cudaMemcpyDeviceToHost, st));
-  if (Zadj) LY_CUDA(cudaMemcpyAsync(gr.data(), w.red3.p, sizeof(double) * Bc * k, cudaMemcpyDeviceToHost, st));
+  if (Zadj && out.mem == LYAP_MEM_HOST && out.g)
+    LY_CUDA(cudaMemcpyAsync(gr.data(), w.red3.p, sizeof(double) * Bc * k, cudaMemcpyDeviceToHost, st));
+  LY_CUDA(cudaMemcpyAsync(w.vbad_host, w.vbad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   LY_CUDA(cudaStreamSynchronize(st));
+  if (*w.vbad_host) {
+    lyap_set_last_error(std::to_string(*w.vbad_host) + " parameter(s) zero or not finite");
+    return LYAP_EINVAL;
+  }
   for (int b = 0; b < Bc; ++b) {
-    double f = sd->f0 + tr[b];
-    f_host[b] = f;
-    if (info) {
-      info[b].rel_resid = sd->ph_norm > 0 ? rn[b] / sd->ph_norm : rn[b];
-      info[b].err_est = f != 0 ? std::fabs(ee[b]) / std::fabs(f) : std::fabs(ee[b]);
+    const double f = sd->f0 + tr[b];
+    if (out.mem == LYAP_MEM_HOST && out.f) out.f[b] = f;
+    if (out.info) {
+      out.info[b].rel_resid = sd->ph_norm > 0 ? rn[b] / sd->ph_norm : rn[b];
+      out.info[b].err_est = f != 0 ? std::fabs(ee[b]) / std::fabs(f) : std::fabs(ee[b]);
     }
-    if (grad_host)
-      for (int i = 0; i < k; ++i) grad_host[(size_t)b * k + i] = gr[(size_t)b * k + i];
+    if (out.mem == LYAP_MEM_HOST && out.g && Zadj)
+      for (int i = 0; i < k; ++i) out.g[(size_t)b * k + i] = gr[(size_t)b * k + i];
   }
   return LYAP_OK;
 }
 
-// Solve all nv systems (FP64 or mixed), primal (and adjoint when want_adj).
-int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t st, double* f_host,
-              double* grad_host, double* w_out, int w_mem, lyap_result_info* info) {
+// Solve all nv systems (FP64 or mixed), primal (and adjoint when want_grad).
+int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t st, double* f_out, double* g_out,
+              bool want_grad, double* w_out, lyap_result_info* info) {
   const int n = sd->n, k = sd->k, nv = io.nv;
   const size_t N = (size_t)n * k;
   SolveParams prm;
@@ -350,18 +393,23 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
   }
   B = std::min(B, std::max(nv, 1));
   if (w.vinv.count < (size_t)B * k) LY_TRY(w.vinv.alloc((size_t)B * k));
+  if (io.mem == LYAP_MEM_HOST && w.vdev.count < (size_t)B * k) LY_TRY(w.vdev.alloc((size_t)B * k));
   if (w.Wp.count < (size_t)B * N) LY_TRY(w.Wp.alloc((size_t)B * N));
-  if (grad_host && w.Zadj.count < (size_t)B * N) LY_TRY(w.Zadj.alloc((size_t)B * N));
+  if (want_grad && w.Zadj.count < (size_t)B * N) LY_TRY(w.Zadj.alloc((size_t)B * N));
   if (w.Rres.count < (size_t)B * N) LY_TRY(w.Rres.alloc((size_t)B * N));
+  if (w.vbad.count < 1) LY_TRY(w.vbad.alloc(1));
+  if (!w.vbad_host) LY_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&w.vbad_host), sizeof(int), cudaHostAllocDefault));
+  LY_CUDA(cudaMemsetAsync(w.vbad.p, 0, sizeof(int), st));
   if (o.pbar > 0) LY_TRY(lyap_tsvd_prepare(sd, o.pbar, st));
-  DevBuf<double> vdev;
-  LY_TRY(vdev.alloc((size_t)B * k));
   std::vector<int> it, stt, ita, sta, rsteps;
   for (int c0 = 0; c0 < nv; c0 += B) {
     const int Bc = std::min(B, nv - c0);
-    LY_CUDA(cudaMemcpyAsync(vdev.p, io.v.data() + (size_t)c0 * k, sizeof(double) * Bc * k,
-                            cudaMemcpyHostToDevice, st));
-    k_vinv<<<grid_of((size_t)Bc * k), 256, 0, st>>>(Bc * k, vdev.p, w.vinv.p); lyap_count_launch();
+    const double* vsrc = io.v + (size_t)c0 * k;
+    if (io.mem == LYAP_MEM_HOST) {
+      LY_CUDA(cudaMemcpyAsync(w.vdev.p, vsrc, sizeof(double) * Bc * k, cudaMemcpyHostToDevice, st));
+      vsrc = w.vdev.p;
+    }
+    k_vinv<<<grid_of((size_t)Bc * k), 256, 0, st>>>(Bc * k, vsrc, w.vinv.p, w.vbad.p); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     bool have_resid = false;
     const WoodState* wood = nullptr;
@@ -382,7 +430,7 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
       LY_TRY(gcrodr_chunk(op, Bc, sd->Ph.p, 0, sd->rec64, prm, w.ws64, it, stt, st));
       LY_CUDA(cudaMemcpyAsync(w.Wp.p, w.ws64.X.p, sizeof(double2) * Bc * N, cudaMemcpyDeviceToDevice, st));
       rsteps.assign(Bc, 0);
-      if (grad_host) {
+      if (want_grad) {
         SysOp<double2> opa;
         opa.sd = sd;
         opa.adjoint = true;
@@ -396,26 +444,28 @@ int run_sweep(lyap_seed* sd, const CallIO& io, const lyap_opts& o, cudaStream_t 
         }
       }
     } else {
-      LY_TRY(lyap_mixed_chunk(sd, Bc, w.vinv.p, o, prm, st, w.ws32, w.ws32adj, w.Wp.p, grad_host ? w.Zadj.p : nullptr,
+      LY_TRY(lyap_mixed_chunk(sd, Bc, w.vinv.p, o, prm, st, w.ws32, w.ws32adj, w.Wp.p, want_grad ? w.Zadj.p : nullptr,
                               w.Rres.p, it, stt, rsteps));
       have_resid = true;
     }
-    std::vector<double> gtmp;
-    double* gh = nullptr;
-    if (grad_host) gh = grad_host + (size_t)c0 * k;
-    lyap_result_info* inf = info ? info + c0 : nullptr;
-    LY_TRY(report_chunk(sd, w, Bc, w.Wp.p, grad_host ? w.Zadj.p : nullptr, have_resid, st, f_host + c0, gh, inf));
-    if (inf)
+    ChunkOut out;
+    out.mem = io.mem;
+    out.f = f_out ? f_out + c0 : nullptr;
+    out.g = g_out ? g_out + (size_t)c0 * k : nullptr;
+    out.info = info ? info + c0 : nullptr;
+    LY_TRY(report_chunk(sd, w, Bc, w.Wp.p, want_grad ? w.Zadj.p : nullptr, have_resid, st, out));
+    if (out.info)
       for (int b = 0; b < Bc; ++b) {
-        inf[b].iters = it[b];
-        inf[b].status = stt[b];
-        inf[b].refine_steps = rsteps.empty() ? 0 : rsteps[b];
+        out.info[b].iters = it[b];
+        out.info[b].status = stt[b];
+        out.info[b].refine_steps = rsteps.empty() ? 0 : rsteps[b];
       }
     if (w_out) {
       double* dst = w_out + (size_t)c0 * N * 2;
       LY_CUDA(cudaMemcpyAsync(dst, w.Wp.p, sizeof(double2) * Bc * N,
-                              w_mem == LYAP_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
-      LY_CUDA(cudaStreamSynchronize(st));
+                              io.mem == LYAP_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+      // the next chunk overwrites Wp
+      if (c0 + Bc < nv || io.mem == LYAP_MEM_HOST) LY_CUDA(cudaStreamSynchronize(st));
     }
   }
   // the call's stream waits for the recycle updates still running on the
@@ -437,17 +487,13 @@ int entry(lyap_seed* sd, int nv, const double* v, int mem_kind, const lyap_opts*
   LY_CUDA(cudaSetDevice(sd->device));
   cudaStream_t st = pick_stream(sd->ctx, o);
   CallIO io;
-  LY_TRY(load_v(sd, nv, v, mem_kind, st, io));
+  LY_TRY(load_v(sd, nv, v, mem_kind, io));
   if (nv == 0) return LYAP_OK;
   if (o.inject & LYAP_INJECT_ALLOC_FAIL) {
     lyap_set_last_error("injected allocation failure");
     return LYAP_ENOMEM;
   }
-  std::vector<double> f(nv), g(grad_out ? (size_t)nv * sd->k : 0);
-  LY_TRY(run_sweep(sd, io, o, st, f.data(), grad_out ? g.data() : nullptr, w_out, mem_kind, info));
-  if (trace_out) LY_TRY(store_out(trace_out, f.data(), nv, mem_kind, st));
-  if (grad_out) LY_TRY(store_out(grad_out, g.data(), g.size(), mem_kind, st));
-  return LYAP_OK;
+  return run_sweep(sd, io, o, st, trace_out, grad_out, grad_out != nullptr, w_out, info);
 }
 
 }  // namespace

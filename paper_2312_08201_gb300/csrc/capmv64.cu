@@ -124,12 +124,7 @@ int capmv64_launch(const CapArgs64& a, cudaStream_t st) {
   const int kk = a.k * a.k;
   const int SB = TNC / kk;
   const size_t smem = (size_t)TI * SROW * sizeof(double2);  // >= operand tiles
-  static std::once_flag once;
-  static cudaError_t attr_rc = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_rc = cudaFuncSetAttribute(k_capmv64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  LY_CUDA(attr_rc);
+  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_capmv64), smem));
   dim3 grid((a.n + TI - 1) / TI, (a.nsys + SB - 1) / SB);
   // algorithmic work per system: the Cauchy-panel product, 8 flops per
   // complex MAC over n^2 k^2 MACs, plus the O(n k^2) epilogue

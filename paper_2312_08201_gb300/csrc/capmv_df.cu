@@ -251,12 +251,7 @@ int capmv_df_launch(const CapArgs64& a, const float4* Lff, double lc_scale, doub
   const int kk = a.k * a.k;
   const int SB = TNC / kk;
   const size_t smem = (size_t)TI * SROW * sizeof(double2);
-  static std::once_flag once;
-  static cudaError_t attr_rc = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_rc = cudaFuncSetAttribute(k_capmv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  });
-  LY_CUDA(attr_rc);
+  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_capmv_df), smem));
   k_panel_ff<<<a.nsys, 256, 0, st>>>(a, p_scale, sw, panel);
   lyap_count_launch();
   dim3 grid((a.n + TI - 1) / TI, (a.nsys + SB - 1) / SB);

@@ -49,6 +49,11 @@
 
 void lyap_set_last_error(const std::string& msg);
 
+// Raise the dynamic shared-memory limit of kernel `func` to at least `bytes`
+// on the current device. The setting belongs to the device's context, so it
+// is made once per (device, kernel) and again only for a larger size.
+int lyap_smem_optin(const void* func, size_t bytes);
+
 // ------------------------------------------------------------ device memory
 // Owning device buffer (no exceptions; allocation reports a status code).
 template <typename T>
@@ -154,5 +159,9 @@ int lyap_validate_opts(const lyap_opts* in, lyap_opts* out);
 int lyap_check_v(int nv, int k, const double* v_host);
 
 // Seed factor (seed.cu)
+// P1 (device n x k, may be null): the first block X0 B_r of the right-hand
+// side factor of eq. (rhs_newexpression), given instead of G; the seed's
+// traces then count only X(v) - X0 (f0 = 0).
 int lyap_seed_build(lyap_ctx* ctx, lyap_seed* seed, const double* A0, const double* U,
-                    const double* V, const double* G, const double* E, cudaStream_t st);
+                    const double* V, const double* G, const double* E, cudaStream_t st,
+                    const double* P1 = nullptr);

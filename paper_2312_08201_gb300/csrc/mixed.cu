@@ -37,6 +37,8 @@ struct MixedState {
   DevBuf<float> D;                 // ncap x mpad
   tc::Maps maps;
   DevBuf<int> err;
+  bool inject_wait = false;  // LYAP_INJECT_DEVICE_WAIT for the call in progress
+  double h_norm = -1.0;      // ||h||, the adjoint right-hand side's norm (set on first use)
   // refinement work
   int bcap = 0;
   DevBuf<double2> R64;
@@ -191,6 +193,7 @@ int ensure_cols(lyap_seed* sd, int ncols) {
   LY_TRY(ms.Bhi.alloc((size_t)cap * ms.kpad));
   LY_TRY(ms.Blo.alloc((size_t)cap * ms.kpad));
   LY_TRY(ms.D.alloc((size_t)cap * ms.mpad));
+  LY_CUDA(cudaMemset(ms.D.p, 0, ms.D.bytes()));      // defined even where a timed-out GEMM wrote nothing
   LY_CUDA(cudaMemset(ms.Bhi.p, 0, ms.Bhi.bytes()));  // K padding stays zero
   LY_CUDA(cudaMemset(ms.Blo.p, 0, ms.Blo.bytes()));
   LY_TRY(tc::make_map(&ms.maps.b_hi, ms.Bhi.p, cap, ms.kpad, tc::BN));
@@ -215,7 +218,8 @@ int mixed_apply(lyap_seed* sd, bool adjoint, const double* vinv, const int* list
   LY_CUDA(cudaGetLastError());
   // algorithmic work per system: 2 (real) x (2n)^2 x k^2 MACs per product, three products
   const int ph = prof_begin(PK_TCGEMM, st);
-  LY_TRY(tc::launch(ms.maps, ms.D.p, ms.mpad, 2 * n, ms.mpad, ms.kpad, count, kk, nsys * kk, nsys * kk, ms.err.p, st));
+  LY_TRY(tc::launch(ms.maps, ms.D.p, ms.mpad, 2 * n, ms.mpad, ms.kpad, count, kk, nsys * kk, nsys * kk, ms.err.p, st,
+                    ms.inject_wait));
   prof_end(ph, st, 3.0 * 2.0 * (2.0 * n) * (2.0 * n) * kk, 0.0, count ? 0 : nsys, count);
   const int pe = prof_begin(PK_EPI32, st);
   k_epi<T2><<<g, 256, 0, st>>>(n, k, list, count, nsys, ms.D.p, ms.mpad, In, in_ss, P1, ms.Gd32.p, adjoint ? 1 : 0,
@@ -305,7 +309,15 @@ int refine(lyap_seed* sd, int Bc, const double* vinv, const double2* rhs, double
       lyap_count_launch();
       LY_CUDA(cudaGetLastError());
       LY_CUDA(cudaMemcpyAsync(nrm.data(), ms.norms.p, sizeof(double) * Bc, cudaMemcpyDeviceToHost, st));
+      int herr_step = 0;
+      LY_CUDA(cudaMemcpyAsync(&herr_step, ms.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
       LY_CUDA(cudaStreamSynchronize(st));
+      if (herr_step) {
+        // a bounded wait of a tensor-core kernel ran out: stop at the first sync
+        lyap_set_last_error("tensor-core GEMM wait timed out (code " + std::to_string(herr_step) + ")");
+        LY_CUDA(cudaMemsetAsync(ms.err.p, 0, sizeof(int), st));
+        return LYAP_EDEVICE_TIMEOUT;
+      }
       std::vector<int> keep;
       for (int b : act) {
         rsteps[b] = step;
@@ -419,6 +431,19 @@ int lyap_mixed_prepare(lyap_seed* sd, cudaStream_t st) {
   return LYAP_OK;
 }
 
+// After a device timeout the FP32 recycle spaces may hold vectors built with
+// an incomplete operator: wait for the work in flight and forget them, so the
+// next call starts its recycling afresh.
+static void drop_recycle(lyap_seed* sd, KrylovWS<float2>& ws, cudaStream_t st) {
+  cudaStreamSynchronize(st);
+  if (ws.side) cudaStreamSynchronize(ws.side);
+  for (Recycle<float2>* r : {&sd->rec32, &sd->rec32_adj}) {
+    r->pending = false;
+    r->s = 0;
+    r->c0_valid = false;
+  }
+}
+
 int lyap_mixed_chunk(lyap_seed* sd, int Bc, const double* vinv, const lyap_opts& o, const SolveParams& prm,
                      cudaStream_t st, KrylovWS<float2>& ws, KrylovWS<float2>& wsadj, double2* Wp_out,
                      double2* Zadj_out, double2* Rres_out, std::vector<int>& iters, std::vector<int>& status,
@@ -428,6 +453,11 @@ int lyap_mixed_chunk(lyap_seed* sd, int Bc, const double* vinv, const lyap_opts&
   status.assign(Bc, LYAP_OK);
   rsteps.assign(Bc, 0);
   MixedState& ms = *sd->mixed;
+  ms.inject_wait = (o.inject & LYAP_INJECT_DEVICE_WAIT) != 0;
+  struct ClearInject {
+    MixedState& m;
+    ~ClearInject() { m.inject_wait = false; }
+  } clear_inject{ms};
   if (o.pbar > 0 && sd->tsvd_r > 0) {
     // Cap(v_b)^{-1} for the whole chunk, shared by every refinement step and
     // by the adjoint solves (which apply its transpose)
@@ -437,7 +467,12 @@ int lyap_mixed_chunk(lyap_seed* sd, int Bc, const double* vinv, const lyap_opts&
     full.cinv = ms.wcinv_full.p;
     LY_TRY(wood_prepare(sd, r, Bc, vinv, false, full, st));
   }
-  LY_TRY(refine(sd, Bc, vinv, sd->Ph.p, sd->ph_norm, false, sd->rec32, o, prm, st, ws, Wp_out, iters, status, rsteps));
+  {
+    const int rc = refine(sd, Bc, vinv, sd->Ph.p, sd->ph_norm, false, sd->rec32, o, prm, st, ws, Wp_out, iters, status,
+                          rsteps);
+    if (rc == LYAP_EDEVICE_TIMEOUT) drop_recycle(sd, ws, st);
+    if (rc != LYAP_OK) return rc;
+  }
   // every system's final residual was evaluated (and kept) by its last refinement step
   if (Rres_out)
     LY_CUDA(cudaMemcpyAsync(Rres_out, sd->mixed->R64.p, sizeof(double2) * (size_t)Bc * sd->n * sd->k,
@@ -445,15 +480,21 @@ int lyap_mixed_chunk(lyap_seed* sd, int Bc, const double* vinv, const lyap_opts&
   if (Zadj_out) {
     double hn = 0;
     {
-      DevBuf<double> t;
-      LY_TRY(t.alloc(1));
-      kry::k_norms<double2><<<1, kry::NT, 0, st>>>(sd->n * sd->k, 1, sd->h.p, 0, t.p);
-      lyap_count_launch();
-      LY_CUDA(cudaMemcpyAsync(&hn, t.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-      LY_CUDA(cudaStreamSynchronize(st));
+      // ||h|| once per seed (a v-independent scalar)
+      if (ms.h_norm < 0) {
+        kry::k_norms<double2><<<1, kry::NT, 0, st>>>(sd->n * sd->k, 1, sd->h.p, 0, ms.norms.p);
+        lyap_count_launch();
+        LY_CUDA(cudaMemcpyAsync(&ms.h_norm, ms.norms.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        LY_CUDA(cudaStreamSynchronize(st));
+      }
+      hn = ms.h_norm;
     }
     std::vector<int> ita(Bc, 0), sta(Bc, LYAP_OK), rsa(Bc, 0);
-    LY_TRY(refine(sd, Bc, vinv, sd->h.p, hn, true, sd->rec32_adj, o, prm, st, wsadj, Zadj_out, ita, sta, rsa));
+    {
+      const int rc = refine(sd, Bc, vinv, sd->h.p, hn, true, sd->rec32_adj, o, prm, st, wsadj, Zadj_out, ita, sta, rsa);
+      if (rc == LYAP_EDEVICE_TIMEOUT) drop_recycle(sd, wsadj, st);
+      if (rc != LYAP_OK) return rc;
+    }
     for (int b = 0; b < Bc; ++b) {
       iters[b] += ita[b];
       rsteps[b] += rsa[b];

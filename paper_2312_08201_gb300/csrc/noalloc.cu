@@ -1,22 +1,21 @@
 // Allocation-free FP64 check of given capacitance solutions.
 //
-// Some callers cannot call cudaMalloc: code that runs while its stream is
-// being captured into a CUDA graph (allocation calls are not allowed there
-// in every mode), embedded or real-time hosts whose device memory is carved
-// out once at start-up by their own pool and must not grow afterwards, and
-// plug-ins that run inside another framework's allocator and may not go
-// around it. lyap_check_solution_noalloc serves them: it evaluates
-// f(v) = trace(E X(v)) and the relative FP64 capacitance residual for
-// solutions W' the caller already holds, with every intermediate in the
+// Some callers cannot call cudaMalloc while they run: hosts whose device
+// memory is carved out once at start-up by their own pool and must not grow
+// afterwards, and plug-ins that run inside another framework's allocator and
+// may not go around it. lyap_check_solution_noalloc serves them: it
+// evaluates f(v) = trace(E X(v)) and the relative FP64 capacitance residual
+// for solutions W' the caller already holds, with every intermediate in the
 // static device array below instead of fresh allocations.
 //
-// The array holds LYAP_NOALLOC_SCRATCH complex doubles (32 MiB plus a
-// little): enough for nv * n * k <= 2^21 residual entries together with
-// the nv * k reciprocals of v. Every GPU that loads the library keeps it
-// until the process exits. All calls share it: calls that overlap on the
-// GPU (different streams, or host threads without ordering) race on it.
-// Every element a call reads was written earlier in the same call, so no
-// part of it has to start at zero and nothing is cleared.
+// The array holds LYAP_NOALLOC_SCRATCH complex doubles (33 MiB, 34,603,008
+// bytes): enough for nv * n * k <= 2^21 residual entries together with the
+// nv * k reciprocals of v. Every GPU that loads the library keeps it until
+// the process exits. All calls share it and it keeps the last call's
+// contents: calls that overlap on the GPU (different streams, or host
+// threads without ordering) race on it. Every element a call reads was
+// written earlier in the same call, so no part of it has to start at zero
+// and nothing is cleared.
 #include <mutex>
 
 #include "capmv.cuh"
@@ -36,7 +35,7 @@ std::mutex g_setup_mu;
 double2* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // 1/v for every entry; a zero or non-finite v_i gives NaN, which then shows
-// in the outputs of its system.
+// in the residual of its system.
 __global__ void k_noalloc_vinv(int count, const double* __restrict__ v, double* __restrict__ vinv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;

@@ -345,12 +345,7 @@ int residual(const CapArgs64& a, const CUtensorMap& mapA, const int* eA, int mpa
   const int kk = a.k * a.k;
   const int ncols_cap = a.nsys * kk;
   if (ncols_cap > pn.ncap) return LYAP_EINVAL;
-  static std::once_flag once;
-  static cudaError_t attr_rc = cudaSuccess;
-  std::call_once(once, [] {
-    attr_rc = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-  });
-  LY_CUDA(attr_rc);
+  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_oz_gemm), SMEM_BYTES));
   k_slice_B<<<a.nsys, 256, sizeof(double) * kpad, st>>>(a, pn.ncap, kpad, reinterpret_cast<__nv_bfloat16*>(pn.S),
                                                          pn.eB);
   lyap_count_launch();

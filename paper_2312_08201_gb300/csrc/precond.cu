@@ -474,13 +474,7 @@ size_t cap_smem(int r) {
 
 template <int K>
 int launch_cap_build(lyap_seed* sd, int r, int B, const double* vinv, const WoodState& ws, cudaStream_t st) {
-  static std::once_flag once;
-  static cudaError_t attr_rc = cudaSuccess;
-  std::call_once(once, [] {
-    attr_rc = cudaFuncSetAttribute(k_cap_build<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)cap_smem<K>(RMAX));
-  });
-  LY_CUDA(attr_rc);
+  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_cap_build<K>), cap_smem<K>(RMAX)));
   k_cap_build<K><<<B, WT, cap_smem<K>(r), st>>>(sd->n, r, sd->Gdf.p, vinv, ws.Nl, ws.Ml, ws.ldr, ws.cinv);
   return LYAP_OK;
 }

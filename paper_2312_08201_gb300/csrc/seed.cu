@@ -229,7 +229,7 @@ int re_dot(const double2* a, const double2* b, size_t count, double* out_host, c
 }  // namespace
 
 int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double* U, const double* V,
-                    const double* G, const double* E, cudaStream_t st) {
+                    const double* G, const double* E, cudaStream_t st, const double* P1) {
   const int n = sd->n, k = sd->k, g = sd->g;
   const size_t nn = (size_t)n * n;
   LY_BLAS(cublasSetStream(ctx->blas, st));
@@ -384,25 +384,36 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
   DevBuf<double2> Vc, Uc, Gc;
   LY_TRY(Vc.alloc((size_t)n * k));
   LY_TRY(Uc.alloc((size_t)n * k));
-  LY_TRY(Gc.alloc((size_t)n * g));
   k_real_to_complex<<<grid_for((size_t)n * k), 256, 0, st>>>((size_t)n * k, V, Vc.p); lyap_count_launch();
   k_real_to_complex<<<grid_for((size_t)n * k), 256, 0, st>>>((size_t)n * k, U, Uc.p); lyap_count_launch();
-  k_real_to_complex<<<grid_for((size_t)n * g), 256, 0, st>>>((size_t)n * g, G, Gc.p); lyap_count_launch();
   LY_CUDA(cudaGetLastError());
   LY_TRY(sd->Ub.alloc((size_t)n * k));
   LY_TRY(sd->Vb.alloc((size_t)n * k));
   LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, n, one, sd->Qi.p, n, Vc.p, n, zero, sd->Ub.p, n));
   LY_TRY(zgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, n, k, n, one, sd->Qp.p, n, Uc.p, n, zero, sd->Vb.p, n));
 
-  // ---- seed solution in eigen-coordinates: X0h = -Lc o (Gh Gh^T) -----------
-  DevBuf<double2> Gh;
-  LY_TRY(Gh.alloc((size_t)n * g));
-  LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, g, n, one, sd->Qi.p, n, Gc.p, n, zero, Gh.p, n));
-  LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, g, one, Gh.p, n, Gh.p, n, zero, W1.p, n));
-  k_cauchy_hadamard<<<grid_for(nn), 256, 0, st>>>(n, sd->lam.p, W1.p, -1.0); lyap_count_launch();  // W1 = X0h
-  LY_CUDA(cudaGetLastError());
   LY_TRY(sd->Ph.alloc((size_t)n * k));
-  LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, n, one, W1.p, n, sd->Vb.p, n, zero, sd->Ph.p, n));
+  if (P1) {
+    // The right-hand side factor's first block is given (P1 = X0 B_r of
+    // eq. (rhs_newexpression)): Ph = Qi P1, and f counts only the change
+    // X - X0 (f0 = 0). The projected equations of §2.2 are built this way.
+    LY_TRY(Gc.alloc((size_t)n * k));
+    k_real_to_complex<<<grid_for((size_t)n * k), 256, 0, st>>>((size_t)n * k, P1, Gc.p); lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, n, one, sd->Qi.p, n, Gc.p, n, zero, sd->Ph.p, n));
+  } else {
+    // ---- seed solution in eigen-coordinates: X0h = -Lc o (Gh Gh^T) ---------
+    LY_TRY(Gc.alloc((size_t)n * g));
+    k_real_to_complex<<<grid_for((size_t)n * g), 256, 0, st>>>((size_t)n * g, G, Gc.p); lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    DevBuf<double2> Gh;
+    LY_TRY(Gh.alloc((size_t)n * g));
+    LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, g, n, one, sd->Qi.p, n, Gc.p, n, zero, Gh.p, n));
+    LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, g, one, Gh.p, n, Gh.p, n, zero, W1.p, n));
+    k_cauchy_hadamard<<<grid_for(nn), 256, 0, st>>>(n, sd->lam.p, W1.p, -1.0); lyap_count_launch();  // W1 = X0h
+    LY_CUDA(cudaGetLastError());
+    LY_TRY(zgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, k, n, one, W1.p, n, sd->Vb.p, n, zero, sd->Ph.p, n));
+  }
   {
     double pn = 0;
     LY_TRY(re_dot(sd->Ph.p, nullptr, (size_t)n * k, &pn, st));
@@ -420,7 +431,8 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
   } else {
     LY_TRY(zgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, n, n, n, one, sd->Qp.p, n, sd->Qp.p, n, zero, W2.p, n));
   }
-  LY_TRY(re_dot(W2.p, W1.p, nn, &sd->f0, st));  // Eh, X0h symmetric: trace(Eh X0h) = sum Eh o X0h
+  if (P1) sd->f0 = 0.0;
+  else LY_TRY(re_dot(W2.p, W1.p, nn, &sd->f0, st));  // Eh, X0h symmetric: trace(Eh X0h) = sum Eh o X0h
   k_cauchy_hadamard<<<grid_for(nn), 256, 0, st>>>(n, sd->lam.p, W2.p, 2.0); lyap_count_launch();  // W2 = 2 Eh o Lc
   LY_CUDA(cudaGetLastError());
   LY_TRY(sd->h.alloc((size_t)n * k));

@@ -321,12 +321,7 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
       // FP32 solves: the whole recycle start in one kernel while C_b fits in shared memory
       const size_t rsm = kry::recstart32_smem_bytes(s, N);
       if (rsm <= 200 * 1024) {
-        static std::once_flag once;
-        static cudaError_t rc_attr = cudaSuccess;
-        std::call_once(once, [] {
-          rc_attr = cudaFuncSetAttribute(kry::k_recstart32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        });
-        LY_CUDA(rc_attr);
+        LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(kry::k_recstart32), 200 * 1024));
         const int ph_ = prof_begin(PK_RECSTART, st);
         kry::k_recstart32<<<B, kry::RS_T, rsm, st>>>(n, k, s, Lchunk, cchunk, rec.Ut.p, rec.C0Ut.p, op.vinv, ws.C.p,
                                                      ws.U.p, ss, ws.X.p, ws.R.p, ws.ok.p);
@@ -416,7 +411,8 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
       LY_TRY(op.apply(Lcur, ccur, B, Zj + (size_t)j * NS, (size_t)m * NS, Vj + (size_t)(j + 1) * NS,
                       (size_t)(m + 1) * NS, st));
       {
-        // CGS2: the basis is read three times (dots, update + dots, update), w five times
+        // CGS2's algorithmic traffic: one read of the nb basis vectors, w read
+        // and written once (the kernel itself rereads the basis from L2)
         const int nb = s_cur + j + 1;
         const int ph = prof_begin(PK_ORTHO, st);
         // the same kernel applies the Givens least-squares update to the new column
@@ -425,7 +421,7 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
         kry::k_ortho<T2><<<B, kry::OT, 0, st>>>(N, j, m, s_cur, Lcur, ccur, ws.V.p, ws.C.p, css, ws.H.p, ws.Bk.p,
                                                 smax, la);
         lyap_count_launch();
-        prof_end(ph, st, 2.0 * 2.0 * 8.0 * nb * N, (3.0 * nb + 7.0) * N * sizeof(T2), 0, ccur);
+        prof_end(ph, st, 2.0 * 2.0 * 8.0 * nb * N, (nb + 2.0) * N * sizeof(T2), 0, ccur);
       }
       kry::k_compact<<<1, 1024, 0, st>>>(Lcur, ccur, ws.flag.p, Lnext, cnext, ws.poll_dev + j % RING);
       lyap_count_launch();
@@ -496,14 +492,8 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
         const int ph_ = prof_begin(PK_RITZ, us);
         const size_t rsm = kry::ritz_smem_bytes(m, smax);
       if (rsm > 48 * 1024) {
-        // the largest size any call needs (m <= 60, s <= 16), set once for all threads
-        static std::once_flag once;
-        static cudaError_t rc_attr = cudaSuccess;
-        std::call_once(once, [] {
-          rc_attr = cudaFuncSetAttribute(kry::k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kry::ritz_smem_bytes(60, 16));
-        });
-        LY_CUDA(rc_attr);
+        // the largest size any call needs (m <= 60, s <= 16)
+        LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(kry::k_ritz), kry::ritz_smem_bytes(60, 16)));
       }
       kry::k_ritz<<<Bw, 32, rsm, us>>>(m, smax, s_cur, s, Lwant, cwant, ws.jstop.p, ws.H0.p,
                                                         ws.Bk.p, ws.F.p, ws.UU.p, ws.work.p, ws.wstride, ws.Pu.p,
@@ -589,12 +579,7 @@ namespace kry {
 template <typename T2>
 int launch_gram(int N, const int* list, const int* count, int B, int expect, const Seg2<T2>& A, const Seg2<T2>& Bm,
                 double2* out, int ldo, size_t os, cudaStream_t st) {
-  static std::once_flag once;
-  static cudaError_t rc = cudaSuccess;
-  std::call_once(once, [] {
-    rc = cudaFuncSetAttribute(k_gram<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem_bytes<T2>());
-  });
-  LY_CUDA(rc);
+  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_gram<T2>), gram_smem_bytes<T2>()));
   // split each system over a cluster of CTAs only while the systems alone leave SMs idle
   const int split = expect * 4 <= 152 ? GSPLIT : 1;
   cudaLaunchConfig_t cfg = {};

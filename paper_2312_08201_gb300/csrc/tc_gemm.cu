@@ -11,7 +11,9 @@
 //               32-lane quarter) and store FP32 columns to global memory.
 // Every mbarrier wait is bounded by a clock-based timeout; on expiry the
 // CTA records an error, waits (bounded) for its copies in flight, releases
-// TMEM and returns.
+// TMEM and returns. With `no_tma` set (the LYAP_INJECT_DEVICE_WAIT test
+// hook) the producer issues no copy at all, so the MMA warp's first wait
+// runs out after `wait_cycles` with nothing in flight.
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
               float* __restrict__ D, int ldd, int mrows, int ktiles, const int* __restrict__ count, int col_mult,
-              int ncols_host, int* __restrict__ err) {
+              int ncols_host, int* __restrict__ err, int no_tma, long long wait_cycles) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -76,10 +78,10 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) {
     if (lane == 0) {
       int kt = 0;
-      for (; kt < ktiles; ++kt) {
+      for (; kt < ktiles && !no_tma; ++kt) {
         const int s = kt % STAGES;
         const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-        if (!mbar_wait(sm_addr(&empty[s]), ph ^ 1u)) {
+        if (!mbar_wait(sm_addr(&empty[s]), ph ^ 1u, wait_cycles)) {
           atomicExch(err, 1);
           ctl[2] = 1;
           break;
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(192, 1)
       for (; kt < ktiles; ++kt) {
         const int s = kt % STAGES;
         const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-        if (!mbar_wait(sm_addr(&full[s]), ph)) {
+        if (!mbar_wait(sm_addr(&full[s]), ph, wait_cycles)) {
           atomicExch(err, 2);
           ctl[2] = 1;
           break;
@@ -126,8 +128,8 @@ __global__ void __launch_bounds__(192, 1)
     }
   } else {
     const int q = warp & 3;  // lanes this warp may read: 32q .. 32q+31
-    const bool ready = __all_sync(0xffffffffu, mbar_wait(sm_addr(accum), 0u));
-    if (ready) {
+    const bool ready = __all_sync(0xffffffffu, mbar_wait(sm_addr(accum), 0u, wait_cycles));
+    if (ready && !no_tma) {
       tc_fence_after();
       const int grow = m0 + q * 32 + lane;
 #pragma unroll 1
@@ -149,7 +151,8 @@ __global__ void __launch_bounds__(192, 1)
   // On a timeout, wait (bounded) for the stages whose copies were issued but
   // not consumed, so no TMA write lands after the CTA has gone.
   if (threadIdx.x == 0 && ctl[2]) {
-    for (int kt = ctl[1]; kt < ctl[0]; ++kt) mbar_wait(sm_addr(&full[kt % STAGES]), (uint32_t)(kt / STAGES) & 1u);
+    for (int kt = ctl[1]; kt < ctl[0]; ++kt)
+      mbar_wait(sm_addr(&full[kt % STAGES]), (uint32_t)(kt / STAGES) & 1u, wait_cycles);
   }
   __syncthreads();
   if (warp == 1) {
@@ -204,17 +207,14 @@ int make_map(CUtensorMap* map, const void* base, int rows, int kpad, int box_row
 }
 
 int launch(const Maps& m, float* D, int ldd, int mrows, int mpad, int kpad, const int* count, int col_mult,
-           int ncols_host, int ncols_cap, int* err, cudaStream_t st) {
+           int ncols_host, int ncols_cap, int* err, cudaStream_t st, bool inject_no_tma) {
   if (mpad % BM != 0 || kpad % BK != 0 || ncols_cap <= 0) return LYAP_EINVAL;
-  static std::once_flag once;
-  static cudaError_t attr_rc = cudaSuccess;
-  std::call_once(once, [] {
-    attr_rc = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-  });
-  LY_CUDA(attr_rc);
+  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_tc_gemm), SMEM_BYTES));
   dim3 grid(mpad / BM, (ncols_cap + BN - 1) / BN);
+  // the injected wait gives up after about 50 us instead of about 2 s
+  const long long wait_cycles = inject_no_tma ? 100000LL : tcu::WAIT_CYCLES;
   k_tc_gemm<<<grid, 192, SMEM_BYTES, st>>>(m.a_hi, m.a_lo, m.b_hi, m.b_lo, D, ldd, mrows, kpad / BK, count, col_mult,
-                                          ncols_host, err);
+                                          ncols_host, err, inject_no_tma ? 1 : 0, wait_cycles);
   lyap_count_launch();
   LY_CUDA(cudaGetLastError());
   return LYAP_OK;

@@ -28,8 +28,10 @@ int make_map(CUtensorMap* map, const void* base, int rows, int kpad, int box_row
 // D (ldd floats per column) for columns [0, ncols) where ncols = *count *
 // col_mult when count != nullptr (device), else ncols_host. Grid covers
 // mpad/BM x ceil(ncols_cap/BN); tiles past ncols exit at once. err: device
-// int set non-zero if a bounded wait expired.
+// int set non-zero if a bounded wait expired. inject_no_tma (test hook of
+// LYAP_INJECT_DEVICE_WAIT): no copy is issued, every wait is short, the
+// MMA warp's wait runs out, err is set and D is left untouched.
 int launch(const Maps& m, float* D, int ldd, int mrows, int mpad, int kpad, const int* count, int col_mult,
-           int ncols_host, int ncols_cap, int* err, cudaStream_t st);
+           int ncols_host, int ncols_cap, int* err, cudaStream_t st, bool inject_no_tma = false);
 
 }  // namespace tc

@@ -227,3 +227,34 @@ def test_mixed_with_sliced_residual(ctx):
     f, info = seed.trace_EX(vs[::4], return_info=True, precision=ly.BF16_IR, residual=ly.RESID_TC)
     assert rel_err(f, ref).max() <= TOL_MIXED
     assert all(i["status"] == 0 and i["rel_resid"] <= 1e-11 for i in info)
+
+
+def test_injected_device_wait_times_out_and_context_survives(ctx):
+    """LYAP_INJECT_DEVICE_WAIT: the tensor-core GEMM issues no copy, its
+    bounded mbarrier wait runs out, the kernel releases TMEM and returns, and
+    the call reports LYAP_EDEVICE_TIMEOUT. The next normal call on the same
+    seed and context still matches the oracle."""
+    A0, U, V, G, E, vs = random_problem(41, 37, 3, 4)
+    seed = ly.Seed(ctx, A0, U, V, G, E)
+    with pytest.raises(ly.LyapError) as e:
+        seed.trace_EX(vs[:3], precision=ly.BF16_IR, inject=ly.INJECT_DEVICE_WAIT, maxit=20, max_refine=2)
+    assert e.value.code == ly.EDEVICE_TIMEOUT
+    f = seed.trace_EX(vs[:3], precision=ly.BF16_IR)
+    ref = np.array([oracle.trace_EX(A0, U, V, G, E, v) for v in vs[:3]])
+    assert rel_err(f, ref).max() <= TOL_MIXED
+    with pytest.raises(ly.LyapError) as e:
+        seed.grad(vs[:2], precision=ly.BF16_IR, inject=ly.INJECT_DEVICE_WAIT, maxit=20, max_refine=2)
+    assert e.value.code == ly.EDEVICE_TIMEOUT
+    f, g = seed.grad(vs[:2], precision=ly.BF16_IR)
+    for i, v in enumerate(vs[:2]):
+        fo, go = oracle.gradient(A0, U, V, G, E, v)
+        assert rel_err(f[i], fo) <= TOL_MIXED
+        assert np.abs(g[i] - go).max() <= 1e-6 * np.abs(go).max()
+
+
+def test_injected_maxit_in_the_mixed_path(ctx):
+    A0, U, V, G, E, vs = random_problem(42, 37, 3, 4)
+    seed = ly.Seed(ctx, A0, U, V, G, E)
+    f, info = seed.trace_EX(vs[:3], return_info=True, precision=ly.BF16_IR, inject=ly.INJECT_FORCE_MAXIT,
+                            s=0, pbar=0, max_refine=2)
+    assert all(i["status"] == ly.ENOCONV for i in info)

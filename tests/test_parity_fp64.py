@@ -149,8 +149,11 @@ def test_injected_allocation_failure_and_maxit(ctx):
     with pytest.raises(ly.LyapError) as e:
         seed.trace_EX(vs[:2], inject=ly.INJECT_ALLOC_FAIL)
     assert e.value.code == ly.ENOMEM
-    f, info = seed.trace_EX(vs[:2], return_info=True, inject=ly.INJECT_FORCE_MAXIT, s=0)
-    assert all(i["status"] in (ly.OK, ly.ENOCONV) for i in info)
+    f, info = seed.trace_EX(vs[:2], return_info=True, inject=ly.INJECT_FORCE_MAXIT, s=0, pbar=0)
+    # one block-Jacobi preconditioned iteration cannot reach the 1e-12
+    # residual on this 24-unknown system (a TSVD of full rank would be exact)
+    assert all(i["status"] == ly.ENOCONV and i["iters"] == 1 for i in info)
+    assert all(i["rel_resid"] > 1e-12 for i in info)
     # the seed stays usable
     f = seed.trace_EX(vs[:2])
     assert rel_err(f, oracle_sweep(A0, U, V, G, E, vs[:2])).max() <= TOL_FP64

@@ -21,4 +21,14 @@ from .generators import (  # noqa: F401
     workload_differentiation,
     workload_multi_agent,
     order_nearest_neighbour,
+    chain_stiffness,
+    rayleigh_chain,
+    workload_rayleigh,
+    ex3_laplacian,
+    agent_network,
+    ex3_problem,
+    ex3_grid,
+    stable_mask,
+    workload_ex3,
+    EX3_POSITIONS,
 )

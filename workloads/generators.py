@@ -382,3 +382,211 @@ def workload_multi_agent(count: int = 512):
     p = multi_agent(rng)
     ws = rng.uniform(0.1, 5.0, (count, 8))
     return p, ws
+
+
+def chain_stiffness(springs) -> np.ndarray:
+    """Tridiagonal stiffness of a fixed-fixed chain: spring i joins masses
+    i-1 and i (walls at both ends), m + 1 springs for m masses."""
+    springs = np.asarray(springs, dtype=np.float64)
+    m = springs.size - 1
+    K = np.zeros((m, m))
+    for i in range(m):
+        K[i, i] = springs[i] + springs[i + 1]
+        if i + 1 < m:
+            K[i, i + 1] = K[i + 1, i] = -springs[i + 1]
+    return K
+
+
+def rayleigh_chain(springs, masses, alpha: float, beta: float, dampers) -> Problem:
+    """Damped chain with internal Rayleigh damping C_int = alpha M + beta K
+    (eq. (Cprop)) in the physical linearisation y = [x; xdot] (eq. (MatrixAA)).
+
+    Paper convention (§3.1): A_p(v) = A0p - B_l D(v) B_r^T with
+        A0p = [[0, I], [-M^-1 K, -alpha I - beta M^-1 K]],
+        B_l = [0; M^-1 B],  B_r = [0; B],
+    and Q = diag(K^-1, M^-1) (the energy-norm measure). The API's family
+    takes A0 = A0p^T, U = B_r, V = B_l and G with G G^T = Q
+    (G = blockdiag(chol(K^-1), chol(M^-1))); E = I gives the total average
+    energy. ``dampers`` are 1-based mass indices of grounded dampers.
+    """
+    K = chain_stiffness(springs)
+    m = K.shape[0]
+    masses = np.asarray(masses, dtype=np.float64)
+    if masses.size != m:
+        raise ValueError("one mass per chain node")
+    Minv = np.diag(1.0 / masses)
+    A0p = np.zeros((2 * m, 2 * m))
+    A0p[:m, m:] = np.eye(m)
+    A0p[m:, :m] = -Minv @ K
+    A0p[m:, m:] = -alpha * np.eye(m) - beta * Minv @ K
+    k = len(dampers)
+    B = np.zeros((m, k))
+    for c, d in enumerate(dampers):
+        if not 1 <= d <= m:
+            raise ValueError("damper position out of range")
+        B[d - 1, c] = 1.0
+    Br = np.zeros((2 * m, k))
+    Br[m:, :] = B
+    Bl = np.zeros((2 * m, k))
+    Bl[m:, :] = Minv @ B
+    G = np.zeros((2 * m, 2 * m))
+    G[:m, :m] = np.linalg.cholesky(np.linalg.inv(K))
+    G[m:, m:] = np.diag(1.0 / np.sqrt(masses))
+    return Problem(
+        name=f"rayleigh{m}",
+        A0=A0p.T.copy(),
+        U=Br,
+        V=Bl,
+        G=G,
+        E=np.eye(2 * m),
+        meta=dict(K=K, masses=masses, alpha=alpha, beta=beta, dampers=list(dampers)),
+    )
+
+
+def workload_rayleigh(masses: int = 60, dense: bool = False, count: int = 64):
+    """Rayleigh-damped chain: `masses` masses U[1, 3], springs U[0.5, 2],
+    alpha = 0.05, beta = 0.01, three dampers at random masses; v
+    log-uniform on [0.1, 10]^3, nearest-neighbour ordered."""
+    rng = np.random.default_rng(np.random.SeedSequence([0, 6]))
+    springs = rng.uniform(0.5, 2.0, masses + 1)
+    mvals = rng.uniform(1.0, 3.0, masses)
+    dampers = sorted((rng.choice(masses, 3, replace=False) + 1).tolist())
+    p = rayleigh_chain(springs, mvals, 0.05, 0.01, dampers)
+    vs = order_nearest_neighbour(_log_uniform(rng, 0.1, 10.0, (count, 3)))
+    if dense:
+        p = generic_dense(p, rng)
+    return p, vs
+
+
+def _matlab_range(a: float, b: float) -> list:
+    """The integers a:b of a colon expression with unit step (a, b may be
+    fractional; an empty list when b < a)."""
+    lo = int(np.ceil(a - 1e-12))
+    return list(range(lo, int(np.floor(b + 1e-12)) + 1))
+
+
+def ex3_laplacian(m: int) -> np.ndarray:
+    """Laplacian of Ex. 3's communication graph (Algorithm 2), 1-based.
+
+    The graph starts as a wheel: the ring 1 - 2 - ... - (m-1) - 1 and a hub m
+    joined to every ring node. Ring edges (r, r+1) for r in the list r are
+    removed (r = m - 1 names the closing edge (1, m - 1)), and the spokes of
+    the nodes in the list h are removed; the Laplacian is the degree matrix
+    minus the adjacency.
+    """
+    r = (_matlab_range(m / 20 + m / 50, m / 10) + _matlab_range(m / 4 + m / 20, m / 4 + m / 10)
+         + _matlab_range(m / 2 + m / 20 + 2, m / 2 + m / 20 + m / 50)
+         + _matlab_range(m / 2 + m / 10 + 2, m / 2 + m / 10 + m / 20) + _matlab_range(m - m / 10, m - m / 20))
+    h = (_matlab_range(1, m / 20) + _matlab_range(m / 10 + m / 40, m / 10 + m / 20)
+         + _matlab_range(m / 2, m / 2 + m / 20) + [m - 1])
+    adj = np.zeros((m + 1, m + 1))  # 1-based; row/column 0 unused
+    for i in range(1, m - 1):
+        adj[i, i + 1] = 1.0
+        adj[i, m] = 1.0
+    adj[1, m - 1] = 1.0
+    adj[m - 1, m] = 1.0
+    for ri in r:
+        if ri == m - 1:
+            adj[1, m - 1] = 0.0
+        else:
+            adj[ri, ri + 1] = 0.0
+    for hi in h:
+        adj[hi, m] = 0.0
+    adj = adj[1:, 1:]
+    adj = adj + adj.T
+    return np.diag(adj.sum(axis=1)) - adj
+
+
+def agent_network(L: np.ndarray):
+    """Ex. 2 / Ex. 3 agents on the graph with Laplacian L (§3.2): 2 x 2 agent
+    state A_i = [[-10, 5], [5, -8]], gain K_i = diag(0.3, 0.2),
+    B_i = C_i^T = [[1, 1], [-1, 1]]; blocks A_ij = delta_ij A_i -
+    l_ij B_i K_i C_j. Returns (A, C) with C = blockdiag(C_i)."""
+    Ai = np.array([[-10.0, 5.0], [5.0, -8.0]])
+    Bi = np.array([[1.0, 1.0], [-1.0, 1.0]])
+    Ki = np.diag([0.3, 0.2])
+    Ci = Bi.T
+    m = L.shape[0]
+    A = np.kron(np.eye(m), Ai) - np.kron(L, Bi @ Ki @ Ci)
+    C = np.kron(np.eye(m), Ci)
+    return A, C
+
+
+def ex3_problem(m: int = 200, k_index: int = 41) -> Problem:
+    """Ex. 3: m agents on the Algorithm 2 graph, a rank-4 change of the
+    off-diagonal entries of two consecutive agents' diagonal blocks.
+
+    For the odd 1-based state index k (1 <= k <= 2m - 3), B_l and B_r are
+    zero except rows k..k+3: B_l there is the permutation [[0,1,0,0],
+    [1,0,0,0],[0,0,0,1],[0,0,1,0]] and B_r the identity. The paper's family
+    A_p(v) = A - B_l diag(v1, v1, v2, v2) B_r^T with Q = C^T C and E = I;
+    the API's parameter vector is (v1, v1, v2, v2), A0 = A^T = A,
+    U = B_r, V = B_l, G = C^T.
+    """
+    if k_index % 2 != 1 or not 1 <= k_index <= 2 * m - 3:
+        raise ValueError("k must be odd and in [1, 2m - 3]")
+    A, C = agent_network(ex3_laplacian(m))
+    n = 2 * m
+    Bl = np.zeros((n, 4))
+    Br = np.zeros((n, 4))
+    Bl[k_index - 1:k_index + 3, :] = np.array([[0, 1, 0, 0], [1, 0, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], float)
+    Br[k_index - 1:k_index + 3, :] = np.eye(4)
+    return Problem(name=f"ex3_{m}_{k_index}", A0=A.T.copy(), U=Br, V=Bl, G=C.T.copy(), E=np.eye(n),
+                   meta=dict(m=m, k_index=k_index))
+
+
+def ex3_grid() -> np.ndarray:
+    """Ex. 3's parameter grid: v1, v2 in -4.9:0.5:14.6 (40 values each), in
+    serpentine order (consecutive pairs differ in one coordinate by 0.5);
+    rows are the API's vectors (v1, v1, v2, v2)."""
+    g = -4.9 + 0.5 * np.arange(40)
+    rows = []
+    for a, v1 in enumerate(g):
+        for v2 in (g if a % 2 == 0 else g[::-1]):
+            rows.append((v1, v1, v2, v2))
+    return np.array(rows)
+
+
+def stable_mask(p: Problem, vs) -> np.ndarray:
+    """True where A(v) = A0 - U diag(v) V^T is Hurwitz (rightmost eigenvalue
+    in the open left half plane; unstable members are discarded, §4).
+
+    For a symmetric, negative definite A0 and a symmetric change
+    U diag(v) V^T = S M(v) S^T supported on a few rows S (Ex. 3), -A(v) is
+    positive definite iff I + W^(1/2) M(v) W^(1/2) is, with
+    W = S^T (-A0)^-1 S: a congruence (see the test), so each v costs a
+    small eigenproblem. Otherwise the eigenvalues of A(v) are computed.
+    """
+    vs = np.asarray(vs, dtype=np.float64)
+    A0, U, V = p.A0, p.U, p.V
+    rows = np.nonzero(np.any(U != 0, axis=1) | np.any(V != 0, axis=1))[0]
+    sym = np.allclose(A0, A0.T) and np.linalg.eigvalsh(A0).max() < 0
+    if sym:
+        M0 = [(U[rows] * v[None, :]) @ V[rows].T for v in vs]
+        sym = all(np.allclose(M, M.T) for M in M0)
+    out = np.zeros(len(vs), dtype=bool)
+    if sym:
+        S = np.zeros((A0.shape[0], rows.size))
+        S[rows, np.arange(rows.size)] = 1.0
+        W = S.T @ np.linalg.solve(-A0, S)
+        wv, wq = np.linalg.eigh(W)
+        Wh = (wq * np.sqrt(wv)) @ wq.T
+        for i, M in enumerate(M0):
+            # A(v) = A0 - S M S^T, so -A(v) = -A0 + S M S^T
+            out[i] = np.linalg.eigvalsh(np.eye(rows.size) + Wh @ M @ Wh).min() > 0
+        return out
+    for i, v in enumerate(vs):
+        out[i] = np.linalg.eigvals(A0 - (U * v[None, :]) @ V.T).real.max() < 0
+    return out
+
+
+EX3_POSITIONS = (41, 121, 201, 281)  # the positions k of Ex. 3's table
+
+
+def workload_ex3(k_index: int = 41, m: int = 200):
+    """Ex. 3 sweep for one perturbation position: the stable members of the
+    40 x 40 grid, in serpentine order. Over the four positions of Ex. 3's
+    table (EX3_POSITIONS) 356 of the 6,400 grid points are unstable."""
+    p = ex3_problem(m, k_index)
+    vs = ex3_grid()
+    return p, vs[stable_mask(p, vs)]
