@@ -267,6 +267,43 @@ int lyap_serve_cancel(lyap_server* srv, uint64_t ticket);
 /* Finish running batches, stop the workers and free the server. */
 void lyap_serve_destroy(lyap_server* srv);
 
+/* --------------------------------------------------- projection framework
+ * The large-scale method of §2.2 (eqs. (EK_def), (param_projected), the
+ * backward error proposition, Algorithm 1). One extended Krylov space
+ * EK_m(A0^T, P), P = [X0 U, V] (eq. (rhs_newexpression) in this header's
+ * convention), is built from the LU factors of A0 and serves every v; the
+ * projected equation of each m is solved by the small-scale path above for
+ * all remaining v in one batch, and v is accepted once its backward error
+ * Delta_{m,v} <= eps.
+ *
+ * lyap_proj_create: A0 n x n, U, V n x k, E n x n symmetric or NULL (= I),
+ *   column-major FP64 in mem_kind memory (copied). XBr (n x k) = X0 U, the
+ *   seed solution times U, with fX0 = trace(E X0), as Assumption 2 of the
+ *   paper supposes them available; when XBr is NULL both come from a
+ *   one-off FP64 eigen-factorisation of A0 with G (n x g), which is then
+ *   released. 1 <= k <= 8, 2k <= n. Errors: LYAP_EINVAL, LYAP_EUNSTABLE_SEED
+ *   (A0 singular or, without XBr, not stable), LYAP_ENOMEM, LYAP_ESOLVER,
+ *   LYAP_ECUDA.
+ * lyap_proj_trace_EX: f(v) for nv parameter vectors (nv x k row-major, in
+ *   mem_kind memory; outputs in the same kind). Algorithm 1 with the
+ *   remaining vectors taken as one batch per m (every v whose Delta meets
+ *   eps leaves, the others wait for the next block) while m < m_max; the
+ *   space is kept and grown across calls. delta_out (may be NULL, host)
+ *   receives Delta_{m,v}, blocks_out (may be NULL, host) the m used; info
+ *   (may be NULL, host) reports LYAP_ENOCONV for a v whose Delta never met
+ *   eps (its trace is then the last one computed). opts->precision selects
+ *   the path of the projected solves. The call synchronises.
+ * lyap_proj_dims: blocks built so far and the basis dimension.
+ */
+typedef struct lyap_proj lyap_proj;
+int lyap_proj_create(lyap_ctx* ctx, int n, int k, int g, const double* A0, const double* U, const double* V,
+                     const double* G, const double* E, const double* XBr, double fX0, int mem_kind,
+                     const lyap_opts* opts, lyap_proj** out);
+int lyap_proj_trace_EX(lyap_proj* proj, int nv, const double* v, int mem_kind, const lyap_opts* opts, double eps,
+                       int m_max, double* trace_out, double* delta_out, int* blocks_out, lyap_result_info* info);
+int lyap_proj_dims(const lyap_proj* proj, int* blocks, int* dim);
+int lyap_proj_free(lyap_proj* proj);
+
 /* ------------------------------------------------- allocation-free check
  * The paper has no counterpart to this call. It is for callers that cannot
  * allocate device memory while they run: hosts that reserve all of their

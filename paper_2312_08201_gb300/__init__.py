@@ -155,6 +155,18 @@ _SIGS = {
     "lyap_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "lyap_serve_destroy": (None, [_P]),
     "lyap_check_solution_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "lyap_proj_create": (
+        ctypes.c_int,
+        [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int,
+         ctypes.POINTER(LyapOpts), ctypes.POINTER(_P)],
+    ),
+    "lyap_proj_trace_EX": (
+        ctypes.c_int,
+        [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(LyapOpts), ctypes.c_double, ctypes.c_int, _P, _P, _P,
+         ctypes.POINTER(ResultInfo)],
+    ),
+    "lyap_proj_dims": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lyap_proj_free": (ctypes.c_int, [_P]),
     "lyap_test_apply": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, _P]),
     "lyap_test_tc_gemm": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
     "lyap_prof_enable": (ctypes.c_int, [ctypes.c_int]),
@@ -356,6 +368,61 @@ class Seed:
         if mem == MEM_HOST:
             return w[..., 0] + 1j * w[..., 1], _infos(info, nv)
         return w, _infos(info, nv)
+
+
+class Projection:
+    """The projection framework of §2.2 (lyap_proj_*): one extended Krylov
+    space EK_m(A0^T, [X0 U, V]) for every v, grown on demand; each v is
+    accepted once its backward error meets eps (Algorithm 1)."""
+
+    def __init__(self, ctx: Context, A0, U, V, G=None, E=None, XBr=None, fX0=0.0, **opts):
+        lib = load()
+        self.ctx = ctx
+        n, k = int(A0.shape[0]), int(U.shape[1])
+        g = int(G.shape[1]) if G is not None else 0
+        o = default_opts(**opts)
+        arrs = [_host_f64(a) for a in (A0, U, V)]
+        ga = _host_f64(G) if G is not None else None
+        ea = _host_f64(E) if E is not None else None
+        xa = _host_f64(XBr) if XBr is not None else None
+        ptr = (lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None)
+        h = _P()
+        _check(lib.lyap_proj_create(ctx.h, n, k, g, *[ptr(a) for a in arrs], ptr(ga), ptr(ea), ptr(xa), float(fX0),
+                                    MEM_HOST, ctypes.byref(o), ctypes.byref(h)), "lyap_proj_create")
+        self.h = h
+        self.n, self.k = n, k
+
+    def trace_EX(self, v, eps=1e-10, m_max=200, return_info=False, **opts):
+        """f(v) per row of v; with return_info also (delta, blocks, infos)."""
+        lib = load()
+        o = default_opts(**opts)
+        va = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1, self.k))
+        nv = va.shape[0]
+        f = np.empty(nv)
+        dl = np.empty(nv)
+        mb = np.empty(nv, dtype=np.int32)
+        info = (ResultInfo * max(nv, 1))()
+        _check(lib.lyap_proj_trace_EX(self.h, nv, va.ctypes.data_as(ctypes.c_void_p), MEM_HOST, ctypes.byref(o),
+                                      float(eps), int(m_max), f.ctypes.data_as(ctypes.c_void_p),
+                                      dl.ctypes.data_as(ctypes.c_void_p), mb.ctypes.data_as(ctypes.c_void_p), info),
+               "lyap_proj_trace_EX")
+        return (f, dl, mb, _infos(info, nv)) if return_info else f
+
+    def dims(self):
+        b, d = ctypes.c_int(), ctypes.c_int()
+        _check(load().lyap_proj_dims(self.h, ctypes.byref(b), ctypes.byref(d)), "lyap_proj_dims")
+        return b.value, d.value
+
+    def free(self):
+        if getattr(self, "h", None):
+            load().lyap_proj_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 class Server:

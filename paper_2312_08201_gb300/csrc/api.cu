@@ -228,11 +228,16 @@ extern "C" int lyap_seed_factor(lyap_ctx* ctx, int n, int k, int g, const double
   sd->k = k;
   sd->g = g;
   LY_TRY(lyap_seed_build(ctx, sd.get(), pA, pU, pV, pG, pE, st));
-  LY_TRY(lyap_mixed_prepare(sd.get(), st));
-  if (o.pbar > 0) LY_TRY(lyap_tsvd_prepare(sd.get(), o.pbar, st));
-  sd->work = new SeedWork();
+  LY_TRY(lyap_seed_finish(sd.get(), o.pbar, true, st));
   if (cond_Q_out) *cond_Q_out = sd->cond_Q;
   *out = sd.release();
+  return LYAP_OK;
+}
+
+int lyap_seed_finish(lyap_seed* sd, int pbar, bool mixed, cudaStream_t st) {
+  if (mixed) LY_TRY(lyap_mixed_prepare(sd, st));
+  if (pbar > 0) LY_TRY(lyap_tsvd_prepare(sd, pbar, st));
+  sd->work = new SeedWork();
   return LYAP_OK;
 }
 

@@ -159,6 +159,10 @@ int lyap_validate_opts(const lyap_opts* in, lyap_opts* out);
 int lyap_check_v(int nv, int k, const double* v_host);
 
 // Seed factor (seed.cu)
+// Operands of the mixed path (mixed = true), the truncated SVD of the
+// preconditioner (pbar > 0) and the solver's workspace cache, after
+// lyap_seed_build.
+int lyap_seed_finish(lyap_seed* seed, int pbar, bool mixed, cudaStream_t st);
 // P1 (device n x k, may be null): the first block X0 B_r of the right-hand
 // side factor of eq. (rhs_newexpression), given instead of G; the seed's
 // traces then count only X(v) - X0 (f0 = 0).

@@ -342,7 +342,10 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
     sd->max_re = hs[0];
     sd->min_sum = hs[1];
     sd->real_path = hs[3] <= 1e-14 * hs[2] ? 1 : 0;
-    if (!(hs[0] < 0.0) || !(hs[1] > 1e-12 * hs[2])) {
+    // A seed built from a given right-hand side factor (a projected
+    // equation of §2.2) needs only the uniqueness condition
+    // lambda_i + lambda_j != 0, not the stability of its own A0.
+    if ((!P1 && !(hs[0] < 0.0)) || !(hs[1] > 1e-12 * hs[2])) {
       lyap_set_last_error("seed A0 is not stable (max Re lambda = " + std::to_string(hs[0]) +
                           ", min |lambda_i + lambda_j| = " + std::to_string(hs[1]) + ")");
       return LYAP_EUNSTABLE_SEED;
