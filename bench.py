@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--residual", choices=["ff", "fp64", "tc"], default="tc",
                     help="arithmetic of the mixed path's refinement residual")
     ap.add_argument("--nv", type=int, default=0, help="parameter vectors of the sweep (0: all 1000)")
+    ap.add_argument("--s", type=int, default=-1, help="recycled vectors (-1: library default)")
     ap.add_argument("--profile-sweep", action="store_true",
                     help="after the measurements, run one more sweep between cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
@@ -331,6 +332,60 @@ def extra_grad(ctx, dev, stream, steps=2):
                 max_rel_err_grad_vs_fp64_path=gerr, seed_factor_s=tf)
 
 
+def extra_ex3(ctx, dev, stream):
+    """Ex. 3 of the paper: the 200-agent network of Algorithm 2, a rank-4
+    change with B_l != B_r at the four positions of the example's table,
+    the stable members of the 40 x 40 grid (6,044 systems in all, negative
+    parameters included). Small-scale path (mixed precision, one batch per
+    position) and the projection framework (backward error 1e-10, the
+    paper's setting), each timed over the whole sweep; both against the FP64
+    small-scale path on the same v."""
+    import numpy as np
+    import torch
+
+    import paper_2312_08201_gb300 as ly
+    from workloads import EX3_POSITIONS, workload_ex3
+
+    probs = [workload_ex3(kp) for kp in EX3_POSITIONS]
+    seeds = [ly.Seed(ctx, p.A0, p.U, p.V, p.G, p.E) for p, _ in probs]
+    vdev = [torch.tensor(vs, dtype=torch.float64, device=dev) for _, vs in probs]
+    total = sum(len(vs) for _, vs in probs)
+    ref = [sd.trace_EX(v, precision=ly.FP64).cpu().numpy() for sd, v in zip(seeds, vdev)]
+
+    def small():
+        return [sd.trace_EX(v, precision=ly.BF16_IR) for sd, v in zip(seeds, vdev)]
+
+    ms, out = _event_time(small, 2, 1, stream)
+    err_small = max(float(np.max(np.abs(o.cpu().numpy() - r) / np.abs(r))) for o, r in zip(out, ref))
+    for sd in seeds:
+        sd.free()
+    # projection framework: the space is built once per position (offline,
+    # reported separately) and then serves the sweep
+    t0 = time.perf_counter()
+    projs = [ly.Projection(ctx, p.A0, p.U, p.V, p.G, p.E) for p, _ in probs]
+    t_off = time.perf_counter() - t0
+    for pj, (p, vs) in zip(projs, probs):
+        pj.trace_EX(vs[:8], eps=1e-10, m_max=200)  # warm-up: grows the spaces
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outp = [pj.trace_EX(vs, eps=1e-10, m_max=200, return_info=True) for pj, (p, vs) in zip(projs, probs)]
+    t_proj = time.perf_counter() - t0
+    err_proj = max(float(np.max(np.abs(o[0] - r) / np.abs(r))) for o, r in zip(outp, ref))
+    dims = [pj.dims()[1] for pj in projs]
+    blocks = np.concatenate([o[2] for o in outp])
+    for pj in projs:
+        pj.free()
+    return dict(workload="Ex. 3: 200 agents (Algorithm 2 graph), n=400, k=4 (B_l != B_r), positions "
+                         f"{list(EX3_POSITIONS)}, {total} stable grid points",
+                unit="evals/s",
+                small_scale=dict(value=total * len(ms) / (sum(ms) / 1e3), ms_per_sweep=float(np.mean(ms)),
+                                 precision="bf16_ir", max_rel_err_vs_fp64_path=err_small),
+                projection=dict(value=total / t_proj, s_per_sweep=t_proj, eps=1e-10, offline_s=t_off,
+                                basis_dims=dims, blocks_mean=float(blocks.mean()), blocks_max=int(blocks.max()),
+                                max_rel_err_vs_fp64_path=err_proj, precision="fp64",
+                                timing="wall clock of the host-driven Algorithm 1 (synchronising)"))
+
+
 def extra_multi_agent(ctx, dev, stream, steps=2):
     """Multi-agent workload: 256 agents (n = 1024), 8 tunable edges, 512
     weight vectors in one lockstep batch, mixed path; 8 of them also on the
@@ -481,6 +536,8 @@ def main():
     opts = dict(precision=ly.BF16_IR if precision == "bf16_ir" else ly.FP64, batch=args.batch)
     if args.pbar >= 0:
         opts["pbar"] = args.pbar
+    if args.s >= 0:
+        opts["s"] = args.s
     if precision == "bf16_ir":
         opts["residual"] = {"ff": ly.RESID_FF, "fp64": ly.RESID_FP64, "tc": ly.RESID_TC}[args.residual]
 
@@ -614,7 +671,8 @@ def main():
         # the figures of the other workloads, after the timed region
         for key, fn in (("fp64_path", lambda: extra_fp64_path(seed, v_dev, f64, stream)),
                         ("grad", lambda: extra_grad(ctx, dev, stream)),
-                        ("multi_agent", lambda: extra_multi_agent(ctx, dev, stream))):
+                        ("multi_agent", lambda: extra_multi_agent(ctx, dev, stream)),
+                        ("ex3", lambda: extra_ex3(ctx, dev, stream))):
             try:
                 line[key] = fn()
             except Exception as exc:  # report, never lose the headline line

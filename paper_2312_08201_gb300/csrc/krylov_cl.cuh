@@ -1,0 +1,211 @@
+// CGS2 orthogonalisation of the Arnoldi step with the basis staged in
+// shared memory across a thread-block cluster (the GCRO-DR step of paper
+// §2.1, same arithmetic as kry::k_ortho).
+//
+// One cluster of C CTAs serves one system; CTA r owns the element slice
+// [r L, min((r+1) L, N)) of every vector. Its thread 0 issues one bulk copy
+// (cp.async.bulk, completion counted on an mbarrier) per basis vector and
+// one for w, so the whole slice of the basis is read from memory once per
+// step; both Gram-Schmidt passes, the norm and the scaling then run from
+// shared memory. The partial inner products of the CTAs meet through
+// distributed shared memory, summed in rank order by every CTA, so all CTAs
+// apply identical coefficients and the result does not depend on timing.
+// CTA 0 writes the new column of H (and Bk) and runs the Givens update.
+//
+// Every wait is bounded; on expiry the CTA sets *err, still takes part in
+// every cluster barrier, waits (bounded) for its copies in flight and
+// returns, so no CTA of the cluster is left waiting.
+#pragma once
+#include <cooperative_groups.h>
+
+#include "krylov.cuh"
+#include "tcgen05_util.cuh"
+
+namespace kry {
+
+constexpr int OCT = 256;          // threads per CTA of k_ortho_cl
+constexpr int OCL_MAXNB = 64;     // basis vectors (s_cur + j + 1 <= m + 1 <= 61)
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Dynamic shared memory of k_ortho_cl: the mbarrier, three sets of partial
+// sums and two coefficient vectors, then (nb + 1) slices of L elements.
+template <typename T2>
+__host__ __device__ constexpr size_t ortho_cl_header() {
+  return ((16 + 3 * 2 * OCL_MAXNB * sizeof(typename RealOf<T2>::T) + 2 * OCL_MAXNB * sizeof(T2)) + 127) / 128 * 128;
+}
+template <typename T2>
+__host__ __device__ constexpr size_t ortho_cl_smem(int nb, int L) {
+  return ortho_cl_header<T2>() + (size_t)(nb + 1) * L * sizeof(T2);
+}
+
+template <typename T2>
+__global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, int s_cur,
+                                                 const int* __restrict__ list, const int* __restrict__ count,
+                                                 T2* __restrict__ V, const T2* __restrict__ C, size_t c_ss,
+                                                 double2* __restrict__ H, double2* __restrict__ Bk, int smax,
+                                                 LsqArgs Ls, int* __restrict__ err) {
+  using R = typename RealOf<T2>::T;
+  namespace cg = cooperative_groups;
+  constexpr int NW = OCT / 32;
+  extern __shared__ __align__(128) unsigned char osm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(osm);             // [0, 8)
+  R* part = reinterpret_cast<R*>(osm + 16);                      // 3 x 2 x OCL_MAXNB partial sums
+  T2* coef = reinterpret_cast<T2*>(osm + 16 + 3 * 2 * OCL_MAXNB * sizeof(R));  // 2 x OCL_MAXNB
+  T2* data = reinterpret_cast<T2*>(osm + ortho_cl_header<T2>());  // (nb + 1) slices of L elements
+  __shared__ double2 hcol[64];
+  __shared__ double cs_s[64];
+  __shared__ double2 sn_s[64];
+  __shared__ R red[NW];
+  __shared__ int failed;
+
+  cg::cluster_group cl = cg::this_cluster();
+  const int ncta = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int slot = blockIdx.x / ncta;
+  if (slot >= *count) return;  // uniform over the cluster
+  const int b = list[slot];
+  const int nb = s_cur + j + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int e0 = rank * L;
+  const int len = max(0, min(L, N - e0));
+  T2* Vb = V + (size_t)b * (m + 1) * N;
+  T2* w = Vb + (size_t)(j + 1) * N;
+  const T2* Cb = C + (size_t)b * c_ss;
+  auto gbasis = [&](int q) -> const T2* { return q < s_cur ? Cb + (size_t)q * N : Vb + (size_t)(q - s_cur) * N; };
+  T2* sw = data + (size_t)nb * L;
+  const uint32_t mb = tcu::sm_addr(bar);
+
+  if (tid == 0) {
+    failed = 0;
+    tcu::mbar_init(mb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0 && len > 0) {
+    const uint32_t bytes = (uint32_t)(len * sizeof(T2));
+    tcu::mbar_expect_tx(mb, bytes * (uint32_t)(nb + 1));
+    for (int q = 0; q < nb; ++q) bulk_g2s(tcu::sm_addr(data + (size_t)q * L), gbasis(q) + e0, bytes, mb);
+    bulk_g2s(tcu::sm_addr(sw), w + e0, bytes, mb);
+  }
+  if (len > 0 && !tcu::mbar_wait(mb, 0)) {
+    if (lane == 0) failed = 1;
+  }
+  __syncthreads();
+  const bool ok = failed == 0;
+  if (!ok && tid == 0) atomicExch(err, 21);
+
+  // partial inner products conj(basis_q) . x over this CTA's slice, one warp per vector
+  auto partial_dots = [&](const T2* x, R* out) {
+    for (int q = warp; q < nb; q += NW) {
+      R ax = R(0), ay = R(0);
+      if (ok) {
+        const T2* vq = data + (size_t)q * L;
+        for (int e = lane; e < len; e += 32) {
+          const T2 a = vq[e], c = x[e];
+          ax += a.x * c.x + a.y * c.y;
+          ay += a.x * c.y - a.y * c.x;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+      }
+      if (lane == 0) {
+        out[2 * q] = ax;
+        out[2 * q + 1] = ay;
+      }
+    }
+  };
+  // coefficients: the cluster's partial sums added in rank order
+  auto gather = [&](R* in, T2* cf) {
+    cl.sync();
+    if (tid < 2 * nb) {
+      R s = R(0);
+      for (int r = 0; r < ncta; ++r) s += cl.map_shared_rank(in, r)[tid];
+      reinterpret_cast<R*>(cf)[tid] = s;
+    }
+    __syncthreads();
+  };
+  // x -= sum_q basis_q coef_q over the slice; returns this thread's sum of |x|^2
+  auto update = [&](const T2* cf) -> R {
+    R nr = R(0);
+    if (!ok) return nr;
+    for (int e = tid; e < len; e += OCT) {
+      T2 we = sw[e];
+      for (int q = 0; q < nb; ++q) we = csub(we, cmul(data[(size_t)q * L + e], cf[q]));
+      sw[e] = we;
+      nr += cabs2(we);
+    }
+    return nr;
+  };
+
+  // pass 1
+  partial_dots(sw, part);
+  gather(part, coef);
+  update(coef);
+  __syncthreads();
+  // pass 2
+  partial_dots(sw, part + 2 * OCL_MAXNB);
+  gather(part + 2 * OCL_MAXNB, coef + OCL_MAXNB);
+  R nr = update(coef + OCL_MAXNB);
+  // norm of the orthogonalised w
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(0xffffffffu, nr, o);
+  if (lane == 0) red[warp] = nr;
+  __syncthreads();
+  R* pn = part + 4 * OCL_MAXNB;
+  if (tid == 0) {
+    R t = R(0);
+    for (int w2 = 0; w2 < NW; ++w2) t += red[w2];
+    pn[0] = t;
+  }
+  cl.sync();
+  R tot = R(0);
+  for (int r = 0; r < ncta; ++r) tot += cl.map_shared_rank(pn, r)[0];
+  // scale and store this CTA's slice of the new basis vector
+  const R rn = sqrt(tot);
+  const R inv = rn > R(0) ? R(1) / rn : R(0);
+  if (ok)
+    for (int e = tid; e < len; e += OCT) w[e0 + e] = cscale(sw[e], inv);
+  if (rank == 0 && ok) {
+    double2* H0c = Ls.H0 + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
+    double2* Bc = Bk + (size_t)b * smax * m + (size_t)j * smax;
+    if (tid < nb) {
+      const int q = tid;
+      const double2 cval = cadd(to_d2(coef[q]), to_d2(coef[OCL_MAXNB + q]));
+      if (q < s_cur) {
+        Bc[q] = cval;
+      } else {
+        H0c[q - s_cur] = cval;
+        hcol[q - s_cur] = cval;
+      }
+    }
+    if (tid >= 64 && tid < 64 + j) {  // the previous rotations
+      cs_s[tid - 64] = Ls.cs[(size_t)b * m + tid - 64];
+      sn_s[tid - 64] = Ls.sn[(size_t)b * m + tid - 64];
+    }
+    double2 gj = make_double2(0.0, 0.0);
+    double tola = 0.0;
+    int itd = 0;
+    if (tid == 0) {
+      gj = Ls.g[(size_t)b * (m + 1) + j];
+      tola = Ls.tolabs[b];
+      itd = Ls.iters_done[b];
+      const double nrm = sqrt((double)tot);
+      H0c[j + 1] = make_double2(nrm, 0.0);
+      hcol[j + 1] = make_double2(nrm, 0.0);
+    }
+    __syncthreads();
+    if (tid == 0) lsq_column(b, j, m, H, hcol, cs_s, sn_s, gj, tola, itd, Ls);
+  }
+  if (!ok && tid == 0 && len > 0) tcu::mbar_wait(mb, 0);  // no copy may land after the CTA has gone
+  cl.sync();  // every CTA's partial sums stay readable until all have read them
+}
+
+}  // namespace kry

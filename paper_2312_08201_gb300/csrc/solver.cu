@@ -21,6 +21,7 @@
 
 #include "cplx.cuh"
 #include "krylov.cuh"
+#include "krylov_cl.cuh"
 #include "solver.h"
 #include "prof.h"
 
@@ -248,6 +249,8 @@ int KrylovWS<T2>::ensure(int B_, int N_, int m_, int s_) {
   LY_TRY(ok.alloc(Bs));
   LY_TRY(hasrec.alloc(Bs));
   LY_TRY(rflag.alloc(Bs));
+  LY_TRY(kerr.alloc(1));
+  LY_CUDA(cudaMemset(kerr.p, 0, sizeof(int)));
   return LYAP_OK;
 }
 
@@ -257,7 +260,59 @@ size_t KrylovWS<T2>::bytes() const {
          Bk.bytes() + g.bytes() + sn.bytes() + coefY.bytes() + coefR.bytes() + F.bytes() + UU.bytes() +
          work.bytes() + Pu.bytes() + Qc.bytes() + Gs.bytes() + Rinv.bytes() + Racc.bytes() + Rtmp.bytes() +
          cs.bytes() + beta.bytes() + tolabs.bytes() + tmpd.bytes() + jstop.bytes() + flag.bytes() + iters.bytes() +
-         lists.bytes() + counts.bytes() + ok.bytes() + hasrec.bytes() + rflag.bytes();
+         lists.bytes() + counts.bytes() + ok.bytes() + hasrec.bytes() + rflag.bytes() + kerr.bytes();
+}
+
+// --------------------------------------------------------- orthogonalisation
+// Shared memory per CTA of the cluster variant; at most this much lets two
+// CTAs share an SM.
+constexpr size_t kOrthoSmemCap = 100 * 1024;
+
+// CGS2 of Arnoldi step j for the listed systems (at most B). The cluster
+// kernel stages each system's basis in shared memory over C CTAs, with C the
+// smallest of 1, 2, 4, 8 whose slices fit kOrthoSmemCap; when none does, or
+// vectors do not start on 16-byte boundaries (bulk copies need them), the
+// kernel that streams the basis from memory runs instead.
+template <typename T2>
+int launch_ortho(int N, int j, int m, int s_cur, const int* list, const int* count, int B, T2* V, const T2* C,
+                 size_t c_ss, double2* H, double2* Bk, int smax, const kry::LsqArgs& la, int* err, cudaStream_t st) {
+  const int nb = s_cur + j + 1;
+  constexpr int kAlign = 16 / sizeof(T2);  // elements per 16 bytes
+  int cl = 0, L = 0;
+  if (((size_t)N * sizeof(T2)) % 16 == 0 && nb <= kry::OCL_MAXNB) {
+    for (int c = 1; c <= 8; c *= 2) {
+      const int l = ((N + c - 1) / c + kAlign - 1) / kAlign * kAlign;
+      if (kry::ortho_cl_smem<T2>(nb, l) <= kOrthoSmemCap) {
+        cl = c;
+        L = l;
+        break;
+      }
+    }
+  }
+  if (cl == 0) {
+    kry::k_ortho<T2><<<B, kry::OT, 0, st>>>(N, j, m, s_cur, list, count, V, C, c_ss, H, Bk, smax, la);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    return LYAP_OK;
+  }
+  const size_t smem = kry::ortho_cl_smem<T2>(nb, L);
+  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(kry::k_ortho_cl<T2>), kOrthoSmemCap));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(B * cl, 1, 1);
+  cfg.blockDim = dim3(kry::OCT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  LY_CUDA(cudaLaunchKernelEx(&cfg, kry::k_ortho_cl<T2>, N, L, j, m, s_cur, list, count, V, C, c_ss, H, Bk, smax, la,
+                             err));
+  lyap_count_launch();
+  return LYAP_OK;
 }
 
 // ------------------------------------------------------------------ solver
@@ -418,9 +473,8 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
         // the same kernel applies the Givens least-squares update to the new column
         const kry::LsqArgs la{ws.H0.p, ws.cs.p, ws.sn.p, ws.g.p, ws.tolabs.p, ws.jstop.p, ws.flag.p, ws.iters.p,
                               maxit};
-        kry::k_ortho<T2><<<B, kry::OT, 0, st>>>(N, j, m, s_cur, Lcur, ccur, ws.V.p, ws.C.p, css, ws.H.p, ws.Bk.p,
-                                                smax, la);
-        lyap_count_launch();
+        LY_TRY(launch_ortho<T2>(N, j, m, s_cur, Lcur, ccur, B, ws.V.p, ws.C.p, css, ws.H.p, ws.Bk.p, smax, la,
+                                ws.kerr.p, st));
         prof_end(ph, st, 2.0 * 2.0 * 8.0 * nb * N, (nb + 2.0) * N * sizeof(T2), 0, ccur);
       }
       kry::k_compact<<<1, 1024, 0, st>>>(Lcur, ccur, ws.flag.p, Lnext, cnext, ws.poll_dev + j % RING);
@@ -454,7 +508,14 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
     kry::k_compact<<<1, 1024, 0, st>>>(Lstart, cstart, ws.flag.p, Lchunk, cchunk); lyap_count_launch();
     LY_CUDA(cudaGetLastError());
     LY_CUDA(cudaMemcpyAsync(&chunk_count, cchunk, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int kerr_h = 0;
+    LY_CUDA(cudaMemcpyAsync(&kerr_h, ws.kerr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     LY_CUDA(cudaStreamSynchronize(st));
+    if (kerr_h) {
+      LY_CUDA(cudaMemsetAsync(ws.kerr.p, 0, sizeof(int), st));
+      lyap_set_last_error("orthogonalisation copy wait timed out (code " + std::to_string(kerr_h) + ")");
+      return LYAP_EDEVICE_TIMEOUT;
+    }
     const int Bw = std::min(B, chunk_count + 1);
     // ---- recycle update (harmonic Ritz) ----------------------------------
     // After the chunk's last cycle only the last system is updated, and only

@@ -37,6 +37,7 @@ struct KrylovWS {
   DevBuf<double2> H, H0, Bk, g, sn, coefY, coefR, F, UU, work, Pu, Qc, Gs, Rinv, Racc, Rtmp;
   DevBuf<double> cs, beta, tolabs, tmpd;
   DevBuf<int> jstop, flag, iters, lists, counts, ok, hasrec, rflag;
+  DevBuf<int> kerr;  // set by a kernel whose bounded wait expired
   // The recycle update of a chunk's last cycle (harmonic Ritz of the last
   // system, hand-over to the Recycle) runs on a side stream, overlapping
   // the caller's next work; the next chunk on this workspace waits for it.
