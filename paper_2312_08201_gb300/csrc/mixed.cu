@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <memory>
 
 #include "cplx.cuh"
@@ -499,6 +500,325 @@ int lyap_mixed_chunk(lyap_seed* sd, int Bc, const double* vinv, const lyap_opts&
       iters[b] += ita[b];
       rsteps[b] += rsa[b];
       if (status[b] == LYAP_OK) status[b] = sta[b];
+    }
+  }
+  return LYAP_OK;
+}
+
+// ------------------------------------------- continuous-batching engine
+namespace {
+
+// new systems: vinv_c[c] = 1 / v[c] (compact), vinv[slot] = vinv_c[c], W[slot] = 0
+__global__ void k_engine_join(int nj, int k, size_t N, const int* __restrict__ slots, const double* __restrict__ v,
+                              double* __restrict__ vinv_c, double* __restrict__ vinv, double2* __restrict__ W) {
+  const int c = blockIdx.y;
+  if (c >= nj) return;
+  const int s = slots[c];
+  if (blockIdx.x == 0 && threadIdx.x < k) {
+    const double x = 1.0 / v[(size_t)c * k + threadIdx.x];
+    vinv_c[(size_t)c * k + threadIdx.x] = x;
+    vinv[(size_t)s * k + threadIdx.x] = x;
+  }
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x)
+    W[(size_t)s * N + e] = make_double2(0.0, 0.0);
+}
+
+// cinv[slot] = staged[c] (r x r per system)
+__global__ void k_engine_cinv(int nj, int rr, const int* __restrict__ slots, const float2* __restrict__ staged,
+                              float2* __restrict__ cinv) {
+  const int c = blockIdx.y;
+  if (c >= nj) return;
+  for (int e = threadIdx.x; e < rr; e += blockDim.x) cinv[(size_t)slots[c] * rr + e] = staged[(size_t)c * rr + e];
+}
+
+// R[slot] = rhs for the listed slots
+__global__ void k_engine_fill(size_t N, const int* __restrict__ slots, int ns, const double2* __restrict__ rhs,
+                              double2* __restrict__ R) {
+  const int c = blockIdx.y;
+  if (c >= ns) return;
+  const int s = slots[c];
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x)
+    R[(size_t)s * N + e] = rhs[e];
+}
+
+// out[c] = ||R[slot_c]|| for the listed slots
+__global__ void __launch_bounds__(kry::NT) k_engine_norms(int N, const int* __restrict__ slots, int ns,
+                                                          const double2* __restrict__ R, double* __restrict__ out) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  if (c >= ns) return;
+  const double2* r = R + (size_t)slots[c] * N;
+  double acc[1] = {0.0};
+  for (int e = threadIdx.x; e < N; e += kry::NT) acc[0] += cabs2(r[e]);
+  kry::block_sum<1>(acc, red);
+  if (threadIdx.x == 0) out[c] = sqrt(acc[0]);
+}
+
+// f[c] = Re <h, A[slot_c]> for the listed slots
+__global__ void __launch_bounds__(kry::NT) k_engine_dot_h(int N, const int* __restrict__ slots, int ns,
+                                                          const double2* __restrict__ A, const double2* __restrict__ h,
+                                                          double* __restrict__ out) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  if (c >= ns) return;
+  const double2* a = A + (size_t)slots[c] * N;
+  double acc[1] = {0.0};
+  for (int e = threadIdx.x; e < N; e += kry::NT) acc[0] += cmul(a[e], h[e]).x;
+  kry::block_sum<1>(acc, red);
+  if (threadIdx.x == 0) out[c] = acc[0];
+}
+
+}  // namespace
+
+struct MixedEngine {
+  int cap = 0, r = 0;
+  DevBuf<double2> W;      // cap x N: FP64 solution of every slot
+  DevBuf<double> vinv;    // cap x k
+  DevBuf<float2> cinv;    // cap x r x r: Cap(v)^{-1} of every slot
+  DevBuf<double> vstage, vinv_c, fout, rout, eout;
+  DevBuf<float2> cstage, cpart_stage;
+  DevBuf<int> slots, slots2;
+  DevBuf<double2> delta;  // cap x N: P^{-1} r of retiring slots (error estimate)
+  std::vector<int> steps, iters;  // per slot; steps < 0: free
+  KrylovWS<float2> ws;
+};
+
+int lyap_engine_create(lyap_seed* sd, int cap, const lyap_opts& o, MixedEngine** out) {
+  *out = nullptr;
+  if (!sd->mixed || cap < 1) return LYAP_EINVAL;
+  std::unique_ptr<MixedEngine> e(new MixedEngine());
+  const size_t N = (size_t)sd->n * sd->k;
+  const int k = sd->k;
+  e->cap = cap;
+  e->r = (o.pbar > 0 && sd->tsvd_r > 0) ? std::min(o.pbar, sd->tsvd_r) : 0;
+  LY_TRY(e->W.alloc((size_t)cap * N));
+  LY_TRY(e->vinv.alloc((size_t)cap * k));
+  LY_TRY(e->vstage.alloc((size_t)cap * k));
+  LY_TRY(e->vinv_c.alloc((size_t)cap * k));
+  LY_TRY(e->fout.alloc(cap));
+  LY_TRY(e->rout.alloc(cap));
+  LY_TRY(e->eout.alloc(cap));
+  LY_TRY(e->slots.alloc(cap));
+  LY_TRY(e->slots2.alloc(cap));
+  LY_TRY(e->delta.alloc((size_t)cap * N));
+  if (e->r > 0) {
+    LY_TRY(e->cinv.alloc((size_t)cap * e->r * e->r));
+    LY_TRY(e->cstage.alloc((size_t)cap * e->r * e->r));
+  }
+  e->steps.assign(cap, -1);
+  e->iters.assign(cap, 0);
+  *out = e.release();
+  return LYAP_OK;
+}
+
+void lyap_engine_free(lyap_seed* sd, MixedEngine* e) {
+  if (!e) return;
+  // a recycle hand-over still pending on the engine's side stream is
+  // resolved before that stream and its event go away
+  Recycle<float2>& rec = sd->rec32;
+  if (e->ws.side) {
+    cudaEventSynchronize(e->ws.side_done);
+    if (rec.pending && rec.ready == e->ws.side_done) {
+      rec.pending = false;
+      if (*rec.ok_host) {
+        rec.s = rec.pending_s;
+        rec.c0_valid = true;
+      }
+    }
+  }
+  delete e;
+}
+
+int lyap_engine_free_slots(const MixedEngine* e) {
+  int c = 0;
+  for (int s : e->steps) c += s < 0 ? 1 : 0;
+  return c;
+}
+
+// One refinement step of every occupied slot: systems join (fresh W = 0)
+// and retire here, so a system waits at most one step to enter the
+// lockstep set. Each step is the refinement of lyap_mixed_chunk: the
+// FP64-accurate residual, the decision per system, and one recycled FP32
+// inner solve for those that go on.
+int lyap_engine_step(lyap_seed* sd, MixedEngine& e, const lyap_opts& o, cudaStream_t st,
+                     const std::vector<EngineJoin>& joins, std::vector<EngineDone>& done) {
+  done.clear();
+  MixedState& ms = *sd->mixed;
+  const int n = sd->n, k = sd->k;
+  const int N = n * k;
+  SolveParams prm;
+  LY_TRY(lyap_params_from_opts(o, prm));
+  SolveParams pin = prm;
+  pin.tol = o.inner_tol;
+  LY_TRY(ensure_refine(sd, e.cap));
+  // ---- joins
+  const int nj = (int)joins.size();
+  if (nj > 0) {
+    std::vector<int> js(nj);
+    std::vector<double> vs((size_t)nj * k);
+    for (int c = 0; c < nj; ++c) {
+      js[c] = joins[c].slot;
+      if (e.steps[js[c]] >= 0) return LYAP_EINVAL;
+      std::memcpy(vs.data() + (size_t)c * k, joins[c].v, sizeof(double) * k);
+    }
+    LY_CUDA(cudaMemcpyAsync(e.slots.p, js.data(), sizeof(int) * nj, cudaMemcpyHostToDevice, st));
+    LY_CUDA(cudaMemcpyAsync(e.vstage.p, vs.data(), sizeof(double) * vs.size(), cudaMemcpyHostToDevice, st));
+    k_engine_join<<<dim3(gx(N), nj), 256, 0, st>>>(nj, k, (size_t)N, e.slots.p, e.vstage.p, e.vinv_c.p, e.vinv.p,
+                                                   e.W.p);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    if (e.r > 0) {
+      WoodState tmp;
+      tmp.cinv = e.cstage.p;
+      LY_TRY(wood_prepare(sd, e.r, nj, e.vinv_c.p, false, tmp, st));
+      k_engine_cinv<<<dim3(1, nj), 256, 0, st>>>(nj, e.r * e.r, e.slots.p, e.cstage.p, e.cinv.p);
+      lyap_count_launch();
+      LY_CUDA(cudaGetLastError());
+    }
+    for (int c = 0; c < nj; ++c) {
+      e.steps[js[c]] = 0;
+      e.iters[js[c]] = 0;
+    }
+  }
+  // ---- residuals: fresh systems start from r = P, the others are evaluated
+  std::vector<int> fresh, old;
+  for (int s = 0; s < e.cap; ++s) {
+    if (e.steps[s] == 0) fresh.push_back(s);
+    else if (e.steps[s] > 0) old.push_back(s);
+  }
+  if (fresh.empty() && old.empty()) return LYAP_OK;
+  std::vector<double> nrm_old(old.size());
+  if (!fresh.empty()) {
+    LY_CUDA(cudaMemcpyAsync(e.slots2.p, fresh.data(), sizeof(int) * fresh.size(), cudaMemcpyHostToDevice, st));
+    k_engine_fill<<<dim3(gx(N), (int)fresh.size()), 256, 0, st>>>((size_t)N, e.slots2.p, (int)fresh.size(),
+                                                                   sd->Ph.p, ms.R64.p);
+    lyap_count_launch();
+  }
+  if (!old.empty()) {
+    const int no = (int)old.size();
+    LY_CUDA(cudaMemcpyAsync(ms.act.p, old.data(), sizeof(int) * no, cudaMemcpyHostToDevice, st));
+    LY_CUDA(cudaMemcpyAsync(ms.cnt.p, &no, sizeof(int), cudaMemcpyHostToDevice, st));
+    CapArgs64 a{};
+    a.n = n;
+    a.k = k;
+    a.lam = sd->lam.p;
+    a.P1 = sd->Ub.p;
+    a.P2 = sd->Vb.p;
+    a.Gd = sd->Gd.p;
+    a.W = e.W.p;
+    a.ldw = N;
+    a.vinv = e.vinv.p;
+    a.rhs = sd->Ph.p;
+    a.ldr = 0;
+    a.out = ms.R64.p;
+    a.ldo = N;
+    a.mode = CAP_RESID;
+    a.list = ms.act.p;
+    a.count = ms.cnt.p;
+    a.nsys = no;
+    if (o.residual == LYAP_RESID_FP64) LY_TRY(capmv64_launch(a, st));
+    else if (o.residual == LYAP_RESID_TC && ms.oz_ok)
+      LY_TRY(oz::residual(a, ms.ozMapA, ms.ozEA.p, ms.mpad, ms.kpad, ms.ozPanel, ms.err.p, st));
+    else LY_TRY(capmv_df_launch(a, ms.Lff.p, ms.lc_scale, ms.p_scale, ms.sw.p, ms.panel_ff.p, st));
+    k_engine_norms<<<no, kry::NT, 0, st>>>(N, ms.act.p, no, ms.R64.p, e.rout.p);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    LY_CUDA(cudaMemcpyAsync(nrm_old.data(), e.rout.p, sizeof(double) * no, cudaMemcpyDeviceToHost, st));
+  }
+  int herr = 0;
+  LY_CUDA(cudaMemcpyAsync(&herr, ms.err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LY_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    LY_CUDA(cudaMemsetAsync(ms.err.p, 0, sizeof(int), st));
+    lyap_set_last_error("tensor-core GEMM wait timed out (code " + std::to_string(herr) + ")");
+    return LYAP_EDEVICE_TIMEOUT;
+  }
+  // ---- decisions
+  const double pn = sd->ph_norm;
+  std::vector<int> go, fin, fin_status;
+  std::vector<double> norms_go, fin_rel;
+  for (int s : fresh) {
+    go.push_back(s);
+    norms_go.push_back(pn);
+  }
+  for (size_t c = 0; c < old.size(); ++c) {
+    const int s = old[c];
+    const double rel = pn > 0 ? nrm_old[c] / pn : nrm_old[c];
+    int stt = 1;  // 1: continue
+    if (!std::isfinite(rel)) stt = LYAP_ENONFINITE;
+    else if (rel <= o.refine_tol) stt = LYAP_OK;
+    else if (e.steps[s] >= std::max(1, o.max_refine)) stt = LYAP_ENOCONV;
+    if (stt == 1) {
+      go.push_back(s);
+      norms_go.push_back(nrm_old[c]);
+    } else {
+      fin.push_back(s);
+      fin_status.push_back(stt);
+      fin_rel.push_back(rel);
+    }
+  }
+  // ---- retire: trace and error estimate (block-Jacobi proxy, as lyap_trace_EX)
+  if (!fin.empty()) {
+    const int nf = (int)fin.size();
+    LY_CUDA(cudaMemcpyAsync(e.slots2.p, fin.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, st));
+    LY_CUDA(cudaMemcpyAsync(ms.cnt.p, &nf, sizeof(int), cudaMemcpyHostToDevice, st));
+    k_engine_dot_h<<<nf, kry::NT, 0, st>>>(N, e.slots2.p, nf, e.W.p, sd->h.p, e.fout.p);
+    lyap_count_launch();
+    LY_TRY(prec_apply<double2>(sd, nullptr, false, e.vinv.p, e.slots2.p, ms.cnt.p, nf, ms.R64.p, (size_t)N,
+                               e.delta.p, (size_t)N, st));
+    k_engine_dot_h<<<nf, kry::NT, 0, st>>>(N, e.slots2.p, nf, e.delta.p, sd->h.p, e.eout.p);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    std::vector<double> fh(nf), eh(nf);
+    LY_CUDA(cudaMemcpyAsync(fh.data(), e.fout.p, sizeof(double) * nf, cudaMemcpyDeviceToHost, st));
+    LY_CUDA(cudaMemcpyAsync(eh.data(), e.eout.p, sizeof(double) * nf, cudaMemcpyDeviceToHost, st));
+    LY_CUDA(cudaStreamSynchronize(st));
+    for (int c = 0; c < nf; ++c) {
+      const int s = fin[c];
+      EngineDone d;
+      d.slot = s;
+      d.f = sd->f0 + fh[c];
+      d.info.iters = e.iters[s];
+      d.info.refine_steps = e.steps[s];
+      d.info.status = fin_status[c];
+      d.info.rel_resid = fin_rel[c];
+      d.info.err_est = d.f != 0 ? std::fabs(eh[c]) / std::fabs(d.f) : std::fabs(eh[c]);
+      done.push_back(d);
+      e.steps[s] = -1;
+    }
+  }
+  if (go.empty()) return LYAP_OK;
+  // ---- one inner solve of every continuing system
+  const int na = (int)go.size();
+  LY_CUDA(cudaMemcpyAsync(ms.act.p, go.data(), sizeof(int) * na, cudaMemcpyHostToDevice, st));
+  // ms.norms is indexed by slot in k_gather_r32 / k_scatter_add
+  {
+    std::vector<double> nfull(e.cap, 0.0);
+    for (int c = 0; c < na; ++c) nfull[go[c]] = norms_go[c];
+    LY_CUDA(cudaMemcpyAsync(ms.norms.p, nfull.data(), sizeof(double) * e.cap, cudaMemcpyHostToDevice, st));
+    k_gather_r32<<<dim3(gx(N), na), 256, 0, st>>>(N, k, ms.act.p, na, ms.R64.p, ms.norms.p, e.vinv.p, ms.R32.p,
+                                                  ms.vinv_c.p);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    SysOp<float2> op;
+    op.sd = sd;
+    op.vinv = ms.vinv_c.p;
+    if (e.r > 0) {
+      if (ms.wcinv.count < (size_t)na * e.r * e.r) LY_TRY(ms.wcinv.alloc((size_t)e.cap * e.r * e.r));
+      if (ms.wpart.count < wood_part_count(n, k, na, e.r)) LY_TRY(ms.wpart.alloc(wood_part_count(n, k, e.cap, e.r)));
+      ms.wood.cinv = ms.wcinv.p;
+      ms.wood.cpart = ms.wpart.p;
+      LY_TRY(wood_bind(sd, e.r, na, e.cinv.p, ms.act.p, ms.wood, st));
+      op.wood = &ms.wood;
+    }
+    std::vector<int> it, stt;
+    LY_TRY(gcrodr_chunk<float2>(op, na, ms.R32.p, (size_t)N, sd->rec32, pin, e.ws, it, stt, st));
+    k_scatter_add<<<dim3(gx(N), na), 256, 0, st>>>(N, ms.act.p, na, e.ws.X.p, ms.norms.p, e.W.p);
+    lyap_count_launch();
+    LY_CUDA(cudaGetLastError());
+    for (int c = 0; c < na; ++c) {
+      e.iters[go[c]] += it[c];
+      e.steps[go[c]] += 1;
     }
   }
   return LYAP_OK;

@@ -5,12 +5,21 @@
 // Each registered seed owns a CUDA stream and a worker thread. Requests
 // enter a FIFO; a request is admitted when the registered seeds' resident
 // bytes plus the workspace of all admitted, unfinished requests stay within
-// the budget. A seed's worker repeatedly takes every request admitted for
-// that seed since its previous batch started, solves them as one lockstep
-// batch on its stream (the seed's factors and recycled Krylov space stay
-// resident), publishes the results and frees their memory share, which
-// admits waiting requests. Workers of different seeds run concurrently, so
-// their kernels overlap on the device.
+// the budget. Workers of different seeds run concurrently, so their kernels
+// overlap on the device; the seed's factors and recycled Krylov space stay
+// resident.
+//
+// Mixed-precision traces (the default path) run through a continuous-
+// batching engine per seed: a fixed set of slots, each holding one
+// parameter vector's solve. Every engine step is one refinement step of all
+// occupied slots (FP64-accurate residual, then one recycled FP32 inner
+// solve, which ends within one or two GMRES cycles); a system whose residual
+// meets the tolerance retires at the step boundary and its slot is refilled
+// at once from the admitted requests, one vector per request in turn, so a
+// request that arrives while the seed is busy starts at the next step
+// instead of waiting for the running requests to finish. A request is
+// published when its last vector retires. Gradients and FP64 requests run as
+// whole lockstep batches between engine steps.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -22,6 +31,7 @@
 #include <vector>
 
 #include "lyap_internal.h"
+#include "mixed.h"
 
 namespace {
 
@@ -37,6 +47,7 @@ struct Request {
   Clock::time_point t_submit, t_done;
   int state = 0;  // 0 queued, 1 admitted, 2 running, 3 done, 4 cancelled
   int rc = LYAP_OK;
+  int placed = 0, finished = 0;  // engine: vectors given a slot, vectors retired
   std::vector<double> f, g;
   std::vector<lyap_result_info> info;
 };
@@ -71,6 +82,11 @@ struct SeedSlot {
   std::deque<uint64_t> ready;
   std::condition_variable cv;
   std::thread worker;
+  // continuous-batching engine (mixed-precision traces)
+  MixedEngine* eng = nullptr;
+  std::vector<std::pair<uint64_t, int>> owner;  // slot -> (request, vector index); request 0: free
+  std::deque<uint64_t> filling;                 // engine requests with vectors not yet placed
+  int occupied = 0;
 };
 
 // Device bytes a request of nv vectors may hold while it runs: the Krylov
@@ -111,69 +127,169 @@ void admit_locked(lyap_server* s) {
   }
 }
 
+constexpr int kEngineSlots = 512;  // slots per seed unless opts.batch sets another count
+
+bool engine_path(const lyap_server* s, const SeedSlot* slot, const Request& r) {
+  return s->opts.precision == LYAP_BF16_IR && !r.grad && slot->sd->mixed != nullptr;
+}
+
+// Publish a finished request (caller holds mu).
+void finish_locked(lyap_server* s, Request& r, int rc) {
+  r.rc = rc;
+  r.t_done = Clock::now();
+  r.state = 3;
+  s->admitted_bytes -= r.bytes;
+  --s->inflight;
+}
+
+// Solve batch-path requests (gradients, FP64) as lockstep batches.
+void run_batches(lyap_server* s, SeedSlot* slot, const std::vector<uint64_t>& batch) {
+  for (int want_grad = 0; want_grad < 2; ++want_grad) {
+    std::vector<uint64_t> ids;
+    std::vector<double> v;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (uint64_t id : batch) {
+        Request& r = s->reqs[id];
+        if (r.grad == (want_grad != 0)) {
+          ids.push_back(id);
+          v.insert(v.end(), r.v.begin(), r.v.end());
+        }
+      }
+    }
+    if (ids.empty()) continue;
+    const int k = slot->sd->k;
+    const int nv = (int)(v.size() / k);
+    std::vector<double> f(nv), g(want_grad ? (size_t)nv * k : 0);
+    std::vector<lyap_result_info> info(nv);
+    lyap_opts o = s->opts;
+    o.stream = slot->stream;
+    o.batch = 0;
+    int rc = want_grad ? lyap_grad(slot->sd, nv, v.data(), LYAP_MEM_HOST, &o, f.data(), g.data(), info.data())
+                       : lyap_trace_EX(slot->sd, nv, v.data(), LYAP_MEM_HOST, &o, f.data(), info.data());
+    std::lock_guard<std::mutex> lk(s->mu);
+    int off = 0;
+    for (uint64_t id : ids) {
+      Request& r = s->reqs[id];
+      r.f.assign(f.begin() + off, f.begin() + off + r.nv);
+      if (want_grad) r.g.assign(g.begin() + (size_t)off * k, g.begin() + (size_t)(off + r.nv) * k);
+      r.info.assign(info.begin() + off, info.begin() + off + r.nv);
+      off += r.nv;
+      finish_locked(s, r, rc);
+    }
+    admit_locked(s);
+    s->cv_done.notify_all();
+  }
+}
+
+// Give free engine slots to the filling requests, one vector per request in
+// turn (caller holds mu).
+void fill_slots_locked(lyap_server* s, SeedSlot* slot, std::vector<EngineJoin>& joins) {
+  const int k = slot->sd->k;
+  int next_free = 0;
+  const int cap = (int)slot->owner.size();
+  while (!slot->filling.empty()) {
+    bool placed_any = false;
+    for (size_t q = 0; q < slot->filling.size(); ++q) {
+      while (next_free < cap && slot->owner[next_free].first != 0) ++next_free;
+      if (next_free >= cap) return;
+      Request& r = s->reqs[slot->filling[q]];
+      if (r.placed >= r.nv) continue;
+      slot->owner[next_free] = {r.id, r.placed};
+      joins.push_back(EngineJoin{next_free, r.v.data() + (size_t)r.placed * k});
+      ++r.placed;
+      ++slot->occupied;
+      placed_any = true;
+    }
+    while (!slot->filling.empty() && s->reqs[slot->filling.front()].placed >= s->reqs[slot->filling.front()].nv)
+      slot->filling.pop_front();
+    if (!placed_any) return;
+  }
+}
+
 void worker_loop(SeedSlot* slot) {
   lyap_server* s = slot->srv;
   cudaSetDevice(slot->sd->device);
   for (;;) {
     std::vector<uint64_t> batch;
+    std::vector<EngineJoin> joins;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      slot->cv.wait(lk, [&] { return s->shutdown || !slot->ready.empty(); });
-      if (s->shutdown && slot->ready.empty()) return;
+      slot->cv.wait(lk, [&] {
+        return s->shutdown || !slot->ready.empty() || slot->occupied > 0 || !slot->filling.empty();
+      });
+      if (s->shutdown && slot->ready.empty() && slot->occupied == 0 && slot->filling.empty()) break;
       while (!slot->ready.empty()) {
         const uint64_t id = slot->ready.front();
         slot->ready.pop_front();
         auto it = s->reqs.find(id);
-        if (it != s->reqs.end() && it->second.state == 1) {
-          it->second.state = 2;
+        if (it == s->reqs.end() || it->second.state != 1) continue;
+        Request& r = it->second;
+        r.state = 2;
+        if (engine_path(s, slot, r)) {
+          r.f.assign(r.nv, 0.0);
+          r.info.assign(r.nv, lyap_result_info{});
+          slot->filling.push_back(id);
+        } else {
           batch.push_back(id);
         }
       }
-    }
-    if (batch.empty()) continue;
-    // Concatenate the batch's parameter vectors (requests with and without
-    // gradients are grouped separately so traces never pay for adjoints).
-    for (int want_grad = 0; want_grad < 2; ++want_grad) {
-      std::vector<uint64_t> ids;
-      std::vector<double> v;
-      {
-        std::lock_guard<std::mutex> lk(s->mu);
-        for (uint64_t id : batch) {
-          Request& r = s->reqs[id];
-          if (r.grad == (want_grad != 0)) {
-            ids.push_back(id);
-            v.insert(v.end(), r.v.begin(), r.v.end());
-          }
+      if (!slot->filling.empty() && !slot->eng) {
+        const int cap = s->opts.batch > 0 ? s->opts.batch : kEngineSlots;
+        lk.unlock();
+        MixedEngine* e = nullptr;
+        const int rc = lyap_engine_create(slot->sd, cap, s->opts, &e);
+        lk.lock();
+        if (rc != LYAP_OK) {  // fail the waiting engine requests
+          for (uint64_t id : slot->filling) finish_locked(s, s->reqs[id], rc);
+          slot->filling.clear();
+          admit_locked(s);
+          s->cv_done.notify_all();
+        } else {
+          slot->eng = e;
+          slot->owner.assign(cap, {0, 0});
         }
       }
-      if (ids.empty()) continue;
-      const int k = slot->sd->k;
-      const int nv = (int)(v.size() / k);
-      std::vector<double> f(nv), g(want_grad ? (size_t)nv * k : 0);
-      std::vector<lyap_result_info> info(nv);
-      lyap_opts o = s->opts;
-      o.stream = slot->stream;
-      o.batch = 0;
-      int rc = want_grad ? lyap_grad(slot->sd, nv, v.data(), LYAP_MEM_HOST, &o, f.data(), g.data(), info.data())
-                         : lyap_trace_EX(slot->sd, nv, v.data(), LYAP_MEM_HOST, &o, f.data(), info.data());
-      const auto now = Clock::now();
-      std::lock_guard<std::mutex> lk(s->mu);
-      int off = 0;
-      for (uint64_t id : ids) {
-        Request& r = s->reqs[id];
-        r.rc = rc;
-        r.f.assign(f.begin() + off, f.begin() + off + r.nv);
-        if (want_grad) r.g.assign(g.begin() + (size_t)off * k, g.begin() + (size_t)(off + r.nv) * k);
-        r.info.assign(info.begin() + off, info.begin() + off + r.nv);
-        off += r.nv;
-        r.t_done = now;
-        r.state = 3;
-        s->admitted_bytes -= r.bytes;
-        --s->inflight;
-      }
-      admit_locked(s);
-      s->cv_done.notify_all();
+      if (slot->eng) fill_slots_locked(s, slot, joins);
     }
+    if (!batch.empty()) run_batches(s, slot, batch);
+    if (!slot->eng || (joins.empty() && slot->occupied == 0)) continue;
+    lyap_opts o = s->opts;
+    o.stream = slot->stream;
+    std::vector<EngineDone> done;
+    const int rc = lyap_engine_step(slot->sd, *slot->eng, o, slot->stream, joins, done);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (rc != LYAP_OK) {
+      // every request with a vector in the engine fails; the engine restarts empty
+      for (auto& ow : slot->owner)
+        if (ow.first != 0) {
+          Request& r = s->reqs[ow.first];
+          if (r.state == 2) finish_locked(s, r, rc);
+          ow = {0, 0};
+        }
+      for (uint64_t id : slot->filling)
+        if (s->reqs[id].state == 2) finish_locked(s, s->reqs[id], rc);
+      slot->filling.clear();
+      slot->occupied = 0;
+      lyap_engine_free(slot->sd, slot->eng);
+      slot->eng = nullptr;
+    } else {
+      for (const EngineDone& d : done) {
+        const auto ow = slot->owner[d.slot];
+        slot->owner[d.slot] = {0, 0};
+        --slot->occupied;
+        Request& r = s->reqs[ow.first];
+        r.f[ow.second] = d.f;
+        r.info[ow.second] = d.info;
+        if (++r.finished == r.nv) finish_locked(s, r, LYAP_OK);
+      }
+    }
+    admit_locked(s);
+    s->cv_done.notify_all();
+  }
+  if (slot->eng) {
+    lyap_engine_free(slot->sd, slot->eng);
+    slot->eng = nullptr;
   }
 }
 

@@ -1,5 +1,6 @@
-"""Serving loop: continuous batching across seeds, admission by device
-memory, latency, and the identity of each result alone and in the mix.
+"""Serving loop: continuous batching across seeds and within a seed,
+admission by device memory, latency, and the identity of each result alone
+and in the mix.
 
 Alone vs mixed: the same request solved through a server with no other
 traffic and inside a concurrent mix of requests on several seeds must agree
@@ -99,3 +100,43 @@ def test_cancel_and_bad_input(setup):
     with pytest.raises(ly.LyapError):
         srv.submit(sid, bad)
     srv.close()
+
+
+def test_request_for_a_busy_seed_overtakes_a_long_request(setup):
+    """Mixed-precision traces join a seed's running set at the next
+    refinement step: a short request submitted while a long one occupies the
+    seed finishes first, and its results equal those of the same request
+    alone (1e-8) and the oracle's."""
+    import time
+
+    ctx, probs, seeds, reqs = setup
+    rng = np.random.default_rng(9)
+    k = probs[0].k
+    long_v = np.exp(rng.uniform(np.log(0.1), np.log(10.0), (1536, k)))
+    short_v = np.exp(rng.uniform(np.log(0.1), np.log(10.0), (8, k)))
+    srv = ly.Server(ctx, precision=ly.BF16_IR, batch=128)
+    sid = srv.register(seeds[0])
+    t_long = srv.submit(sid, long_v)
+    time.sleep(0.05)
+    t_short = srv.submit(sid, short_v)
+    done = {}
+    while len(done) < 2:
+        for name, t, nv in (("long", t_long, len(long_v)), ("short", t_short, len(short_v))):
+            if name not in done:
+                r = srv.poll(t, nv, k)
+                if r is not None:
+                    done[name] = (time.perf_counter(), r)
+        time.sleep(0.002)
+    srv.close()
+    assert done["short"][0] < done["long"][0]
+    assert done["short"][1]["latency_s"] < done["long"][1]["latency_s"]
+    alone = run_requests(ctx, seeds, [(0, short_v, False)], ly.BF16_IR)[0]
+    fs = done["short"][1]["f"]
+    assert np.all(np.abs(fs - alone["f"]) <= 1e-8 * np.abs(alone["f"]))
+    p = probs[0]
+    ref = [oracle.trace_EX(p.A0, p.U, p.V, p.G, p.E, x) for x in short_v[:2]]
+    assert np.all(np.abs(fs[:2] - ref) <= 1e-8 * np.abs(ref))
+    fl = done["long"][1]["f"]
+    ref = [oracle.trace_EX(p.A0, p.U, p.V, p.G, p.E, x) for x in long_v[[0, 1535]]]
+    assert np.all(np.abs(fl[[0, 1535]] - ref) <= 1e-8 * np.abs(ref))
+    assert all(i["status"] == 0 for i in done["long"][1]["info"])
