@@ -87,3 +87,29 @@ def test_serving_workload_seeds_through_server(ctx):
         fo = oracle.trace_EX(q.A0, q.U, q.V, q.G, q.E, v[5])
         assert rel_err(r["f"][5], fo) <= 1e-8
         assert all(i["status"] == 0 for i in r["info"])
+
+
+def test_serving_seed_of_3200_states_against_the_oracle(ctx):
+    """The largest serving seed (1600 masses, n = 3200) through the server's
+    engine: its refinement residual runs in float-float (n > 1023). One
+    parameter vector against the oracle (about two minutes of CPU), the
+    request's others against the FP64 GPU path."""
+    probs = workload_serving_seeds(dense=True, sizes=(1600,))
+    structured = workload_serving_seeds(dense=False, sizes=(1600,))[0]  # the same first seed, unrotated
+    q = probs[0]
+    assert q.n == 3200 and structured.k == q.k
+    seed = ly.Seed(ctx, q.A0, q.U, q.V, q.G, q.E)
+    rng = np.random.default_rng(17)
+    v = np.exp(rng.uniform(np.log(0.1), np.log(10.0), (16, q.k)))
+    srv = ly.Server(ctx, precision=ly.BF16_IR)
+    sid = srv.register(seed)
+    t = srv.submit(sid, v)
+    srv.run()
+    r = srv.poll(t, 16, q.k)
+    srv.close()
+    assert all(i["status"] == 0 for i in r["info"])
+    f64 = seed.trace_EX(v[:3], precision=ly.FP64)
+    assert rel_err(r["f"][:3], f64).max() <= 1e-8
+    fo = oracle.trace_EX(structured.A0, structured.U, structured.V, structured.G, structured.E, v[0])
+    assert rel_err(r["f"][0], fo) <= 1e-8
+    assert rel_err(f64[0], fo) <= 1e-10
