@@ -263,7 +263,7 @@ def run_serving(args, local):
     rates = sv["rates"]
     line = dict(metric=METRIC, value=rates["0.95"]["evals_per_s"], unit="evals/s", n_gpus=1, steps=args.requests,
                 warmup=16, ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="bf16x3-gemm/f32-krylov/int-sliced-bf16-refine (ff-refine for n > 1023)" if prec == ly.BF16_IR
+                dtype="bf16x3-gemm/f32-krylov/int-sliced-bf16-refine" if prec == ly.BF16_IR
                 else "f64", data="synthetic",
                 config=dict(workload="serving: " + sv["workload"], n=sv["n"], k=sv["k"]),
                 saturation_evals_per_s=sv["saturation_evals_per_s"], rates=rates, seed_factor_s=sv["seed_factor_s"],

@@ -84,7 +84,8 @@ extern "C" {
  * products by FMA) and runs on the FP32 pipes; FP64 uses the FP64 pipes;
  * TC (the default) splits both operands into 8 exact 6-bit integer digits
  * (48 bits, scaled per row/column) whose products the BF16 tensor cores sum
- * without rounding; it needs n <= 1023, and FF is used above. */
+ * without rounding; above 2n = 2046 the K dimension runs in chunks whose
+ * exact sums are added in float-float. */
 #define LYAP_RESID_FF 0
 #define LYAP_RESID_FP64 1
 #define LYAP_RESID_TC 2

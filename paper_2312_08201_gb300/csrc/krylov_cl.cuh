@@ -24,6 +24,11 @@
 namespace kry {
 
 constexpr int OCT = 256;          // threads per CTA of k_ortho_cl
+// Norm of the orthogonalised vector from the second pass's coefficients:
+// ||w2||^2 = ||w1||^2 - ||h2||^2 (w1 - w2 = V h2 with V orthonormal), with
+// ||w1||^2 reduced together with the second pass's inner products, so the
+// step needs two cluster reductions instead of three.
+constexpr bool kFoldNorm = true;
 constexpr int OCL_MAXNB = 64;     // basis vectors (s_cur + j + 1 <= m + 1 <= 61)
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -123,9 +128,9 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
     }
   };
   // coefficients: the cluster's partial sums added in rank order
-  auto gather = [&](R* in, T2* cf) {
+  auto gather = [&](R* in, T2* cf, int extra) {
     cl.sync();
-    if (tid < 2 * nb) {
+    if (tid < 2 * nb + extra) {
       R s = R(0);
       for (int r = 0; r < ncta; ++r) s += cl.map_shared_rank(in, r)[tid];
       reinterpret_cast<R*>(cf)[tid] = s;
@@ -145,29 +150,46 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
     return nr;
   };
 
+  auto block_total = [&](R x) -> R {  // sum over the CTA, on thread 0
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    R t = R(0);
+    if (tid == 0)
+      for (int w2 = 0; w2 < NW; ++w2) t += red[w2];
+    return t;
+  };
   // pass 1
   partial_dots(sw, part);
-  gather(part, coef);
-  update(coef);
+  gather(part, coef, 0);
+  const R n1 = update(coef);
   __syncthreads();
-  // pass 2
-  partial_dots(sw, part + 2 * OCL_MAXNB);
-  gather(part + 2 * OCL_MAXNB, coef + OCL_MAXNB);
-  R nr = update(coef + OCL_MAXNB);
-  // norm of the orthogonalised w
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(0xffffffffu, nr, o);
-  if (lane == 0) red[warp] = nr;
-  __syncthreads();
-  R* pn = part + 4 * OCL_MAXNB;
-  if (tid == 0) {
-    R t = R(0);
-    for (int w2 = 0; w2 < NW; ++w2) t += red[w2];
-    pn[0] = t;
-  }
-  cl.sync();
   R tot = R(0);
-  for (int r = 0; r < ncta; ++r) tot += cl.map_shared_rank(pn, r)[0];
+  if (kFoldNorm) {
+    // pass 2 with ||w1||^2 in the same reduction
+    R* p2 = part + 2 * OCL_MAXNB;
+    const R t1 = block_total(n1);
+    if (tid == 0) p2[2 * nb] = t1;
+    partial_dots(sw, p2);
+    gather(p2, coef + OCL_MAXNB, 1);
+    update(coef + OCL_MAXNB);
+    const R* c2 = reinterpret_cast<const R*>(coef + OCL_MAXNB);
+    tot = c2[2 * nb];
+    for (int q = 0; q < 2 * nb; ++q) tot -= c2[q] * c2[q];
+    tot = tot > R(0) ? tot : R(0);
+  } else {
+    // pass 2
+    partial_dots(sw, part + 2 * OCL_MAXNB);
+    gather(part + 2 * OCL_MAXNB, coef + OCL_MAXNB, 0);
+    const R nr = update(coef + OCL_MAXNB);
+    // norm of the orthogonalised w
+    R* pn = part + 4 * OCL_MAXNB;
+    const R t2 = block_total(nr);
+    if (tid == 0) pn[0] = t2;
+    cl.sync();
+    for (int r = 0; r < ncta; ++r) tot += cl.map_shared_rank(pn, r)[0];
+  }
   // scale and store this CTA's slice of the new basis vector
   const R rn = sqrt(tot);
   const R inv = rn > R(0) ? R(1) / rn : R(0);

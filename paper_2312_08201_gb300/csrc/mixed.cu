@@ -53,7 +53,7 @@ struct MixedState {
   double lc_scale = 1.0, p_scale = 1.0;
   DevBuf<double> sw;   // bcap
   DevBuf<float4> panel_ff;  // bcap x k^2 n
-  // integer-sliced tensor-core residual (oz_gemm.cu), when 2n <= oz::KMAX
+  // integer-sliced tensor-core residual (oz_gemm.cu; K in chunks above 2n = 2046)
   bool oz_ok = false;
   DevBuf<__nv_bfloat16> ozA;  // NS x mpad x kpad digits of the Cauchy matrix
   DevBuf<int> ozEA;           // mpad
@@ -414,7 +414,7 @@ int lyap_mixed_prepare(lyap_seed* sd, cudaStream_t st) {
     LY_TRY(ms->Lff.alloc((size_t)n * n));
     LY_TRY(capmv_df_build_lc(n, sd->lam.p, ms->lc_scale, ms->Lff.p, st));
   }
-  if (2 * n <= oz::KMAX) {
+  {
     LY_TRY(ms->ozA.alloc((size_t)oz::NS * ms->mpad * ms->kpad));
     LY_TRY(ms->ozEA.alloc(ms->mpad));
     LY_TRY(oz::slice_A(n, sd->lam.p, ms->mpad, ms->kpad, ms->ozA.p, ms->ozEA.p, st));

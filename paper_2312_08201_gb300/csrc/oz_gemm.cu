@@ -16,6 +16,7 @@
 // and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(256) k_slice_B(CapArgs64 a, int ncap, int kpad
 
 __global__ void __launch_bounds__(192, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              float2* __restrict__ D, int ldd, int mrows, int mpad, int ncap, int ktiles,
+              float2* __restrict__ D, int ldd, int mrows, int mpad, int ncap, int kt0, int ktiles, int accumulate,
               const int* __restrict__ count, int col_mult, int ncols_host, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -183,8 +184,8 @@ __global__ void __launch_bounds__(192, 1)
         mbar_expect_tx(fb, STAGE_BYTES);
 #pragma unroll 1
         for (int g = 0; g < NS; ++g) {
-          tma_load_2d(sm_addr(st + g * TILE_A), &tmA, fb, kt * BK, g * mpad + m0);
-          tma_load_2d(sm_addr(st + NS * TILE_A + g * TILE_B), &tmB, fb, kt * BK, g * ncap + n0);
+          tma_load_2d(sm_addr(st + g * TILE_A), &tmA, fb, (kt0 + kt) * BK, g * mpad + m0);
+          tma_load_2d(sm_addr(st + NS * TILE_A + g * TILE_B), &tmB, fb, (kt0 + kt) * BK, g * ncap + n0);
         }
       }
       ctl[0] = kt;
@@ -253,7 +254,19 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = n0 + c0 + j;
-          if (grow < mrows && col < ncols) D[(size_t)col * ldd + grow] = make_float2(h[j], l[j]);
+          if (grow < mrows && col < ncols) {
+            float2* dp = D + (size_t)col * ldd + grow;
+            if (accumulate) {
+              // add this K chunk to the earlier ones: exact two-sum of the high
+              // words, its error and the low words in the low word
+              const float2 o = *dp;
+              const float s2 = o.x + h[j];
+              const float t2 = s2 - o.x;
+              *dp = make_float2(s2, o.y + l[j] + ((o.x - (s2 - t2)) + (h[j] - t2)));
+            } else {
+              *dp = make_float2(h[j], l[j]);
+            }
+          }
         }
       }
     } else {
@@ -309,7 +322,7 @@ __global__ void __launch_bounds__(128) k_oz_epi(CapArgs64 a, const float2* __res
 }  // namespace
 
 int slice_A(int n, const double2* lam, int mpad, int kpad, void* S, int* eA, cudaStream_t st) {
-  if (2 * n > KMAX || mpad % BM != 0 || kpad % BK != 0) return LYAP_EINVAL;
+  if (mpad % BM != 0 || kpad % BK != 0) return LYAP_EINVAL;
   k_slice_A<<<mpad, 256, 0, st>>>(n, lam, mpad, kpad, reinterpret_cast<__nv_bfloat16*>(S), eA);
   lyap_count_launch();
   LY_CUDA(cudaGetLastError());
@@ -340,12 +353,14 @@ int make_map(CUtensorMap* map, const void* base, int rows_total, int kpad, int b
 
 int residual(const CapArgs64& a, const CUtensorMap& mapA, const int* eA, int mpad, int kpad, Panel& pn, int* err,
              cudaStream_t st) {
-  if (a.k < 1 || a.k > 8 || 2 * a.n > KMAX) return LYAP_EINVAL;
+  if (a.k < 1 || a.k > 8) return LYAP_EINVAL;
   if (a.nsys <= 0) return LYAP_OK;
   const int kk = a.k * a.k;
   const int ncols_cap = a.nsys * kk;
   if (ncols_cap > pn.ncap) return LYAP_EINVAL;
   LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_oz_gemm), SMEM_BYTES));
+  // one column of kpad doubles in shared memory (51 KB at n = 3200)
+  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_slice_B), sizeof(double) * kpad));
   k_slice_B<<<a.nsys, 256, sizeof(double) * kpad, st>>>(a, pn.ncap, kpad, reinterpret_cast<__nv_bfloat16*>(pn.S),
                                                          pn.eB);
   lyap_count_launch();
@@ -353,9 +368,14 @@ int residual(const CapArgs64& a, const CUtensorMap& mapA, const int* eA, int mpa
   // tensor work per system: NS (NS + 1) / 2 BF16 products of the (2n x 2n) x (2n x k^2) real-split GEMM
   const int ph = prof_begin(PK_OZGEMM, st);
   dim3 grid(mpad / BM, (ncols_cap + BN - 1) / BN);
-  k_oz_gemm<<<grid, 192, SMEM_BYTES, st>>>(mapA, pn.mapB, pn.D, mpad, 2 * a.n, mpad, pn.ncap, kpad / BK, a.count, kk,
-                                          ncols_cap, err);
-  lyap_count_launch();
+  // K in chunks of at most KCHUNK, each summed exactly in FP32 and added to
+  // the previous chunks' float-float results (one chunk for 2n <= KCHUNK)
+  for (int k0 = 0; k0 < kpad; k0 += KCHUNK) {
+    const int kt = (std::min(KCHUNK, kpad - k0)) / BK;
+    k_oz_gemm<<<grid, 192, SMEM_BYTES, st>>>(mapA, pn.mapB, pn.D, mpad, 2 * a.n, mpad, pn.ncap, k0 / BK, kt,
+                                            k0 > 0 ? 1 : 0, a.count, kk, ncols_cap, err);
+    lyap_count_launch();
+  }
   prof_end(ph, st, PAIRS * 2.0 * (2.0 * a.n) * (2.0 * a.n) * kk, 0.0, a.count ? 0 : a.nsys, a.count);
   LY_CUDA(cudaGetLastError());
   k_oz_epi<<<dim3((a.n + 127) / 128, a.nsys), 128, 0, st>>>(a, pn.D, mpad, eA, pn.eB);

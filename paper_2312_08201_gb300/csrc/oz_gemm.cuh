@@ -11,9 +11,9 @@
 // small integers, hence exact in BF16, and a digit product is at most 2^10.
 // For each order d = s + t <= NS - 1 the tensor cores accumulate
 //     ACC_d[r][c] = sum_{s+t=d} sum_k a_s[r][k] b_t[c][k]
-// in FP32 over the whole K. Every partial sum is an integer below
-// (d+1) K 2^10 <= NS K 2^10 < 2^24, so no rounding happens: this is what
-// bounds K (2n <= 2046). The result
+// in FP32. Every partial sum is an integer below (d+1) K 2^10 <= NS K 2^10,
+// which stays below 2^24 (no rounding) for K <= 2046; longer K runs in
+// chunks of KCHUNK whose exact results are added in float-float. The result
 //     D[r][c] = 2^(eA[r] + eB[c] - 12) sum_d 64^-d ACC_d[r][c]
 // is combined in float-float; dropping the orders d >= NS leaves an error of
 // about 2^-47 of |A||B|^T.
@@ -33,6 +33,7 @@ constexpr int BN = 64;           // panel columns per CTA (per order accumulator
 constexpr int BK = 32;           // K per stage: 32 BF16 = one 64-byte swizzle row
 constexpr int STAGES = 2;
 constexpr int KMAX = 2046;       // largest K with exact FP32 accumulation
+constexpr int KCHUNK = 2016;     // K per accumulation chunk (a multiple of BK, at most KMAX)
 
 // Digits of the real-split Cauchy matrix of a seed (rows mpad, K kpad):
 // S: NS x mpad x kpad BF16 (slice-major), eA: mpad exponents.

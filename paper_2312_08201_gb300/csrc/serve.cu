@@ -27,6 +27,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -50,6 +51,7 @@ struct Request {
   int placed = 0, finished = 0;  // engine: vectors given a slot, vectors retired
   std::vector<double> f, g;
   std::vector<lyap_result_info> info;
+  std::string error;  // the worker's error detail when rc != LYAP_OK
 };
 
 struct SeedSlot;
@@ -136,6 +138,7 @@ bool engine_path(const lyap_server* s, const SeedSlot* slot, const Request& r) {
 // Publish a finished request (caller holds mu).
 void finish_locked(lyap_server* s, Request& r, int rc) {
   r.rc = rc;
+  if (rc != LYAP_OK) r.error = lyap_last_error();  // the worker thread's detail
   r.t_done = Clock::now();
   r.state = 3;
   s->admitted_bytes -= r.bytes;
@@ -391,6 +394,7 @@ extern "C" int lyap_serve_poll(lyap_server* s, uint64_t ticket, double* trace_ou
     if (info) std::memcpy(info, r.info.data(), sizeof(lyap_result_info) * r.nv);
   }
   if (latency_s) *latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
+  if (rc != LYAP_OK) lyap_set_last_error(r.error);
   s->reqs.erase(it);
   return rc;
 }

@@ -262,3 +262,29 @@ def test_injected_maxit_in_the_mixed_path(ctx):
     f, info = seed.trace_EX(vs[:3], return_info=True, precision=ly.BF16_IR, inject=ly.INJECT_FORCE_MAXIT,
                             s=0, pbar=0, max_refine=2)
     assert all(i["status"] == ly.ENOCONV for i in info)
+
+
+@pytest.mark.parametrize("n,k", [(1100, 2), (2100, 3)])
+def test_sliced_operator_in_k_chunks(ctx, n, k):
+    """2n above 2046: the integer-sliced product runs K in chunks whose
+    exact FP32 sums are added in float-float (2 and 3 chunks here); same
+    1e-12 bound against the FP64 operator, and a refined solve against the
+    oracle."""
+    import torch
+
+    A0, U, V, G, E, vs = random_problem(70 + n, n, k, 2)
+    seed = ly.Seed(ctx, A0, U, V, G, None)
+    rng = np.random.default_rng(n)
+    w = rng.standard_normal((5, k, n, 2))
+    v = torch.tensor(vs[:5], dtype=torch.float64, device="cuda")
+    wt = torch.tensor(w, dtype=torch.float64, device="cuda")
+    for adjoint in (False, True):
+        y64 = ly.test_apply(seed, v, wt, ly.FP64, adjoint).cpu().numpy()
+        ytc = ly.test_apply(seed, v, wt, ly.TEST_TC, adjoint).cpu().numpy()
+        for b in range(5):
+            assert np.linalg.norm(ytc[b] - y64[b]) <= 1e-12 * np.linalg.norm(y64[b]), (adjoint, b)
+    if n == 1100:
+        f, info = seed.trace_EX(vs[:3], return_info=True, precision=ly.BF16_IR, residual=ly.RESID_TC)
+        assert all(i["status"] == 0 for i in info)
+        ref = np.array([oracle.trace_EX(A0, U, V, G, np.eye(n), x) for x in vs[:2]])
+        assert rel_err(f[:2], ref).max() <= TOL_MIXED

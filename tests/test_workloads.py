@@ -91,9 +91,9 @@ def test_serving_workload_seeds_through_server(ctx):
 
 def test_serving_seed_of_3200_states_against_the_oracle(ctx):
     """The largest serving seed (1600 masses, n = 3200) through the server's
-    engine: its refinement residual runs in float-float (n > 1023). One
-    parameter vector against the oracle (about two minutes of CPU), the
-    request's others against the FP64 GPU path."""
+    engine: its refinement residual runs the integer-sliced product in four
+    K chunks (2n = 6400). One parameter vector against the oracle (about two
+    minutes of CPU), the request's others against the FP64 GPU path."""
     probs = workload_serving_seeds(dense=True, sizes=(1600,))
     structured = workload_serving_seeds(dense=False, sizes=(1600,))[0]  # the same first seed, unrotated
     q = probs[0]
