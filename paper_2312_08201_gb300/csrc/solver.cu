@@ -264,54 +264,82 @@ size_t KrylovWS<T2>::bytes() const {
 }
 
 // --------------------------------------------------------- orthogonalisation
-// Shared memory per CTA of the cluster variant; at most this much lets two
-// CTAs share an SM.
+// Shared memory per CTA of the cluster variant; at most kOrthoSmemCap lets
+// two CTAs share an SM. Long vectors (nk of several thousand) use clusters
+// of 16 CTAs (a non-portable size) and then up to kOrthoSmemBig per CTA.
 constexpr size_t kOrthoSmemCap = 100 * 1024;
+constexpr size_t kOrthoSmemBig = 200 * 1024;
+
+namespace {
+// Clusters of 16 CTAs need an opt-in per device and kernel.
+template <typename T2>
+int allow_cluster16() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  LY_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return LYAP_OK;
+  LY_CUDA(cudaFuncSetAttribute(kry::k_ortho_cl<T2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  done.push_back(dev);
+  return LYAP_OK;
+}
+}  // namespace
 
 // CGS2 of Arnoldi step j for the listed systems (at most B). The cluster
-// kernel stages each system's basis in shared memory over C CTAs, with C the
-// smallest of 1, 2, 4, 8 whose slices fit kOrthoSmemCap; when none does, or
-// vectors do not start on 16-byte boundaries (bulk copies need them), the
-// kernel that streams the basis from memory runs instead.
+// kernel stages each system's basis in shared memory over C CTAs: the
+// smallest C of 1, 2, 4, 8 whose slices fit kOrthoSmemCap, else 16 CTAs at
+// kOrthoSmemCap, else the smallest C up to 16 at kOrthoSmemBig. When none
+// fits, the vectors do not start on 16-byte boundaries (bulk copies need
+// them) or the cluster cannot be scheduled, the kernel that streams the
+// basis from memory runs instead.
 template <typename T2>
 int launch_ortho(int N, int j, int m, int s_cur, const int* list, const int* count, int B, T2* V, const T2* C,
                  size_t c_ss, double2* H, double2* Bk, int smax, const kry::LsqArgs& la, int* err, cudaStream_t st) {
   const int nb = s_cur + j + 1;
   constexpr int kAlign = 16 / sizeof(T2);  // elements per 16 bytes
   int cl = 0, L = 0;
+  auto slice = [&](int c) { return ((N + c - 1) / c + kAlign - 1) / kAlign * kAlign; };
   if (((size_t)N * sizeof(T2)) % 16 == 0 && nb <= kry::OCL_MAXNB) {
-    for (int c = 1; c <= 8; c *= 2) {
-      const int l = ((N + c - 1) / c + kAlign - 1) / kAlign * kAlign;
-      if (kry::ortho_cl_smem<T2>(nb, l) <= kOrthoSmemCap) {
+    const int tiers[][2] = {{1, 0}, {2, 0}, {4, 0}, {8, 0}, {16, 0}, {1, 1}, {2, 1}, {4, 1}, {8, 1}, {16, 1}};
+    for (const auto& t : tiers) {
+      const int c = t[0];
+      const size_t cap = t[1] ? kOrthoSmemBig : kOrthoSmemCap;
+      if (kry::ortho_cl_smem<T2>(nb, slice(c)) <= cap) {
         cl = c;
-        L = l;
+        L = slice(c);
         break;
       }
     }
   }
-  if (cl == 0) {
-    kry::k_ortho<T2><<<B, kry::OT, 0, st>>>(N, j, m, s_cur, list, count, V, C, c_ss, H, Bk, smax, la);
-    lyap_count_launch();
-    LY_CUDA(cudaGetLastError());
-    return LYAP_OK;
+  if (cl > 0) {
+    const size_t smem = kry::ortho_cl_smem<T2>(nb, L);
+    LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(kry::k_ortho_cl<T2>), smem > kOrthoSmemCap ? kOrthoSmemBig
+                                                                                                    : kOrthoSmemCap));
+    if (cl > 8) LY_TRY(allow_cluster16<T2>());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(B * cl, 1, 1);
+    cfg.blockDim = dim3(kry::OCT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kry::k_ortho_cl<T2>, N, L, j, m, s_cur, list, count, V, C, c_ss,
+                                             H, Bk, smax, la, err);
+    if (e == cudaSuccess) {
+      lyap_count_launch();
+      return LYAP_OK;
+    }
+    (void)cudaGetLastError();  // a cluster shape the device cannot hold: stream instead
   }
-  const size_t smem = kry::ortho_cl_smem<T2>(nb, L);
-  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(kry::k_ortho_cl<T2>), kOrthoSmemCap));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(B * cl, 1, 1);
-  cfg.blockDim = dim3(kry::OCT, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cl;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  LY_CUDA(cudaLaunchKernelEx(&cfg, kry::k_ortho_cl<T2>, N, L, j, m, s_cur, list, count, V, C, c_ss, H, Bk, smax, la,
-                             err));
+  kry::k_ortho<T2><<<B, kry::OT, 0, st>>>(N, j, m, s_cur, list, count, V, C, c_ss, H, Bk, smax, la);
   lyap_count_launch();
+  LY_CUDA(cudaGetLastError());
   return LYAP_OK;
 }
 
