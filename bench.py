@@ -32,9 +32,10 @@ WORKLOAD = "chain400 n=800 k=2, 1000 v log-uniform [1e-2,1e2]^2 NN-ordered, Haar
 FP64_PEAK_FLOPS_PER_CLK_SM = 4.0  # 2 FP64 FMA per clock per SM (1.25 TFLOP/s at 2070 MHz x 152 SMs)
 SMS = 152
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel,
-# from a one-kernel ncu capture of the same workload (see profiles/); empty
-# while no capture of the kernels as they stand exists.
-MEASURED_TRAFFIC_PER_LAUNCH = {}
+# averaged over every launch of that kernel in one 1000-vector sweep of this
+# workload, from a one-kernel ncu capture (profiles/ortho_cl_800state_1000v.md).
+# Valid for the kernel as it stands; a change to the kernel invalidates it.
+MEASURED_TRAFFIC_PER_LAUNCH = {"ortho": 109.54e6}
 FP32_LANES_PER_SM = 128.0  # FP32 lane-instructions per clock per SM
 L2_FLUSH_BYTES = 256 << 20
 
@@ -642,7 +643,8 @@ def main():
         roof["algorithmic_bytes_per_launch"] = d["bytes"] / d["launches"]
         if dom_name in MEASURED_TRAFFIC_PER_LAUNCH and precision == "bf16_ir" and nv == 1000:
             roof["traffic"] = MEASURED_TRAFFIC_PER_LAUNCH[dom_name]
-            roof["traffic_note"] = "DRAM bytes per launch from one ncu capture of a full sweep (cold caches)"
+            roof["traffic_note"] = ("DRAM bytes per launch, mean over the kernel's launches in one sweep, "
+                                    "from a one-kernel ncu capture (1 pass)")
     kernels = {kname: dict(launches=v["launches"], ms=round(v["total_ms"], 3),
                            share=round(v["total_ms"] / max(1e-9, sum(x["total_ms"] for x in prof.values())), 4))
                for kname, v in prof.items()}

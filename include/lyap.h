@@ -268,6 +268,24 @@ int lyap_serve_cancel(lyap_server* srv, uint64_t ticket);
 /* Finish running batches, stop the workers and free the server. */
 void lyap_serve_destroy(lyap_server* srv);
 
+/* --------------------------------------------- independent explicit check
+ * Verification of given solutions through the explicit Lyapunov solution
+ * (O(n^3) per vector, FP64): for nv parameter vectors v (nv x k row-major)
+ * and their shifted capacitance solutions w (nv x n x k complex128, as
+ * written by lyap_param_solve), forms
+ *   X(v) = X0 + Qp (Lc o (W' Ub^T + Ub W'^T)) Qp^T
+ * (§2.1, eqs. (splitXv), (seedLE), (Xsmalllastline)) and evaluates the true
+ * residual of the equation, R = A(v)^T X + X A(v) + G G^T, from the
+ * caller's A0 (n x n), U, V (n x k), G (n x g) and E (n x n symmetric or
+ * NULL for I). backward_err_out[b] = ||R||_F / (2 ||A(v)||_F ||X||_F +
+ * ||G G^T||_F) (the form of §2.2's backward error proposition) and
+ * trace_out[b] = trace(E X(v)), both host arrays. All other pointers are
+ * in mem_kind memory. Synchronises. Errors: LYAP_EINVAL, LYAP_ENOMEM,
+ * LYAP_ECUDA, LYAP_ESOLVER. */
+int lyap_check_explicit(lyap_seed* seed, int nv, const double* v, const double* w, const double* A0, const double* U,
+                        const double* V, const double* G, int g, const double* E, int mem_kind,
+                        double* backward_err_out, double* trace_out);
+
 /* --------------------------------------------------- projection framework
  * The large-scale method of §2.2 (eqs. (EK_def), (param_projected), the
  * backward error proposition, Algorithm 1). One extended Krylov space

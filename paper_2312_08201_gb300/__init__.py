@@ -155,6 +155,9 @@ _SIGS = {
     "lyap_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "lyap_serve_destroy": (None, [_P]),
     "lyap_check_solution_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "lyap_check_explicit": (
+        ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P]
+    ),
     "lyap_proj_create": (
         ctypes.c_int,
         [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int,
@@ -423,6 +426,23 @@ class Projection:
             self.free()
         except Exception:
             pass
+
+
+def check_explicit(seed, v, W, A0, U, V, G, E=None):
+    """lyap_check_explicit on host arrays: v (nv, k); W the complex (nv, k, n)
+    solutions of Seed.param_solve. Returns (backward errors, traces)."""
+    lib = load()
+    va = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1, seed.k))
+    nv = va.shape[0]
+    Wc = np.ascontiguousarray(np.asarray(W, dtype=np.complex128).reshape(nv, seed.k, seed.n))
+    mats = [_host_f64(a) for a in (A0, U, V, G)]
+    ea = _host_f64(E) if E is not None else None
+    be = np.empty(nv)
+    tr = np.empty(nv)
+    ptr = (lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None)
+    _check(lib.lyap_check_explicit(seed.h, nv, ptr(va), ptr(Wc), *[ptr(a) for a in mats], int(mats[3].shape[1]),
+                                   ptr(ea), MEM_HOST, ptr(be), ptr(tr)), "lyap_check_explicit")
+    return be, tr
 
 
 class Server:
