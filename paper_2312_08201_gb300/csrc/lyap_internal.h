@@ -144,6 +144,7 @@ struct lyap_seed {
   // O ~ tsvd_N tsvd_M^T, nk x tsvd_r each (FP32), built on first use.
   DevBuf<float2> tsvd_N, tsvd_M;
   int tsvd_r = 0;
+  DevBuf<float2> cap_work;  // K(v)^{-1} Nl of a chunk of systems while Cap(v)^{-1} is built
   // Recycle spaces: primal/adjoint x FP64/FP32-inner.
   Recycle<double2> rec64, rec64_adj;
   Recycle<float2> rec32, rec32_adj;

@@ -141,6 +141,84 @@ struct Elim<K, K> {
   static __device__ __forceinline__ void run(float (&)[K][K], float (&)[K][K], float2 (&)[K]) {}
 };
 
+// LU factorisation with partial pivoting of the k x k block, kept in
+// registers: U on and above the diagonal, the multipliers of each step
+// below it, and the pivot row of each step in piv (at step C, columns >= C
+// of rows C and piv[C] are swapped; lu_solve replays the swaps in order).
+template <int K, int C>
+struct Lu {
+  static __device__ __forceinline__ void run(float (&Ar)[K][K], float (&Ai)[K][K], int (&piv)[K]) {
+    float best = Ar[C][C] * Ar[C][C] + Ai[C][C] * Ai[C][C];
+    int p = C;
+#pragma unroll
+    for (int r = C + 1; r < K; ++r) {
+      const float a = Ar[r][C] * Ar[r][C] + Ai[r][C] * Ai[r][C];
+      if (a > best) {
+        best = a;
+        p = r;
+      }
+    }
+    piv[C] = p;
+#pragma unroll
+    for (int r = C + 1; r < K; ++r) {
+      const bool sw = r == p;
+#pragma unroll
+      for (int q = C; q < K; ++q) {  // earlier multipliers stay: lu_solve swaps x step by step
+        const float ar = Ar[C][q], ai = Ai[C][q], br = Ar[r][q], bi = Ai[r][q];
+        Ar[C][q] = sw ? br : ar;
+        Ai[C][q] = sw ? bi : ai;
+        Ar[r][q] = sw ? ar : br;
+        Ai[r][q] = sw ? ai : bi;
+      }
+    }
+    const float2 inv = best > 0.f ? make_float2(Ar[C][C] / best, -Ai[C][C] / best) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = C + 1; r < K; ++r) {
+      const float2 f = cmul(make_float2(Ar[r][C], Ai[r][C]), inv);
+#pragma unroll
+      for (int q = C + 1; q < K; ++q) {
+        const float2 v = csub(make_float2(Ar[r][q], Ai[r][q]), cmul(f, make_float2(Ar[C][q], Ai[C][q])));
+        Ar[r][q] = v.x;
+        Ai[r][q] = v.y;
+      }
+      Ar[r][C] = f.x;
+      Ai[r][C] = f.y;
+    }
+    Lu<K, C + 1>::run(Ar, Ai, piv);
+  }
+};
+template <int K>
+struct Lu<K, K> {
+  static __device__ __forceinline__ void run(float (&)[K][K], float (&)[K][K], int (&)[K]) {}
+};
+
+// x <- (P L U)^{-1} x with the factors of Lu
+template <int K>
+__device__ __forceinline__ void lu_solve(const float (&Ar)[K][K], const float (&Ai)[K][K], const int (&piv)[K],
+                                         float2 (&x)[K]) {
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+#pragma unroll
+    for (int r = c + 1; r < K; ++r) {
+      const bool sw = r == piv[c];
+      const float2 a = x[c], b = x[r];
+      x[c] = sw ? b : a;
+      x[r] = sw ? a : b;
+    }
+#pragma unroll
+    for (int r = c + 1; r < K; ++r) x[r] = csub(x[r], cmul(make_float2(Ar[r][c], Ai[r][c]), x[c]));
+  }
+#pragma unroll
+  for (int c = K - 1; c >= 0; --c) {
+    float2 s = x[c];
+#pragma unroll
+    for (int q = c + 1; q < K; ++q) s = csub(s, cmul(make_float2(Ar[c][q], Ai[c][q]), x[q]));
+    const float d = Ar[c][c] * Ar[c][c] + Ai[c][c] * Ai[c][c];
+    x[c] = d > 0.f ? make_float2((s.x * Ar[c][c] + s.y * Ai[c][c]) / d, (s.y * Ar[c][c] - s.x * Ai[c][c]) / d)
+                   : make_float2(0.f, 0.f);
+  }
+}
+
 template <int K>
 __device__ __forceinline__ void bsolve(int n, int j, const float2* __restrict__ Gd, int gT, const float (&vb)[K],
                                        float2 (&x)[K]) {
@@ -173,88 +251,12 @@ __device__ __forceinline__ void load_vb(const double* __restrict__ vinv, int b, 
 }
 
 
-// Rows of Nl and Ml staged per step of the capacitance product: J K r
-// entries of each, about 32 K-blocks' worth of rows.
-template <int K>
-struct CapRows {
-  static constexpr int J = K <= 2 ? 32 : (K <= 4 ? 16 : 8);
-};
-
-// Cap_b^{-1} with Cap_b = I - Ml^T K_b^{-1} Nl (r x r, column-major), one CTA
-// per system: the product accumulates over chunks of J rows, then
-// Gauss-Jordan elimination with partial pivoting inverts it in shared memory.
-template <int K>
-__global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const float2* __restrict__ Gd,
-                                                  const double* __restrict__ vinv, const float2* __restrict__ Nl,
-                                                  const float2* __restrict__ Ml, int ldr, float2* __restrict__ cinv) {
-  extern __shared__ float2 sw[];  // [J x K x rp] K^{-1} Nl rows, [J x K x rp] Ml rows; then C, Inv (r x r each)
-  __shared__ float2 fcol[RMAX];
-  __shared__ int piv_s;
-  constexpr int J = CapRows<K>::J;
-  const int rp = r | 1;  // odd row length: the fill's stores spread over the banks
-  float2* sm = sw + (size_t)J * K * rp;
-  const int b = blockIdx.x;
-  float vb[K];
-  load_vb<K>(vinv, b, vb);
+// Gauss-Jordan inversion with partial pivoting of the r x r matrix C
+// (column-major, shared memory), by the whole CTA; Inv starts as I and
+// ends as C^{-1}; C is destroyed.
+__device__ void gj_invert(int r, float2* C, float2* Inv, float2* fcol, int* piv_sp) {
   const int nout = r * r;
-  // each thread owns a 4 x 4 tile of Cap (rows l0.., columns l20..): one pair
-  // of shared loads per row of the tile feeds 16 multiply-adds
-  const int tr = (r + 3) / 4, ntile = tr * tr;  // <= 256 = WT for r <= 64
-  const int tile = threadIdx.x;
-  const int l0 = 4 * (tile % tr), l20 = 4 * (tile / tr);
-  float2 acc[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = make_float2(0.f, 0.f);
-  for (int j0 = 0; j0 < n; j0 += J) {
-    // consecutive threads take consecutive rows j of a column l (coalesced)
-    for (int e = threadIdx.x; e < J * r; e += WT) {
-      const int jj = e % J, l = e / J, j = j0 + jj;
-      float2 x[K];
-      if (j < n) {
-#pragma unroll
-        for (int t = 0; t < K; ++t) x[t] = Nl[(size_t)t * n + j + (size_t)l * ldr];
-        bsolve<K>(n, j, Gd, 0, vb, x);
-      }
-#pragma unroll
-      for (int t = 0; t < K; ++t) {
-        sw[((size_t)jj * K + t) * rp + l] = j < n ? x[t] : make_float2(0.f, 0.f);
-        sm[((size_t)jj * K + t) * rp + l] = j < n ? Ml[(size_t)t * n + j + (size_t)l * ldr] : make_float2(0.f, 0.f);
-      }
-    }
-    __syncthreads();
-    if (tile < ntile) {
-      for (int q = 0; q < J * K; ++q) {
-        float2 mv[4], wv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          mv[u] = l0 + u < r ? sm[(size_t)q * rp + l0 + u] : make_float2(0.f, 0.f);
-          wv[u] = l20 + u < r ? sw[(size_t)q * rp + l20 + u] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = cfma(mv[u], wv[v], acc[u][v]);
-      }
-    }
-    __syncthreads();
-  }
-  float2* C = sw;            // r x r, column-major: C[i + q r]
-  float2* Inv = sw + nout;   // r x r
-  if (tile < ntile) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int l = l0 + u, l2 = l20 + v;
-        if (l < r && l2 < r) {
-          C[l + l2 * r] = make_float2((l == l2 ? 1.f : 0.f) - acc[u][v].x, -acc[u][v].y);
-          Inv[l + l2 * r] = make_float2(l == l2 ? 1.f : 0.f, 0.f);
-        }
-      }
-  }
-  __syncthreads();
+  int& piv_s = *piv_sp;
   for (int c = 0; c < r; ++c) {
     if (threadIdx.x < 32) {
       float best = -1.f;
@@ -307,6 +309,61 @@ __global__ void __launch_bounds__(WT) k_cap_build(int n, int r, const float2* __
     }
     __syncthreads();
   }
+}
+
+// Y_b = K_b(v)^{-1} Nl for the systems of a chunk (Y: nsys x nk x r, column-
+// major per system). One thread per (row j, system): the k x k block is
+// factorised once and its factors solve the r columns.
+template <int K>
+__global__ void __launch_bounds__(WT) k_kinv_nl(int n, int r, const float2* __restrict__ Gd,
+                                                const double* __restrict__ vinv, const float2* __restrict__ Nl,
+                                                int ldr, int nsys, float2* __restrict__ Y) {
+  const int j = blockIdx.x * WT + threadIdx.x;
+  const int b = blockIdx.y;
+  if (j >= n || b >= nsys) return;
+  float vb[K];
+  load_vb<K>(vinv, b, vb);
+  float Ar[K][K], Ai[K][K];
+#pragma unroll
+  for (int t = 0; t < K; ++t)
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+      const float2 g = Gd[(size_t)(p * K + t) * n + j];
+      Ar[t][p] = (t == p ? vb[t] : 0.f) - g.x;
+      Ai[t][p] = -g.y;
+    }
+  int piv[K];
+  Lu<K, 0>::run(Ar, Ai, piv);
+  const size_t nk = (size_t)n * K;
+  float2* Yb = Y + (size_t)b * nk * r;
+  for (int l = 0; l < r; ++l) {
+    float2 x[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) x[t] = Nl[(size_t)t * n + j + (size_t)l * ldr];
+    lu_solve<K>(Ar, Ai, piv, x);
+#pragma unroll
+    for (int t = 0; t < K; ++t) Yb[(size_t)t * n + j + (size_t)l * nk] = x[t];
+  }
+}
+
+// cinv_b = (I + C_b)^{-1} for C_b = -Ml^T Y_b (r x r, from the batched GEMM)
+__global__ void __launch_bounds__(WT) k_cap_inv(int r, const float2* __restrict__ Cin, float2* __restrict__ cinv) {
+  extern __shared__ float2 cm[];  // C, Inv (r x r each)
+  __shared__ float2 fcol[RMAX];
+  __shared__ int piv_s;
+  const int b = blockIdx.x;
+  const int nout = r * r;
+  float2* C = cm;
+  float2* Inv = cm + nout;
+  for (int e = threadIdx.x; e < nout; e += WT) {
+    const int i = e % r, q = e / r;
+    float2 c = Cin[(size_t)b * nout + e];
+    if (i == q) c.x += 1.f;
+    C[e] = c;
+    Inv[e] = make_float2(i == q ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  gj_invert(r, C, Inv, fcol, &piv_s);
   for (int o = threadIdx.x; o < nout; o += WT) cinv[(size_t)b * nout + o] = Inv[o];
 }
 
@@ -467,15 +524,40 @@ __global__ void __launch_bounds__(WT) k_prec_b(int n, const int* __restrict__ li
   }
 }
 
-template <int K>
-size_t cap_smem(int r) {
-  return sizeof(float2) * std::max<size_t>((size_t)2 * CapRows<K>::J * K * (r | 1), (size_t)2 * r * r);
-}
+// Cap(v_b)^{-1} for systems b < B: Y_b = K_b^{-1} Nl (k_kinv_nl), then
+// Cap_b - I = -Ml^T Y_b for all systems of a chunk in one strided-batched
+// CGEMM (FP32, cuBLAS), then one Gauss-Jordan inversion per system. Chunks
+// of systems keep the Y buffer (nk x r per system) within kCapWorkBytes.
+constexpr size_t kCapWorkBytes = size_t(1) << 30;
 
 template <int K>
 int launch_cap_build(lyap_seed* sd, int r, int B, const double* vinv, const WoodState& ws, cudaStream_t st) {
-  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_cap_build<K>), cap_smem<K>(RMAX)));
-  k_cap_build<K><<<B, WT, cap_smem<K>(r), st>>>(sd->n, r, sd->Gdf.p, vinv, ws.Nl, ws.Ml, ws.ldr, ws.cinv);
+  const int n = sd->n;
+  const size_t nk = (size_t)n * K, per = nk * (size_t)r * sizeof(float2) + (size_t)r * r * sizeof(float2);
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)B, kCapWorkBytes / per));
+  const size_t need = (size_t)chunk * (nk * r + (size_t)r * r);
+  if (sd->cap_work.count < need) LY_TRY(sd->cap_work.alloc(need));
+  float2* Y = sd->cap_work.p;
+  float2* Cm = Y + (size_t)chunk * nk * r;
+  LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_cap_inv), 2 * sizeof(float2) * RMAX * RMAX));
+  lyap_ctx* ctx = sd->ctx;
+  for (int b0 = 0; b0 < B; b0 += chunk) {
+    const int nb = std::min(chunk, B - b0);
+    k_kinv_nl<K><<<dim3((n + WT - 1) / WT, nb), WT, 0, st>>>(n, r, sd->Gdf.p, vinv + (size_t)b0 * K, ws.Nl, ws.ldr,
+                                                             nb, Y);
+    {
+      std::lock_guard<std::mutex> lk(ctx->handle_mu);  // library handles are shared by the context's users
+      LY_BLAS(cublasSetStream(ctx->blas, st));
+      const cuComplex m1 = make_cuComplex(-1.f, 0.f), z = make_cuComplex(0.f, 0.f);
+      LY_BLAS(cublasCgemmStridedBatched(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, r, r, (int)nk, &m1,
+                                        reinterpret_cast<const cuComplex*>(ws.Ml), ws.ldr, 0,
+                                        reinterpret_cast<const cuComplex*>(Y), (int)nk, (long long)nk * r, &z,
+                                        reinterpret_cast<cuComplex*>(Cm), r, (long long)r * r, nb));
+    }
+    k_cap_inv<<<nb, WT, 2 * sizeof(float2) * r * r, st>>>(r, Cm, ws.cinv + (size_t)b0 * r * r);
+    lyap_count_launch(2);
+    LY_CUDA(cudaGetLastError());
+  }
   return LYAP_OK;
 }
 
