@@ -375,8 +375,9 @@ __global__ void __launch_bounds__(WT) k_cap_inv(int r, const float2* __restrict_
 // systems):
 //   k_prec_a: z = K^{-1} r for the tile, and the tile's partial sums of
 //             c = B^T z, written per row tile (no atomics: deterministic);
-//   k_prec_b: c = sum of the partials, y = Cap^{-1} c (recomputed by every
-//             row tile of the system tile), z += K^{-1} (A y) for the tile.
+//   k_prec_y: c = sum of the partials, y = Cap^{-1} c, one CTA per system,
+//             y written over the first row tile's partial;
+//   k_prec_b: z += K^{-1} (A y) for the tile.
 // FP32 arithmetic; input and output in the Krylov precision.
 constexpr int PST = 16;
 template <int K>
@@ -422,24 +423,82 @@ __global__ void __launch_bounds__(WT) k_prec_a(int n, const int* __restrict__ li
     }
   }
   if (r <= 0) return;
-  __syncthreads();
+  // c partials: thread (lp, sp) owns ranks 2lp, 2lp+1 of systems 2sp, 2sp+1;
+  // QC rows of B at a time are staged in shared memory (coalesced over rows)
+  constexpr int QC = 16;
+  __shared__ float2 bs[QC][RMAX + 1];  // odd row length: the fill's stores spread over the banks
   const int rows = min(RT, n - j0);
-  for (int e = threadIdx.x; e < r * PST; e += WT) {
-    const int sl = e % PST, l = e / PST;
-    if (s0 + sl >= nact) continue;
-    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+  const int lp = threadIdx.x & 31, sp = threadIdx.x >> 5;
+  const int l0 = 2 * lp, sl0 = 2 * sp;
+  float2 acc[2][2];
 #pragma unroll
-    for (int t = 0; t < K; ++t) {
-      const float2* bcol = Bop + (size_t)t * n + j0 + (size_t)l * ldr;
-      int q = 0;
-#pragma unroll 4
-      for (; q + 1 < rows; q += 2) {
-        a0 = cfma(bcol[q], zs[sl][t][q], a0);
-        a1 = cfma(bcol[q + 1], zs[sl][t][q + 1], a1);
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int w = 0; w < 2; ++w) acc[u][w] = make_float2(0.f, 0.f);
+  for (int t = 0; t < K; ++t)
+    for (int q0 = 0; q0 < rows; q0 += QC) {
+      __syncthreads();  // the previous chunk is consumed (and, first time, zs is complete)
+      for (int e = threadIdx.x; e < QC * r; e += WT) {
+        const int qq = e % QC, l = e / QC;
+        bs[qq][l] = q0 + qq < rows ? Bop[(size_t)t * n + j0 + q0 + qq + (size_t)l * ldr] : make_float2(0.f, 0.f);
       }
-      if (q < rows) a0 = cfma(bcol[q], zs[sl][t][q], a0);
+      __syncthreads();
+#pragma unroll 4
+      for (int qq = 0; qq < QC; ++qq) {
+        const float2 b0 = bs[qq][l0], b1 = bs[qq][l0 + 1];
+        const float2 z0 = zs[sl0][t][min(q0 + qq, RT - 1)], z1 = zs[sl0 + 1][t][min(q0 + qq, RT - 1)];
+        acc[0][0] = cfma(b0, z0, acc[0][0]);
+        acc[0][1] = cfma(b0, z1, acc[0][1]);
+        acc[1][0] = cfma(b1, z0, acc[1][0]);
+        acc[1][1] = cfma(b1, z1, acc[1][1]);
+      }
     }
-    Cp[((size_t)blockIdx.x * nslots + s0 + sl) * r + l] = cadd(a0, a1);
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+      if (l0 + u < r && s0 + sl0 + w < nact) Cp[((size_t)blockIdx.x * nslots + s0 + sl0 + w) * r + l0 + u] = acc[u][w];
+}
+
+// y = Cap^{-1} c (Cap^{-T} c for the adjoint) for the listed systems, c the
+// sum of k_prec_a's row-tile partials; one CTA per system slot. Cap^{-1} is
+// staged in shared memory with an odd column stride, so both the plain and
+// the transposed product read it without bank conflicts.
+__global__ void __launch_bounds__(WT) k_prec_y(const int* __restrict__ list, const int* __restrict__ count, int adj,
+                                               int r, const float2* __restrict__ cinv, float2* __restrict__ Cp,
+                                               int nslots, int ntx) {
+  __shared__ float2 Cs[RMAX * (RMAX + 1)];
+  __shared__ float2 cs[RMAX];
+  __shared__ float2 ys[WT / RMAX][RMAX];
+  const int s = blockIdx.x;
+  if (s >= *count) return;
+  const int rp = r | 1;
+  const float2* Ci = cinv + (size_t)list[s] * r * r;
+  for (int e = threadIdx.x; e < r * r; e += WT) Cs[(e % r) + (e / r) * rp] = Ci[e];
+  for (int l = threadIdx.x; l < r; l += WT) {
+    float2 c = make_float2(0.f, 0.f);
+    for (int tx = 0; tx < ntx; ++tx) c = cadd(c, Cp[((size_t)tx * nslots + s) * r + l]);
+    cs[l] = c;
+  }
+  __syncthreads();
+  // thread (l, g): the terms q = g, g + G, ... of y_l
+  constexpr int G = WT / RMAX;
+  const int l = threadIdx.x % RMAX, g = threadIdx.x / RMAX;
+  float2 y = make_float2(0.f, 0.f);
+  if (l < r) {
+    if (adj) {
+      for (int q = g; q < r; q += G) y = cfma(Cs[q + l * rp], cs[q], y);
+    } else {
+      for (int q = g; q < r; q += G) y = cfma(Cs[l + q * rp], cs[q], y);
+    }
+  }
+  ys[g][l] = y;
+  __syncthreads();
+  if (threadIdx.x < r) {
+    float2 t = ys[0][threadIdx.x];
+#pragma unroll
+    for (int u = 1; u < G; ++u) t = cadd(t, ys[u][threadIdx.x]);
+    Cp[(size_t)s * r + threadIdx.x] = t;
   }
 }
 
@@ -448,40 +507,16 @@ __global__ void __launch_bounds__(WT) k_prec_b(int n, const int* __restrict__ li
                                                const float2* __restrict__ Gd, int adj,
                                                const double* __restrict__ vinv, T2* __restrict__ Out, size_t out_ss,
                                                int r, const float2* __restrict__ Aop, int ldr,
-                                               const float2* __restrict__ cinv, const float2* __restrict__ Cp,
-                                               int nslots, int ntx) {
+                                               const float2* __restrict__ Yp) {
   constexpr int RT = PrecTile<K>::RT;
-  __shared__ float2 cs[PST][RMAX + 1];
   __shared__ float2 ys[PST][RMAX + 1];
   const int nact = *count;
   const int s0 = blockIdx.y * PST;
   if (s0 >= nact) return;
   const int j0 = blockIdx.x * RT;
-  // one warp per system of the tile, lanes over the rank index: the partial
-  // sums and Cap^{-1} are read with coalesced, independent loads
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int sl = warp; sl < PST; sl += WT / 32) {
-    const bool live = s0 + sl < nact;
-    for (int l = lane; l < r; l += 32) {
-      float2 c = make_float2(0.f, 0.f);
-      if (live)
-        for (int tx = 0; tx < ntx; ++tx) c = cadd(c, Cp[((size_t)tx * nslots + s0 + sl) * r + l]);
-      cs[sl][l] = c;
-    }
-    __syncwarp();
-    // y = Cap^{-1} c, or Cap^{-T} c for the adjoint
-    for (int l = lane; l < r; l += 32) {
-      float2 y = make_float2(0.f, 0.f);
-      if (live) {
-        const float2* Ci = cinv + (size_t)list[s0 + sl] * r * r;
-        if (adj) {
-          for (int q = 0; q < r; ++q) y = cfma(Ci[q + (size_t)l * r], cs[sl][q], y);
-        } else {
-          for (int q = 0; q < r; ++q) y = cfma(Ci[l + (size_t)q * r], cs[sl][q], y);
-        }
-      }
-      ys[sl][l] = y;
-    }
+  for (int e = threadIdx.x; e < PST * r; e += WT) {
+    const int sl = e / r, l = e % r;
+    ys[sl][l] = s0 + sl < nact ? Yp[(size_t)(s0 + sl) * r + l] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   // thread = (row, group of PG systems): each entry of the row of A is
@@ -573,9 +608,11 @@ void launch_prec(lyap_seed* sd, const WoodState* ws, bool adjoint, const double*
   const float2* Bm = ws ? (adjoint ? ws->Nl : ws->Ml) : nullptr;
   k_prec_a<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, In, in_ss, Out, out_ss, r, Bm,
                                        ws ? ws->ldr : 0, ws ? ws->cpart : nullptr, B);
-  if (r > 0)
+  if (r > 0) {
+    k_prec_y<<<B, WT, 0, st>>>(list, count, adjoint ? 1 : 0, r, ws->cinv, ws->cpart, B, ntx);
     k_prec_b<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, Out, out_ss, r, A, ws->ldr,
-                                         ws->cinv, ws->cpart, B, ntx);
+                                         ws->cpart);
+  }
 }
 
 
@@ -732,7 +769,7 @@ int prec_apply(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* v
     case 8: launch_prec<T2, 8>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
     default: return LYAP_EINVAL;
   }
-  lyap_count_launch(ws ? 2 : 1);
+  lyap_count_launch(ws ? 3 : 1);
   // algorithmic bytes per system: read r, write z, read+write z again when r > 0
   const int r = ws ? ws->r : 0;
   const double N = (double)sd->n * sd->k;
