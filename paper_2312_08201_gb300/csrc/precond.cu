@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "cplx.cuh"
@@ -559,6 +560,70 @@ __global__ void __launch_bounds__(WT) k_prec_b(int n, const int* __restrict__ li
   }
 }
 
+// FP32 Krylov vectors: the two products of the apply run as GEMMs over all B
+// system columns (C = B^T Z and D = A Y), with the per-system steps around
+// them in the kernels below. Columns of systems that are not listed hold
+// whatever the vectors hold and are never read back.
+
+// y_b = Cap_b^{-1} c_b (Cap_b^{-T} for the adjoint) for the listed systems,
+// c_b = C[:, b]; one CTA per system slot, Cap^{-1} staged as in k_prec_y.
+__global__ void __launch_bounds__(WT) k_prec_ysys(const int* __restrict__ list, const int* __restrict__ count,
+                                                  int adj, int r, const float2* __restrict__ cinv,
+                                                  const float2* __restrict__ C, float2* __restrict__ Y) {
+  __shared__ float2 Cs[RMAX * (RMAX + 1)];
+  __shared__ float2 cs[RMAX];
+  __shared__ float2 ys[WT / RMAX][RMAX];
+  const int s = blockIdx.x;
+  if (s >= *count) return;
+  const int b = list[s];
+  const int rp = r | 1;
+  const float2* Ci = cinv + (size_t)b * r * r;
+  for (int e = threadIdx.x; e < r * r; e += WT) Cs[(e % r) + (e / r) * rp] = Ci[e];
+  for (int l = threadIdx.x; l < r; l += WT) cs[l] = C[(size_t)b * r + l];
+  __syncthreads();
+  constexpr int G = WT / RMAX;
+  const int l = threadIdx.x % RMAX, g = threadIdx.x / RMAX;
+  float2 y = make_float2(0.f, 0.f);
+  if (l < r) {
+    if (adj) {
+      for (int q = g; q < r; q += G) y = cfma(Cs[q + l * rp], cs[q], y);
+    } else {
+      for (int q = g; q < r; q += G) y = cfma(Cs[l + q * rp], cs[q], y);
+    }
+  }
+  ys[g][l] = y;
+  __syncthreads();
+  if (threadIdx.x < r) {
+    float2 t = ys[0][threadIdx.x];
+#pragma unroll
+    for (int u = 1; u < G; ++u) t = cadd(t, ys[u][threadIdx.x]);
+    Y[(size_t)b * r + threadIdx.x] = t;
+  }
+}
+
+// z_b += K_b^{-1} D[:, b] (K^T for the adjoint) for the listed systems; one
+// thread per (row j, system slot).
+template <int K>
+__global__ void __launch_bounds__(WT) k_prec_dsys(int n, const int* __restrict__ list, const int* __restrict__ count,
+                                                  const float2* __restrict__ Gd, int adj,
+                                                  const double* __restrict__ vinv, const float2* __restrict__ D,
+                                                  float2* __restrict__ Out, size_t out_ss) {
+  const int j = blockIdx.x * WT + threadIdx.x;
+  const int s = blockIdx.y;
+  if (j >= n || s >= *count) return;
+  const int b = list[s];
+  const size_t nk = (size_t)n * K;
+  float vb[K];
+  load_vb<K>(vinv, b, vb);
+  float2 x[K];
+#pragma unroll
+  for (int t = 0; t < K; ++t) x[t] = D[(size_t)b * nk + (size_t)t * n + j];
+  bsolve<K>(n, j, Gd, adj, vb, x);
+  float2* out = Out + (size_t)b * out_ss;
+#pragma unroll
+  for (int t = 0; t < K; ++t) out[(size_t)t * n + j] = cadd(out[(size_t)t * n + j], x[t]);
+}
+
 // Cap(v_b)^{-1} for systems b < B: Y_b = K_b^{-1} Nl (k_kinv_nl), then
 // Cap_b - I = -Ml^T Y_b for all systems of a chunk in one strided-batched
 // CGEMM (FP32, cuBLAS), then one Gauss-Jordan inversion per system. Chunks
@@ -596,9 +661,16 @@ int launch_cap_build(lyap_seed* sd, int r, int B, const double* vinv, const Wood
   return LYAP_OK;
 }
 
+// Compute type of the apply's two GEMMs: FP32 throughout. The basis is
+// flexible (Z = P^{-1} V is stored), so the preconditioner's rounding only
+// shapes the convergence rate; but where the rank-p Woodbury correction is
+// nearly exact (a coupling of rank <= p) TF32 products (11 bits) cost that
+// exactness and the inner iterations rise by half.
+constexpr cublasComputeType_t kPrecGemmCompute = CUBLAS_COMPUTE_32F;
+
 template <typename T2, int K>
-void launch_prec(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* vinv, const int* list,
-                 const int* count, int B, const T2* In, size_t in_ss, T2* Out, size_t out_ss, cudaStream_t st) {
+int launch_prec(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* vinv, const int* list,
+                const int* count, int B, const T2* In, size_t in_ss, T2* Out, size_t out_ss, cudaStream_t st) {
   constexpr int RT = PrecTile<K>::RT;
   const int n = sd->n;
   const int r = ws ? ws->r : 0;
@@ -606,13 +678,45 @@ void launch_prec(lyap_seed* sd, const WoodState* ws, bool adjoint, const double*
   const dim3 grid(ntx, (B + PST - 1) / PST);
   const float2* A = ws ? (adjoint ? ws->Ml : ws->Nl) : nullptr;
   const float2* Bm = ws ? (adjoint ? ws->Nl : ws->Ml) : nullptr;
+  if constexpr (std::is_same<T2, float2>::value) {
+    if (r > 0) {
+      const int nk = n * K;
+      float2* C = ws->cpart;               // r x B
+      float2* Y = C + (size_t)r * B;        // r x B
+      float2* D = Y + (size_t)r * B;        // nk x B
+      k_prec_a<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, In, in_ss, Out, out_ss,
+                                           0, nullptr, 0, nullptr, B);
+      lyap_ctx* ctx = sd->ctx;
+      const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+      {
+        std::lock_guard<std::mutex> lk(ctx->handle_mu);  // library handles are shared by the context's users
+        LY_BLAS(cublasSetStream(ctx->blas, st));
+        LY_BLAS(cublasGemmEx(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, r, B, nk, &one, Bm, CUDA_C_32F, ws->ldr, Out,
+                             CUDA_C_32F, (int)out_ss, &zero, C, CUDA_C_32F, r, kPrecGemmCompute, CUBLAS_GEMM_DEFAULT));
+      }
+      k_prec_ysys<<<B, WT, 0, st>>>(list, count, adjoint ? 1 : 0, r, ws->cinv, C, Y);
+      {
+        std::lock_guard<std::mutex> lk(ctx->handle_mu);
+        LY_BLAS(cublasSetStream(ctx->blas, st));
+        LY_BLAS(cublasGemmEx(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, nk, B, r, &one, A, CUDA_C_32F, ws->ldr, Y,
+                             CUDA_C_32F, r, &zero, D, CUDA_C_32F, nk, kPrecGemmCompute, CUBLAS_GEMM_DEFAULT));
+      }
+      k_prec_dsys<K><<<dim3((n + WT - 1) / WT, B), WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, D,
+                                                                Out, out_ss);
+      lyap_count_launch(3);
+      return LYAP_OK;
+    }
+  }
   k_prec_a<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, In, in_ss, Out, out_ss, r, Bm,
                                        ws ? ws->ldr : 0, ws ? ws->cpart : nullptr, B);
+  lyap_count_launch();
   if (r > 0) {
     k_prec_y<<<B, WT, 0, st>>>(list, count, adjoint ? 1 : 0, r, ws->cinv, ws->cpart, B, ntx);
     k_prec_b<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, Out, out_ss, r, A, ws->ldr,
                                          ws->cpart);
+    lyap_count_launch(2);
   }
+  return LYAP_OK;
 }
 
 
@@ -723,7 +827,10 @@ int wood_bind(lyap_seed* sd, int r, int B, const float2* cinv_full, const int* i
 
 size_t wood_part_count(int n, int k, int B, int r) {
   const int RT = k <= 4 ? PrecTile<1>::RT : PrecTile<8>::RT;
-  return (size_t)((n + RT - 1) / RT) * (size_t)B * (size_t)std::max(r, 0);
+  r = std::max(r, 0);
+  const size_t parts = (size_t)((n + RT - 1) / RT) * (size_t)B * (size_t)r;  // row-tile partials (FP64 vectors)
+  const size_t gemm = ((size_t)2 * r + (size_t)n * k) * (size_t)B;          // C, Y, D of the GEMM form
+  return r > 0 ? std::max(parts, gemm) : 0;
 }
 
 int wood_prepare(lyap_seed* sd, int r, int B, const double* vinv, bool /*adjoint*/, WoodState& ws, cudaStream_t st) {
@@ -758,18 +865,19 @@ int prec_apply(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* v
                const int* count, int B, const T2* In, size_t in_ss, T2* Out, size_t out_ss, cudaStream_t st) {
   if (ws && ws->r <= 0) ws = nullptr;
   const int ph = prof_begin(PK_PRECOND, st);
+  int rc = LYAP_OK;
   switch (sd->k) {
-    case 1: launch_prec<T2, 1>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
-    case 2: launch_prec<T2, 2>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
-    case 3: launch_prec<T2, 3>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
-    case 4: launch_prec<T2, 4>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
-    case 5: launch_prec<T2, 5>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
-    case 6: launch_prec<T2, 6>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
-    case 7: launch_prec<T2, 7>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
-    case 8: launch_prec<T2, 8>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 1: rc = launch_prec<T2, 1>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 2: rc = launch_prec<T2, 2>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 3: rc = launch_prec<T2, 3>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 4: rc = launch_prec<T2, 4>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 5: rc = launch_prec<T2, 5>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 6: rc = launch_prec<T2, 6>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 7: rc = launch_prec<T2, 7>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
+    case 8: rc = launch_prec<T2, 8>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
     default: return LYAP_EINVAL;
   }
-  lyap_count_launch(ws ? 3 : 1);
+  if (rc != LYAP_OK) return rc;
   // algorithmic bytes per system: read r, write z, read+write z again when r > 0
   const int r = ws ? ws->r : 0;
   const double N = (double)sd->n * sd->k;
