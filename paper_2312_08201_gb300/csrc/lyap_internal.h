@@ -122,6 +122,11 @@ struct lyap_seed {
   int device = 0;  // kept here so the seed can be released after its context
   int n = 0, k = 0, g = 0;
   int real_path = 0;
+  // 1 when the eigen-decomposition is exactly real (symmetric A0): lam, Qp,
+  // Qi and every projected factor have zero imaginary parts, so the mixed
+  // path's Cauchy products use the real n x n matrix, with the real and
+  // imaginary parts of each panel column as two columns.
+  int real_arith = 0;
   double cond_Q = 0, f0 = 0, max_re = 0, min_sum = 0;
   // Eigen-data (P convention): A0^T = Qp diag(lam) Qp^{-1}.
   DevBuf<double2> lam;  // n

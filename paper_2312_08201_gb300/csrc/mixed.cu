@@ -31,6 +31,12 @@
 
 struct MixedState {
   int mpad = 0, kpad = 0;
+  // Layout of the Cauchy products. rs = 2: the complex matrix in real-split
+  // form (rows / K entries 2i, 2i+1 = Re, Im of index i), one panel column
+  // per (system, p, t). rs = 1 (exactly real eigen-data): the real n x n
+  // matrix, and cm = 2 panel columns per (system, p, t), its real and
+  // imaginary parts; half the tensor work of the split form.
+  int rs = 2, cm = 1;
   DevBuf<__nv_bfloat16> Ahi, Alo;  // mpad x kpad
   DevBuf<float2> Ub32, Vb32, Gd32;
   int ncap = 0;
@@ -66,16 +72,17 @@ struct MixedState {
 
 namespace {
 
-__global__ void k_build_A(int n, const double2* __restrict__ lam, int mpad, int kpad, __nv_bfloat16* __restrict__ Ah,
-                          __nv_bfloat16* __restrict__ Al) {
+__global__ void k_build_A(int n, const double2* __restrict__ lam, int mpad, int kpad, int rs,
+                          __nv_bfloat16* __restrict__ Ah, __nv_bfloat16* __restrict__ Al) {
   const size_t total = (size_t)mpad * kpad;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(idx / kpad), c = (int)(idx % kpad);
-    const int i = r >> 1, j = c >> 1;
+    const int i = r / rs, j = c / rs;
     double v = 0.0;
     if (i < n && j < n) {
       double2 L = crcp(cadd(lam[i], lam[j]));
-      if ((r & 1) == 0) v = (c & 1) == 0 ? L.x : -L.y;
+      if (rs == 1) v = L.x;
+      else if ((r & 1) == 0) v = (c & 1) == 0 ? L.x : -L.y;
       else v = (c & 1) == 0 ? L.y : L.x;
     }
     __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
@@ -91,10 +98,11 @@ __global__ void k_to_f32(size_t count, const double2* __restrict__ in, float2* _
 }
 
 // Panel columns col = slot*k^2 + p*k + t: Z[j] = W_slot[j, p] * P2[j, t],
-// stored split (hi, lo) and real-split along K (2j, 2j+1).
+// stored split (hi, lo); rs = 2: real-split along K (2j, 2j+1) in column
+// col; rs = 1: Re Z in column 2 col and Im Z in column 2 col + 1.
 template <typename T2>
 __global__ void k_panel(int n, int k, const int* __restrict__ list, const int* __restrict__ count, int nsys,
-                        const T2* __restrict__ In, size_t in_ss, const float2* __restrict__ P2, int kpad,
+                        const T2* __restrict__ In, size_t in_ss, const float2* __restrict__ P2, int kpad, int rs,
                         __nv_bfloat16* __restrict__ Bh, __nv_bfloat16* __restrict__ Bl) {
   const int slot = blockIdx.y;
   const int ns = count ? *count : nsys;
@@ -108,12 +116,14 @@ __global__ void k_panel(int n, int k, const int* __restrict__ list, const int* _
     const float2 wf = make_float2((float)w.x, (float)w.y);
     for (int t = 0; t < k; ++t) {
       const float2 z = cmul(wf, P2[(size_t)t * n + j]);
-      const size_t o = (size_t)(slot * kk + p * k + t) * kpad + 2 * j;
+      const size_t col = (size_t)(slot * kk + p * k + t);
+      const size_t o = rs == 2 ? col * kpad + 2 * j : 2 * col * kpad + j;  // Re of z
+      const size_t oi = rs == 2 ? o + 1 : o + kpad;                         // Im of z
       const __nv_bfloat16 hr = __float2bfloat16_rn(z.x), hi = __float2bfloat16_rn(z.y);
       Bh[o] = hr;
-      Bh[o + 1] = hi;
+      Bh[oi] = hi;
       Bl[o] = __float2bfloat16_rn(z.x - __bfloat162float(hr));
-      Bl[o + 1] = __float2bfloat16_rn(z.y - __bfloat162float(hi));
+      Bl[oi] = __float2bfloat16_rn(z.y - __bfloat162float(hi));
     }
   }
 }
@@ -121,7 +131,7 @@ __global__ void k_panel(int n, int k, const int* __restrict__ list, const int* _
 // out[i, t] = sum_p P1[i,p] (Lc Z)[i, (slot,p,t)] + sum_p W[i,p] Gd(i,p,t); then T or C0.
 template <typename T2>
 __global__ void k_epi(int n, int k, const int* __restrict__ list, const int* __restrict__ count, int nsys,
-                      const float* __restrict__ D, int ldd, const T2* __restrict__ In, size_t in_ss,
+                      const float* __restrict__ D, int ldd, int rs, const T2* __restrict__ In, size_t in_ss,
                       const float2* __restrict__ P1, const float2* __restrict__ Gd, int gT,
                       const double* __restrict__ vinv, int mode, T2* __restrict__ Out, size_t out_ss) {
   const int slot = blockIdx.y;
@@ -138,7 +148,9 @@ __global__ void k_epi(int n, int k, const int* __restrict__ list, const int* __r
   for (int t = 0; t < k; ++t) {
     float2 o = make_float2(0.f, 0.f);
     for (int p = 0; p < k; ++p) {
-      o = cfma(P1[(size_t)p * n + i], D2[(size_t)(slot * kk + p * k + t) * ld2 + i], o);
+      const size_t col = (size_t)(slot * kk + p * k + t);
+      const float2 lz = rs == 2 ? D2[col * ld2 + i] : make_float2(D[2 * col * ldd + i], D[(2 * col + 1) * ldd + i]);
+      o = cfma(P1[(size_t)p * n + i], lz, o);
       const size_t g = gT ? ((size_t)(t * k + p) * n + i) : ((size_t)(p * k + t) * n + i);
       o = cfma(w[p], Gd[g], o);
     }
@@ -208,22 +220,23 @@ int mixed_apply(lyap_seed* sd, bool adjoint, const double* vinv, const int* list
                 const T2* In, size_t in_ss, T2* Out, size_t out_ss, int mode, cudaStream_t st) {
   MixedState& ms = *sd->mixed;
   const int n = sd->n, k = sd->k, kk = k * k;
-  LY_TRY(ensure_cols(sd, nsys * kk));
+  LY_TRY(ensure_cols(sd, nsys * kk * ms.cm));
   const float2* P1 = adjoint ? ms.Vb32.p : ms.Ub32.p;
   const float2* P2 = adjoint ? ms.Ub32.p : ms.Vb32.p;
   dim3 g((n + 255) / 256, nsys);
   const int pp = prof_begin(PK_PANEL, st);
-  k_panel<T2><<<g, 256, 0, st>>>(n, k, list, count, nsys, In, in_ss, P2, ms.kpad, ms.Bhi.p, ms.Blo.p);
+  k_panel<T2><<<g, 256, 0, st>>>(n, k, list, count, nsys, In, in_ss, P2, ms.kpad, ms.rs, ms.Bhi.p, ms.Blo.p);
   lyap_count_launch();
   prof_end(pp, st, 0.0, (double)n * k * sizeof(T2) + 8.0 * n * kk, count ? 0 : nsys, count);
   LY_CUDA(cudaGetLastError());
-  // algorithmic work per system: 2 (real) x (2n)^2 x k^2 MACs per product, three products
+  // tensor work per system: 2 (real) x (rs n)^2 x cm k^2 MACs per product, three products
   const int ph = prof_begin(PK_TCGEMM, st);
-  LY_TRY(tc::launch(ms.maps, ms.D.p, ms.mpad, 2 * n, ms.mpad, ms.kpad, count, kk, nsys * kk, nsys * kk, ms.err.p, st,
-                    ms.inject_wait));
-  prof_end(ph, st, 3.0 * 2.0 * (2.0 * n) * (2.0 * n) * kk, 0.0, count ? 0 : nsys, count);
+  const int cols = kk * ms.cm;
+  LY_TRY(tc::launch(ms.maps, ms.D.p, ms.mpad, ms.rs * n, ms.mpad, ms.kpad, count, cols, nsys * cols, nsys * cols,
+                    ms.err.p, st, ms.inject_wait));
+  prof_end(ph, st, 3.0 * 2.0 * (double)(ms.rs * n) * (ms.rs * n) * cols, 0.0, count ? 0 : nsys, count);
   const int pe = prof_begin(PK_EPI32, st);
-  k_epi<T2><<<g, 256, 0, st>>>(n, k, list, count, nsys, ms.D.p, ms.mpad, In, in_ss, P1, ms.Gd32.p, adjoint ? 1 : 0,
+  k_epi<T2><<<g, 256, 0, st>>>(n, k, list, count, nsys, ms.D.p, ms.mpad, ms.rs, In, in_ss, P1, ms.Gd32.p, adjoint ? 1 : 0,
                                vinv, mode, Out, out_ss);
   lyap_count_launch();
   prof_end(pe, st, 0.0, (double)kk * n * 8.0 + 4.0 * n * k * sizeof(T2), count ? 0 : nsys, count);
@@ -244,7 +257,7 @@ int ensure_refine(lyap_seed* sd, int Bc) {
   LY_TRY(ms.sw.alloc(Bc));
   LY_TRY(ms.panel_ff.alloc((size_t)Bc * sd->k * sd->k * sd->n));
   if (ms.oz_ok) {
-    const int ncap = ((Bc * sd->k * sd->k + oz::BN - 1) / oz::BN) * oz::BN;
+    const int ncap = ((Bc * sd->k * sd->k * ms.cm + oz::BN - 1) / oz::BN) * oz::BN;
     LY_TRY(ms.ozB.alloc((size_t)oz::NS * ncap * ms.kpad));
     LY_TRY(ms.ozEB.alloc(ncap));
     LY_TRY(ms.ozD.alloc((size_t)ncap * ms.mpad));
@@ -304,7 +317,7 @@ int refine(lyap_seed* sd, int Bc, const double* vinv, const double2* rhs, double
       a.nsys = nact;
       if (o.residual == LYAP_RESID_FP64) LY_TRY(capmv64_launch(a, st));
       else if (o.residual == LYAP_RESID_TC && ms.oz_ok)
-        LY_TRY(oz::residual(a, ms.ozMapA, ms.ozEA.p, ms.mpad, ms.kpad, ms.ozPanel, ms.err.p, st));
+        LY_TRY(oz::residual(a, ms.ozMapA, ms.ozEA.p, ms.mpad, ms.kpad, ms.rs, ms.ozPanel, ms.err.p, st));
       else LY_TRY(capmv_df_launch(a, ms.Lff.p, ms.lc_scale, ms.p_scale, ms.sw.p, ms.panel_ff.p, st));
       kry::k_norms<double2><<<Bc, kry::NT, 0, st>>>(N, Bc, ms.R64.p, N, ms.norms.p);
       lyap_count_launch();
@@ -379,11 +392,13 @@ void lyap_mixed_free(lyap_seed* sd) {
 int lyap_mixed_prepare(lyap_seed* sd, cudaStream_t st) {
   std::unique_ptr<MixedState> ms(new MixedState());
   const int n = sd->n, k = sd->k;
-  ms->mpad = ((2 * n + tc::BM - 1) / tc::BM) * tc::BM;
-  ms->kpad = ((2 * n + tc::BK - 1) / tc::BK) * tc::BK;
+  ms->rs = sd->real_arith ? 1 : 2;
+  ms->cm = sd->real_arith ? 2 : 1;
+  ms->mpad = ((ms->rs * n + tc::BM - 1) / tc::BM) * tc::BM;
+  ms->kpad = ((ms->rs * n + tc::BK - 1) / tc::BK) * tc::BK;
   LY_TRY(ms->Ahi.alloc((size_t)ms->mpad * ms->kpad));
   LY_TRY(ms->Alo.alloc((size_t)ms->mpad * ms->kpad));
-  k_build_A<<<gx((size_t)ms->mpad * ms->kpad) * 16, 256, 0, st>>>(n, sd->lam.p, ms->mpad, ms->kpad, ms->Ahi.p,
+  k_build_A<<<gx((size_t)ms->mpad * ms->kpad) * 16, 256, 0, st>>>(n, sd->lam.p, ms->mpad, ms->kpad, ms->rs, ms->Ahi.p,
                                                                   ms->Alo.p);
   lyap_count_launch();
   LY_CUDA(cudaGetLastError());
@@ -417,7 +432,7 @@ int lyap_mixed_prepare(lyap_seed* sd, cudaStream_t st) {
   {
     LY_TRY(ms->ozA.alloc((size_t)oz::NS * ms->mpad * ms->kpad));
     LY_TRY(ms->ozEA.alloc(ms->mpad));
-    LY_TRY(oz::slice_A(n, sd->lam.p, ms->mpad, ms->kpad, ms->ozA.p, ms->ozEA.p, st));
+    LY_TRY(oz::slice_A(n, sd->lam.p, ms->mpad, ms->kpad, ms->rs, ms->ozA.p, ms->ozEA.p, st));
     LY_TRY(oz::make_map(&ms->ozMapA, ms->ozA.p, oz::NS * ms->mpad, ms->kpad, oz::BM));
     ms->oz_ok = true;
   }
@@ -718,7 +733,7 @@ int lyap_engine_step(lyap_seed* sd, MixedEngine& e, const lyap_opts& o, cudaStre
     a.nsys = no;
     if (o.residual == LYAP_RESID_FP64) LY_TRY(capmv64_launch(a, st));
     else if (o.residual == LYAP_RESID_TC && ms.oz_ok)
-      LY_TRY(oz::residual(a, ms.ozMapA, ms.ozEA.p, ms.mpad, ms.kpad, ms.ozPanel, ms.err.p, st));
+      LY_TRY(oz::residual(a, ms.ozMapA, ms.ozEA.p, ms.mpad, ms.kpad, ms.rs, ms.ozPanel, ms.err.p, st));
     else LY_TRY(capmv_df_launch(a, ms.Lff.p, ms.lc_scale, ms.p_scale, ms.sw.p, ms.panel_ff.p, st));
     k_engine_norms<<<no, kry::NT, 0, st>>>(N, ms.act.p, no, ms.R64.p, e.rout.p);
     lyap_count_launch();
@@ -878,7 +893,7 @@ extern "C" int lyap_test_apply(lyap_seed* sd, int nsys, const double* v, const d
     } else if (precision == LYAP_TEST_TC) {
       MixedState& ms = *sd->mixed;
       if (!ms.oz_ok) return LYAP_EINVAL;
-      const int ncap = ((nsys * k * k + oz::BN - 1) / oz::BN) * oz::BN;
+      const int ncap = ((nsys * k * k * ms.cm + oz::BN - 1) / oz::BN) * oz::BN;
       DevBuf<__nv_bfloat16> Bd;
       DevBuf<int> eB;
       DevBuf<float2> Dd;
@@ -891,7 +906,7 @@ extern "C" int lyap_test_apply(lyap_seed* sd, int nsys, const double* v, const d
       pn.D = Dd.p;
       pn.ncap = ncap;
       LY_TRY(oz::make_map(&pn.mapB, Bd.p, oz::NS * ncap, ms.kpad, oz::BN));
-      LY_TRY(oz::residual(a, ms.ozMapA, ms.ozEA.p, ms.mpad, ms.kpad, pn, ms.err.p, st));
+      LY_TRY(oz::residual(a, ms.ozMapA, ms.ozEA.p, ms.mpad, ms.kpad, ms.rs, pn, ms.err.p, st));
       LY_CUDA(cudaStreamSynchronize(st));
     } else {
       DevBuf<double> sw;

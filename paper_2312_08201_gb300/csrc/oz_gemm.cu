@@ -67,14 +67,15 @@ __device__ __forceinline__ void write_digits(double x, __nv_bfloat16* S, size_t 
   }
 }
 
-__global__ void __launch_bounds__(256) k_slice_A(int n, const double2* __restrict__ lam, int mpad, int kpad,
+__global__ void __launch_bounds__(256) k_slice_A(int n, const double2* __restrict__ lam, int mpad, int kpad, int rs,
                                                  __nv_bfloat16* __restrict__ S, int* __restrict__ eA) {
   __shared__ double red[256];
   const int r = blockIdx.x;
-  const int rows = 2 * n;
+  const int rows = rs * n;
   auto val = [&](int c) -> double {
     if (r >= rows || c >= rows) return 0.0;
-    const double2 L = crcp(cadd(lam[r >> 1], lam[c >> 1]));
+    const double2 L = crcp(cadd(lam[r / rs], lam[c / rs]));
+    if (rs == 1) return L.x;
     if ((r & 1) == 0) return (c & 1) == 0 ? L.x : -L.y;
     return (c & 1) == 0 ? L.y : L.x;
   };
@@ -99,30 +100,33 @@ __device__ __forceinline__ void write_digits_int(long long q, __nv_bfloat16* S, 
   }
 }
 
-// Panel digits of the listed systems: column slot * k^2 + p k + t holds
-// W_b[:, p] o P2[:, t], real-split along K. The column is formed once in
-// shared memory; its digits come from one rounding to 48 bits and integer
-// digit extraction (GB300's FP64 pipe is narrow).
-__global__ void __launch_bounds__(256) k_slice_B(CapArgs64 a, int ncap, int kpad, __nv_bfloat16* __restrict__ S,
-                                                 int* __restrict__ eB) {
+// Panel digits of the listed systems: W_b[:, p] o P2[:, t] for (p, t) =
+// pt, real-split along K in column slot * k^2 + pt (rs = 2), or its real and
+// imaginary parts in columns 2 (slot * k^2 + pt) and 2 (slot * k^2 + pt) + 1
+// (rs = 1). The column is formed once in shared memory; its digits come from
+// one rounding to 48 bits and integer digit extraction (GB300's FP64 pipe is
+// narrow).
+__global__ void __launch_bounds__(256) k_slice_B(CapArgs64 a, int ncap, int kpad, int rs,
+                                                 __nv_bfloat16* __restrict__ S, int* __restrict__ eB) {
   extern __shared__ double zcol[];  // kpad
   __shared__ double red[256];
   const int nsys = a.count ? *a.count : a.nsys;
   const int slot = blockIdx.x;
   if (slot >= nsys) return;
   const int b = a.list ? a.list[slot] : slot;
-  const int n = a.n, k = a.k, kk = k * k, rows = 2 * n;
+  const int n = a.n, k = a.k, kk = k * k, rows = rs * n, cm = 3 - rs;
   const double2* Wb = a.W + (size_t)b * a.ldw;
-  for (int pt = 0; pt < kk; ++pt) {
+  for (int q = 0; q < kk * cm; ++q) {
+    const int pt = q / cm, h = q % cm;  // h: 1 for the imaginary-part column (rs = 1)
     const int p = pt / k, t = pt % k;
-    const int col = slot * kk + pt;
+    const int col = slot * kk * cm + q;
     double mx = 0.0;
     for (int c = threadIdx.x; c < kpad; c += blockDim.x) {
       double v = 0.0;
       if (c < rows) {
-        const int j = c >> 1;
+        const int j = c / rs;
         const double2 z = cmul(Wb[(size_t)p * n + j], a.P2[(size_t)t * n + j]);
-        v = (c & 1) ? z.y : z.x;
+        v = (rs == 2 ? (c & 1) : h) ? z.y : z.x;
       }
       zcol[c] = v;
       mx = fmax(mx, fabs(v));
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(192, 1)
 
 // T(v) W (or the residual) from the sliced product: S_{p,t}[i] for the
 // listed systems, then the same FP64 epilogue as the other residual kernels.
-__global__ void __launch_bounds__(128) k_oz_epi(CapArgs64 a, const float2* __restrict__ D, int ldd,
+__global__ void __launch_bounds__(128) k_oz_epi(CapArgs64 a, const float2* __restrict__ D, int ldd, int rs,
                                                 const int* __restrict__ eA, const int* __restrict__ eB) {
   const int nsys = a.count ? *a.count : a.nsys;
   const int slot = blockIdx.y;
@@ -298,14 +302,18 @@ __global__ void __launch_bounds__(128) k_oz_epi(CapArgs64 a, const float2* __res
   if (i >= n) return;
   const int b = a.list ? a.list[slot] : slot;
   const double2* Wb = a.W + (size_t)b * a.ldw;
-  const int er = eA[2 * i], ei = eA[2 * i + 1];
+  const int er = rs == 2 ? eA[2 * i] : eA[i], ei = rs == 2 ? eA[2 * i + 1] : eA[i];
   for (int t = 0; t < k; ++t) {
     double2 o = make_double2(0.0, 0.0);
     for (int p = 0; p < k; ++p) {
       const int col = slot * kk + p * k + t;
-      const float2 dr = D[(size_t)col * ldd + 2 * i], di = D[(size_t)col * ldd + 2 * i + 1];
-      const int ec = eB[col] - 12;
-      const double2 S = make_double2(ldexp((double)dr.x + (double)dr.y, er + ec), ldexp((double)di.x + (double)di.y, ei + ec));
+      // real part: row 2i of column col (rs = 2) or row i of column 2 col (rs = 1)
+      const size_t xr = rs == 2 ? (size_t)col * ldd + 2 * i : (size_t)(2 * col) * ldd + i;
+      const size_t xi = rs == 2 ? xr + 1 : xr + ldd;
+      const int cr = rs == 2 ? col : 2 * col, ci = rs == 2 ? col : 2 * col + 1;
+      const float2 dr = D[xr], di = D[xi];
+      const double2 S = make_double2(ldexp((double)dr.x + (double)dr.y, er + eB[cr] - 12),
+                                     ldexp((double)di.x + (double)di.y, ei + eB[ci] - 12));
       o = cfma(a.P1[(size_t)p * n + i], S, o);
       const size_t gidx = a.gT ? ((size_t)(t * k + p) * n + i) : ((size_t)(p * k + t) * n + i);
       o = cfma(Wb[(size_t)p * n + i], a.Gd[gidx], o);
@@ -321,9 +329,9 @@ __global__ void __launch_bounds__(128) k_oz_epi(CapArgs64 a, const float2* __res
 
 }  // namespace
 
-int slice_A(int n, const double2* lam, int mpad, int kpad, void* S, int* eA, cudaStream_t st) {
-  if (mpad % BM != 0 || kpad % BK != 0) return LYAP_EINVAL;
-  k_slice_A<<<mpad, 256, 0, st>>>(n, lam, mpad, kpad, reinterpret_cast<__nv_bfloat16*>(S), eA);
+int slice_A(int n, const double2* lam, int mpad, int kpad, int rs, void* S, int* eA, cudaStream_t st) {
+  if (mpad % BM != 0 || kpad % BK != 0 || (rs != 1 && rs != 2)) return LYAP_EINVAL;
+  k_slice_A<<<mpad, 256, 0, st>>>(n, lam, mpad, kpad, rs, reinterpret_cast<__nv_bfloat16*>(S), eA);
   lyap_count_launch();
   LY_CUDA(cudaGetLastError());
   return LYAP_OK;
@@ -351,34 +359,35 @@ int make_map(CUtensorMap* map, const void* base, int rows_total, int kpad, int b
   return LYAP_OK;
 }
 
-int residual(const CapArgs64& a, const CUtensorMap& mapA, const int* eA, int mpad, int kpad, Panel& pn, int* err,
-             cudaStream_t st) {
-  if (a.k < 1 || a.k > 8) return LYAP_EINVAL;
+int residual(const CapArgs64& a, const CUtensorMap& mapA, const int* eA, int mpad, int kpad, int rs, Panel& pn,
+             int* err, cudaStream_t st) {
+  if (a.k < 1 || a.k > 8 || (rs != 1 && rs != 2)) return LYAP_EINVAL;
   if (a.nsys <= 0) return LYAP_OK;
+  const int cm = 3 - rs;  // panel columns per (system, p, t)
   const int kk = a.k * a.k;
-  const int ncols_cap = a.nsys * kk;
+  const int ncols_cap = a.nsys * kk * cm;
   if (ncols_cap > pn.ncap) return LYAP_EINVAL;
   LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_oz_gemm), SMEM_BYTES));
   // one column of kpad doubles in shared memory (51 KB at n = 3200)
   LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_slice_B), sizeof(double) * kpad));
-  k_slice_B<<<a.nsys, 256, sizeof(double) * kpad, st>>>(a, pn.ncap, kpad, reinterpret_cast<__nv_bfloat16*>(pn.S),
+  k_slice_B<<<a.nsys, 256, sizeof(double) * kpad, st>>>(a, pn.ncap, kpad, rs, reinterpret_cast<__nv_bfloat16*>(pn.S),
                                                          pn.eB);
   lyap_count_launch();
   LY_CUDA(cudaGetLastError());
-  // tensor work per system: NS (NS + 1) / 2 BF16 products of the (2n x 2n) x (2n x k^2) real-split GEMM
+  // tensor work per system: NS (NS + 1) / 2 BF16 products of the (rs n x rs n) x (rs n x cm k^2) GEMM
   const int ph = prof_begin(PK_OZGEMM, st);
   dim3 grid(mpad / BM, (ncols_cap + BN - 1) / BN);
   // K in chunks of at most KCHUNK, each summed exactly in FP32 and added to
   // the previous chunks' float-float results (one chunk for 2n <= KCHUNK)
   for (int k0 = 0; k0 < kpad; k0 += KCHUNK) {
     const int kt = (std::min(KCHUNK, kpad - k0)) / BK;
-    k_oz_gemm<<<grid, 192, SMEM_BYTES, st>>>(mapA, pn.mapB, pn.D, mpad, 2 * a.n, mpad, pn.ncap, k0 / BK, kt,
-                                            k0 > 0 ? 1 : 0, a.count, kk, ncols_cap, err);
+    k_oz_gemm<<<grid, 192, SMEM_BYTES, st>>>(mapA, pn.mapB, pn.D, mpad, rs * a.n, mpad, pn.ncap, k0 / BK, kt,
+                                            k0 > 0 ? 1 : 0, a.count, kk * cm, ncols_cap, err);
     lyap_count_launch();
   }
-  prof_end(ph, st, PAIRS * 2.0 * (2.0 * a.n) * (2.0 * a.n) * kk, 0.0, a.count ? 0 : a.nsys, a.count);
+  prof_end(ph, st, PAIRS * 2.0 * (double)(rs * a.n) * (rs * a.n) * kk * cm, 0.0, a.count ? 0 : a.nsys, a.count);
   LY_CUDA(cudaGetLastError());
-  k_oz_epi<<<dim3((a.n + 127) / 128, a.nsys), 128, 0, st>>>(a, pn.D, mpad, eA, pn.eB);
+  k_oz_epi<<<dim3((a.n + 127) / 128, a.nsys), 128, 0, st>>>(a, pn.D, mpad, rs, eA, pn.eB);
   lyap_count_launch();
   LY_CUDA(cudaGetLastError());
   return LYAP_OK;

@@ -2,8 +2,10 @@
 // integer slicing (the splitting scheme of Ozaki et al. for error-free
 // matrix products), used for the mixed path's refinement residual.
 //
-// Every row r of the real-split Cauchy matrix A (2n x 2n) and every panel
-// column c of B (one (system, p, t) column, K = 2n) is scaled by a power of
+// Every row r of the real-split Cauchy matrix A (2n x 2n; for exactly real
+// eigenvalues the real n x n matrix, with the real and imaginary parts of a
+// panel column as two columns) and every panel column c of B (one
+// (system, p, t) column, K = 2n or n) is scaled by a power of
 // two so that its entries lie in [-1/2, 1/2], then written as NS = 8
 // balanced base-64 digits:
 //     A[r][k] = 2^eA[r] sum_s a_s[r][k] 64^-(s+1),   a_s in [-32, 32],
@@ -35,9 +37,10 @@ constexpr int STAGES = 2;
 constexpr int KMAX = 2046;       // largest K with exact FP32 accumulation
 constexpr int KCHUNK = 2016;     // K per accumulation chunk (a multiple of BK, at most KMAX)
 
-// Digits of the real-split Cauchy matrix of a seed (rows mpad, K kpad):
-// S: NS x mpad x kpad BF16 (slice-major), eA: mpad exponents.
-int slice_A(int n, const double2* lam, int mpad, int kpad, void* S, int* eA, cudaStream_t st);
+// Digits of the Cauchy matrix of a seed (rows mpad, K kpad): real-split
+// (2n x 2n, rs = 2) or, for exactly real eigenvalues, the real n x n matrix
+// (rs = 1). S: NS x mpad x kpad BF16 (slice-major), eA: mpad exponents.
+int slice_A(int n, const double2* lam, int mpad, int kpad, int rs, void* S, int* eA, cudaStream_t st);
 
 // Operand maps (64-byte swizzle, box BK x rows) over slice-stacked matrices.
 int make_map(CUtensorMap* map, const void* base, int rows_total, int kpad, int box_rows);
@@ -53,8 +56,10 @@ struct Panel {
 // r = rhs - T(v) W (CAP_RESID) or T(v) W (CAP_T) for the listed systems of a
 // (n, k, W, P1, P2, Gd, vinv, rhs, out, list, count): digits of the panel,
 // the tensor-core product, and the FP64 epilogue. mapA/eA: the seed's
-// digits; err: device flag for an expired bounded wait.
-int residual(const CapArgs64& a, const CUtensorMap& mapA, const int* eA, int mpad, int kpad, Panel& pn,
+// digits, in the layout rs of slice_A; with rs = 1 every panel column is two
+// columns (real and imaginary parts), so pn holds 2 k^2 columns per system;
+// err: device flag for an expired bounded wait.
+int residual(const CapArgs64& a, const CUtensorMap& mapA, const int* eA, int mpad, int kpad, int rs, Panel& pn,
              int* err, cudaStream_t st);
 
 }  // namespace oz

@@ -286,6 +286,7 @@ int lyap_seed_build(lyap_ctx* ctx, lyap_seed* sd, const double* A0, const double
     k_from_symmetric<<<grid_for(nn), 256, 0, st>>>(n, Vr.p, w.p, sd->Qp.p, sd->Qi.p, sd->lam.p);
     lyap_count_launch();
     LY_CUDA(cudaGetLastError());
+    sd->real_arith = 1;
   } else {
     // ---- eig(A_p), A_p = A0^T (complex FP64, right eigenvectors) ----------
     k_transpose_to_complex<<<grid_for(nn), 256, 0, st>>>(n, A0, W1.p); lyap_count_launch();

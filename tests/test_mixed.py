@@ -288,3 +288,65 @@ def test_sliced_operator_in_k_chunks(ctx, n, k):
         assert all(i["status"] == 0 for i in info)
         ref = np.array([oracle.trace_EX(A0, U, V, G, np.eye(n), x) for x in vs[:2]])
         assert rel_err(f[:2], ref).max() <= TOL_MIXED
+
+
+def symmetric_problem(seed, n, k, g):
+    """A0 = Q diag(lam) Q^T made exactly symmetric, so the seed's
+    eigen-decomposition is exactly real."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = -rng.uniform(0.05, 3.0, n)
+    A0 = (Q * lam) @ Q.T
+    A0 = (A0 + A0.T) / 2
+    U = rng.standard_normal((n, k)) * 0.3
+    V = rng.standard_normal((n, k)) * 0.3
+    G = rng.standard_normal((n, g))
+    E = rng.standard_normal((n, n))
+    E = E @ E.T / n
+    vs = rng.uniform(0.2, 2.0, (24, k))
+    return A0, U, V, G, E, vs
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+@pytest.mark.parametrize("n,k", [(70, 3), (130, 2)])
+def test_real_cauchy_layout_on_complex_vectors(ctx, n, k, adjoint):
+    """With an exactly real eigen-decomposition the mixed path multiplies by
+    the real n x n Cauchy matrix and takes the real and imaginary parts of
+    each panel column as two columns. Complex inputs (as complex recycled
+    vectors make them) must still give T(v) w: the tcgen05 operator within
+    1e-4 and the integer-sliced residual within 1e-12 of the FP64 operator.
+    n = 130 spans two 128-row tiles with a ragged tail."""
+    import torch
+
+    A0, U, V, G, E, vs = symmetric_problem(n + k, n, k, 4)
+    seed = ly.Seed(ctx, A0, U, V, G, E)
+    assert seed.stats()["real_path"] == 1
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal((9, k, n, 2))
+    v = torch.tensor(vs[:9], dtype=torch.float64, device="cuda")
+    wt = torch.tensor(w, dtype=torch.float64, device="cuda")
+    y64 = ly.test_apply(seed, v, wt, ly.FP64, adjoint).cpu().numpy()
+    y16 = ly.test_apply(seed, v, wt, ly.BF16_IR, adjoint).cpu().numpy()
+    ytc = ly.test_apply(seed, v, wt, ly.TEST_TC, adjoint).cpu().numpy()
+    for b in range(9):
+        nb = np.linalg.norm(y64[b])
+        assert np.linalg.norm(y16[b] - y64[b]) <= 1e-4 * nb, b
+        assert np.linalg.norm(ytc[b] - y64[b]) <= 1e-12 * nb, b
+        # the imaginary part of the output is not zero: the Im columns count
+        assert np.linalg.norm(y64[b][..., 1]) > 0.1 * nb
+
+
+def test_mixed_symmetric_seed_against_the_oracle(ctx):
+    """Two calls on one symmetric seed (the second starts from the first's
+    recycled space) against the oracle, traces and gradients."""
+    A0, U, V, G, E, vs = symmetric_problem(11, 90, 3, 5)
+    seed = ly.Seed(ctx, A0, U, V, G, E)
+    f1 = seed.trace_EX(vs[:12], precision=ly.BF16_IR)
+    f2, g2 = seed.grad(vs[12:], precision=ly.BF16_IR)
+    for i, v in enumerate(vs):
+        fo = oracle.trace_EX(A0, U, V, G, E, v)
+        f = f1[i] if i < 12 else f2[i - 12]
+        assert rel_err(f, fo) <= TOL_MIXED, i
+    for i in (0, 5, 11):
+        _, go = oracle.gradient(A0, U, V, G, E, vs[12 + i])
+        assert np.abs(np.asarray(g2[i]) - go).max() <= 1e-6 * np.abs(go).max(), i
