@@ -30,6 +30,7 @@ constexpr int OCT = 256;          // threads per CTA of k_ortho_cl
 // step needs two cluster reductions instead of three.
 constexpr bool kFoldNorm = true;
 constexpr int OCL_MAXNB = 64;     // basis vectors (s_cur + j + 1 <= m + 1 <= 61)
+constexpr int OCL_MAXC = 16;      // CTAs per cluster (the launcher's largest tier)
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -127,12 +128,17 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
       }
     }
   };
-  // coefficients: the cluster's partial sums added in rank order
+  // coefficients: the cluster's partial sums added in rank order; the remote
+  // loads are all issued before the first add (ranks past ncta add zero)
   auto gather = [&](R* in, T2* cf, int extra) {
     cl.sync();
     if (tid < 2 * nb + extra) {
+      R v[OCL_MAXC];
+#pragma unroll
+      for (int r = 0; r < OCL_MAXC; ++r) v[r] = r < ncta ? cl.map_shared_rank(in, r)[tid] : R(0);
       R s = R(0);
-      for (int r = 0; r < ncta; ++r) s += cl.map_shared_rank(in, r)[tid];
+#pragma unroll
+      for (int r = 0; r < OCL_MAXC; ++r) s += v[r];
       reinterpret_cast<R*>(cf)[tid] = s;
     }
     __syncthreads();
@@ -195,6 +201,9 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
   const R inv = rn > R(0) ? R(1) / rn : R(0);
   if (ok)
     for (int e = tid; e < len; e += OCT) w[e0 + e] = cscale(sw[e], inv);
+  double2 gj = make_double2(0.0, 0.0);
+  double tola = 0.0;
+  int itd = 0;
   if (rank == 0 && ok) {
     double2* H0c = Ls.H0 + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
     double2* Bc = Bk + (size_t)b * smax * m + (size_t)j * smax;
@@ -212,9 +221,6 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
       cs_s[tid - 64] = Ls.cs[(size_t)b * m + tid - 64];
       sn_s[tid - 64] = Ls.sn[(size_t)b * m + tid - 64];
     }
-    double2 gj = make_double2(0.0, 0.0);
-    double tola = 0.0;
-    int itd = 0;
     if (tid == 0) {
       gj = Ls.g[(size_t)b * (m + 1) + j];
       tola = Ls.tolabs[b];
@@ -224,10 +230,12 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
       hcol[j + 1] = make_double2(nrm, 0.0);
     }
     __syncthreads();
-    if (tid == 0) lsq_column(b, j, m, H, hcol, cs_s, sn_s, gj, tola, itd, Ls);
   }
   if (!ok && tid == 0 && len > 0) tcu::mbar_wait(mb, 0);  // no copy may land after the CTA has gone
   cl.sync();  // every CTA's partial sums stay readable until all have read them
+  // the serial Givens update reads only rank 0's own shared memory, so the
+  // other CTAs of the cluster are already free
+  if (rank == 0 && ok && tid == 0) lsq_column(b, j, m, H, hcol, cs_s, sn_s, gj, tola, itd, Ls);
 }
 
 }  // namespace kry
