@@ -103,37 +103,63 @@ struct LsqArgs {
 // column (h, j + 2 entries) and the previous rotations (cs_s, sn_s) are in
 // shared memory, and gj = g[j], tolabs, iterations done were loaded before
 // the column was; only stores go to global memory.
+//
+// R is the arithmetic of the rotations: the precision of the Krylov vectors.
+// With FP32 vectors the column's entries carry FP32 inner products, and a
+// serial chain of FP64 operations on one thread (GB300's FP64 rate is 1/64
+// of its FP32 rate) would cost more than the rest of the Arnoldi step;
+// storage stays FP64 either way.
+template <typename R>
 __device__ __forceinline__ void lsq_column(int b, int j, int m, double2* __restrict__ H, const double2* h,
                                            const double* cs_s, const double2* sn_s, double2 gj, double tola,
                                            int iters_done, const LsqArgs& L) {
+  using C = typename Cplx<R>::T;
+  const auto in = [](double2 x) -> C { return C{(R)x.x, (R)x.y}; };
+  const auto out = [](C x) -> double2 { return make_double2((double)x.x, (double)x.y); };
   double2* hg = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
-  double2 top = h[0];
+  C top = in(h[0]);
   for (int i = 0; i < j; ++i) {
-    const double2 bot = h[i + 1];
-    const double ci = cs_s[i];
-    const double2 si = sn_s[i];
-    hg[i] = cadd(cscale(top, ci), cmul(si, bot));
+    const C bot = in(h[i + 1]);
+    const R ci = (R)cs_s[i];
+    const C si = in(sn_s[i]);
+    hg[i] = out(cadd(cscale(top, ci), cmul(si, bot)));
     top = csub(cscale(bot, ci), cjmul(si, top));
   }
-  const double2 low = h[j + 1];
-  double cj;
-  double2 sj;
-  sd::givens<double2, double>(top, low, cj, sj);
-  const double2 rho = cadd(cscale(top, cj), cmul(sj, low));
-  const double sub = low.x;
-  hg[j] = rho;
+  const C low = in(h[j + 1]);
+  R cj;
+  C sj;
+  {  // rotation zeroing low under top, scaled so that no square overflows
+    const R ax = sqrt(cabs2(top)), ay = sqrt(cabs2(low));
+    if (ay == R(0)) {
+      cj = R(1);
+      sj = C{R(0), R(0)};
+    } else if (ax == R(0)) {
+      cj = R(0);
+      sj = C{R(1), R(0)};
+    } else {
+      const R mx = ax > ay ? ax : ay;
+      const R r = mx * sqrt((ax / mx) * (ax / mx) + (ay / mx) * (ay / mx));
+      cj = ax / r;
+      sj = cscale(cjmul(low, cscale(top, R(1) / ax)), R(1) / r);  // (top / |top|) conj(low) / r
+    }
+  }
+  const C rho = cadd(cscale(top, cj), cmul(sj, low));
+  const double sub = (double)low.x;
+  hg[j] = out(rho);
   hg[j + 1] = make_double2(0.0, 0.0);
-  L.cs[(size_t)b * m + j] = cj;
-  L.sn[(size_t)b * m + j] = sj;
+  L.cs[(size_t)b * m + j] = (double)cj;
+  L.sn[(size_t)b * m + j] = out(sj);
   double2* gb = L.g + (size_t)b * (m + 1);
-  gb[j] = cscale(gj, cj);
-  const double2 gn = cscale(cjmul(sj, gj), -1.0);
-  gb[j + 1] = gn;
-  const double res = sqrt(cabs2(gn));
+  const C gjc = in(gj);
+  gb[j] = out(cscale(gjc, cj));
+  const C gn = cscale(cjmul(sj, gjc), R(-1));
+  gb[j + 1] = out(gn);
+  const double res = sqrt(cabs2(out(gn)));
+  const double2 rhod = out(rho);
   int st = ST_RUN;
-  if (!isfinite(res) || !isfinite(rho.x) || !isfinite(rho.y)) st = ST_NONFINITE;
+  if (!isfinite(res) || !isfinite(rhod.x) || !isfinite(rhod.y)) st = ST_NONFINITE;
   else if (res <= tola) st = ST_CONV;
-  else if (!(sub > 1e-14 * sqrt(cabs2(rho)))) st = ST_CONV;  // invariant subspace: exact in the space
+  else if (!(sub > 1e-14 * sqrt(cabs2(rhod)))) st = ST_CONV;  // invariant subspace: exact in the space
   else if (iters_done + j + 1 >= L.maxit) st = ST_MAXIT;
   L.jstop[b] = j + 1;  // provisional when still running (the cycle may end here)
   if (st != ST_RUN) L.flag[b] = -st;  // negative: stopped this cycle with a final status
@@ -295,7 +321,8 @@ __global__ void __launch_bounds__(OT, sizeof(T2) == 8 ? 2 : 1) k_ortho(int N, in
     hcol[j + 1] = make_double2(nrm, 0.0);
   }
   __syncthreads();
-  if (threadIdx.x == 0) lsq_column(b, j, m, H, hcol, cs_s, sn_s, gj, tola, itd, L);  // while the others normalise w
+  if (threadIdx.x == 0)  // while the others normalise w
+    lsq_column<typename RealOf<T2>::T>(b, j, m, H, hcol, cs_s, sn_s, gj, tola, itd, L);
   const R rn = sqrt(tot);
   const R inv = rn > R(0) ? R(1) / rn : R(0);
   for (int e = threadIdx.x; e < N; e += OT) w[e] = cscale(w[e], inv);

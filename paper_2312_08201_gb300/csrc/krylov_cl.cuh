@@ -110,12 +110,25 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
     for (int q = warp; q < nb; q += NW) {
       R ax = R(0), ay = R(0);
       if (ok) {
+        // four independent accumulators, so the shared-memory loads overlap
         const T2* vq = data + (size_t)q * L;
-        for (int e = lane; e < len; e += 32) {
-          const T2 a = vq[e], c = x[e];
-          ax += a.x * c.x + a.y * c.y;
-          ay += a.x * c.y - a.y * c.x;
+        R bx[4] = {R(0), R(0), R(0), R(0)}, by[4] = {R(0), R(0), R(0), R(0)};
+        int e = lane;
+        for (; e + 96 < len; e += 128) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const T2 a = vq[e + 32 * u], c = x[e + 32 * u];
+            bx[u] += a.x * c.x + a.y * c.y;
+            by[u] += a.x * c.y - a.y * c.x;
+          }
         }
+        for (; e < len; e += 32) {
+          const T2 a = vq[e], c = x[e];
+          bx[0] += a.x * c.x + a.y * c.y;
+          by[0] += a.x * c.y - a.y * c.x;
+        }
+        ax = (bx[0] + bx[1]) + (bx[2] + bx[3]);
+        ay = (by[0] + by[1]) + (by[2] + by[3]);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -148,8 +161,15 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
     R nr = R(0);
     if (!ok) return nr;
     for (int e = tid; e < len; e += OCT) {
-      T2 we = sw[e];
-      for (int q = 0; q < nb; ++q) we = csub(we, cmul(data[(size_t)q * L + e], cf[q]));
+      // two partial sums over the basis, so consecutive loads are independent
+      T2 s0 = sw[e], s1 = T2{R(0), R(0)};
+      int q = 0;
+      for (; q + 1 < nb; q += 2) {
+        s0 = csub(s0, cmul(data[(size_t)q * L + e], cf[q]));
+        s1 = csub(s1, cmul(data[(size_t)(q + 1) * L + e], cf[q + 1]));
+      }
+      if (q < nb) s0 = csub(s0, cmul(data[(size_t)q * L + e], cf[q]));
+      const T2 we = cadd(s0, s1);
       sw[e] = we;
       nr += cabs2(we);
     }
@@ -235,7 +255,7 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
   cl.sync();  // every CTA's partial sums stay readable until all have read them
   // the serial Givens update reads only rank 0's own shared memory, so the
   // other CTAs of the cluster are already free
-  if (rank == 0 && ok && tid == 0) lsq_column(b, j, m, H, hcol, cs_s, sn_s, gj, tola, itd, Ls);
+  if (rank == 0 && ok && tid == 0) lsq_column<R>(b, j, m, H, hcol, cs_s, sn_s, gj, tola, itd, Ls);
 }
 
 }  // namespace kry
