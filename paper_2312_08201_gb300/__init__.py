@@ -517,10 +517,10 @@ def prof_enable(on: bool = True):
 
 def prof_read():
     """(per-kernel records, library kernel launches since prof_enable)."""
-    arr = (ProfKernel * 16)()
+    arr = (ProfKernel * 32)()
     cnt = ctypes.c_int()
     launches = ctypes.c_longlong()
-    _check(load().lyap_prof_read(arr, 16, ctypes.byref(cnt), ctypes.byref(launches)), "lyap_prof_read")
+    _check(load().lyap_prof_read(arr, 32, ctypes.byref(cnt), ctypes.byref(launches)), "lyap_prof_read")
     recs = {
         arr[i].name.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms, units=arr[i].units,
                                    flops=arr[i].flops, bytes=arr[i].bytes)

@@ -165,6 +165,64 @@ __device__ __forceinline__ void lsq_column(int b, int j, int m, double2* __restr
   if (st != ST_RUN) L.flag[b] = -st;  // negative: stopped this cycle with a final status
 }
 
+// The serial part of lsq_column on copies in shared memory, for a caller
+// that converts in parallel: hr[0..j+1] holds the column in the precision R
+// and is rotated in place (hr[0..j] the rotated column, hr[j+1] = 0), csr and
+// snr the previous rotations. Only the rotation's own results (cs, sn, g,
+// jstop, flag) go to global memory here; the caller stores hr into H.
+template <typename R>
+__device__ __forceinline__ void lsq_rotate(int b, int j, int m, typename Cplx<R>::T* hr, const R* csr,
+                                           const typename Cplx<R>::T* snr, double2 gj, double tola,
+                                           int iters_done, const LsqArgs& L) {
+  using C = typename Cplx<R>::T;
+  C top = hr[0];
+  for (int i = 0; i < j; ++i) {
+    const C bot = hr[i + 1];
+    const R ci = csr[i];
+    const C si = snr[i];
+    hr[i] = cadd(cscale(top, ci), cmul(si, bot));
+    top = csub(cscale(bot, ci), cjmul(si, top));
+  }
+  const C low = hr[j + 1];
+  R cj;
+  C sj;
+  {  // rotation zeroing low under top, scaled so that no square overflows
+    const R ax = sqrt(cabs2(top)), ay = sqrt(cabs2(low));
+    if (ay == R(0)) {
+      cj = R(1);
+      sj = C{R(0), R(0)};
+    } else if (ax == R(0)) {
+      cj = R(0);
+      sj = C{R(1), R(0)};
+    } else {
+      const R mx = ax > ay ? ax : ay;
+      const R r = mx * sqrt((ax / mx) * (ax / mx) + (ay / mx) * (ay / mx));
+      cj = ax / r;
+      sj = cscale(cjmul(low, cscale(top, R(1) / ax)), R(1) / r);  // (top / |top|) conj(low) / r
+    }
+  }
+  const C rho = cadd(cscale(top, cj), cmul(sj, low));
+  hr[j] = rho;
+  hr[j + 1] = C{R(0), R(0)};
+  const C gjc = C{(R)gj.x, (R)gj.y};
+  const C gn = cscale(cjmul(sj, gjc), R(-1));
+  const C g0 = cscale(gjc, cj);
+  L.cs[(size_t)b * m + j] = (double)cj;
+  L.sn[(size_t)b * m + j] = make_double2((double)sj.x, (double)sj.y);
+  double2* gb = L.g + (size_t)b * (m + 1);
+  gb[j] = make_double2((double)g0.x, (double)g0.y);
+  gb[j + 1] = make_double2((double)gn.x, (double)gn.y);
+  const R res = sqrt(cabs2(gn));
+  const R rr = sqrt(cabs2(rho));
+  int st = ST_RUN;
+  if (!isfinite(res) || !isfinite(rho.x) || !isfinite(rho.y)) st = ST_NONFINITE;
+  else if ((double)res <= tola) st = ST_CONV;
+  else if (!((double)low.x > 1e-14 * (double)rr)) st = ST_CONV;  // invariant subspace: exact in the space
+  else if (iters_done + j + 1 >= L.maxit) st = ST_MAXIT;
+  L.jstop[b] = j + 1;  // provisional when still running (the cycle may end here)
+  if (st != ST_RUN) L.flag[b] = -st;  // negative: stopped this cycle with a final status
+}
+
 // ----------------------------------------------------------- CGS2 Arnoldi
 // Sum 32 per-thread values over a warp: after the call lane l holds, in
 // v[0], the warp total of value l (a butterfly that halves the values per

@@ -63,9 +63,10 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
   R* part = reinterpret_cast<R*>(osm + 16);                      // 3 x 2 x OCL_MAXNB partial sums
   T2* coef = reinterpret_cast<T2*>(osm + 16 + 3 * 2 * OCL_MAXNB * sizeof(R));  // 2 x OCL_MAXNB
   T2* data = reinterpret_cast<T2*>(osm + ortho_cl_header<T2>());  // (nb + 1) slices of L elements
-  __shared__ double2 hcol[64];
-  __shared__ double cs_s[64];
-  __shared__ double2 sn_s[64];
+  using C2 = typename Cplx<R>::T;
+  __shared__ C2 hr[66];   // column j of H in the vectors' precision (rank 0)
+  __shared__ R csr[64];   // previous rotations
+  __shared__ C2 snr[64];
   __shared__ R red[NW];
   __shared__ int failed;
 
@@ -106,38 +107,53 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
   if (!ok && tid == 0) atomicExch(err, 21);
 
   // partial inner products conj(basis_q) . x over this CTA's slice, one warp per vector
+  // Two basis vectors per warp and pass over x (x is read once for both);
+  // two independent accumulators per product, so the loads overlap.
   auto partial_dots = [&](const T2* x, R* out) {
-    for (int q = warp; q < nb; q += NW) {
-      R ax = R(0), ay = R(0);
+    for (int q = warp; q < nb; q += 2 * NW) {
+      const int q2 = q + NW < nb ? q + NW : q;  // a lone last vector is paired with itself
+      R ax = R(0), ay = R(0), cx = R(0), cy = R(0);
       if (ok) {
-        // four independent accumulators, so the shared-memory loads overlap
-        const T2* vq = data + (size_t)q * L;
-        R bx[4] = {R(0), R(0), R(0), R(0)}, by[4] = {R(0), R(0), R(0), R(0)};
+        const T2* va = data + (size_t)q * L;
+        const T2* vb = data + (size_t)q2 * L;
+        R p[8] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
         int e = lane;
-        for (; e + 96 < len; e += 128) {
+        for (; e + 32 < len; e += 64) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const T2 a = vq[e + 32 * u], c = x[e + 32 * u];
-            bx[u] += a.x * c.x + a.y * c.y;
-            by[u] += a.x * c.y - a.y * c.x;
+          for (int u = 0; u < 2; ++u) {
+            const T2 c = x[e + 32 * u], a = va[e + 32 * u], d = vb[e + 32 * u];
+            p[4 * u + 0] += a.x * c.x + a.y * c.y;
+            p[4 * u + 1] += a.x * c.y - a.y * c.x;
+            p[4 * u + 2] += d.x * c.x + d.y * c.y;
+            p[4 * u + 3] += d.x * c.y - d.y * c.x;
           }
         }
-        for (; e < len; e += 32) {
-          const T2 a = vq[e], c = x[e];
-          bx[0] += a.x * c.x + a.y * c.y;
-          by[0] += a.x * c.y - a.y * c.x;
+        if (e < len) {
+          const T2 c = x[e], a = va[e], d = vb[e];
+          p[0] += a.x * c.x + a.y * c.y;
+          p[1] += a.x * c.y - a.y * c.x;
+          p[2] += d.x * c.x + d.y * c.y;
+          p[3] += d.x * c.y - d.y * c.x;
         }
-        ax = (bx[0] + bx[1]) + (bx[2] + bx[3]);
-        ay = (by[0] + by[1]) + (by[2] + by[3]);
+        ax = p[0] + p[4];
+        ay = p[1] + p[5];
+        cx = p[2] + p[6];
+        cy = p[3] + p[7];
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         ax += __shfl_xor_sync(0xffffffffu, ax, o);
         ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        cx += __shfl_xor_sync(0xffffffffu, cx, o);
+        cy += __shfl_xor_sync(0xffffffffu, cy, o);
       }
       if (lane == 0) {
         out[2 * q] = ax;
         out[2 * q + 1] = ay;
+        if (q2 != q) {
+          out[2 * q2] = cx;
+          out[2 * q2 + 1] = cy;
+        }
       }
     }
   };
@@ -225,6 +241,7 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
   double tola = 0.0;
   int itd = 0;
   if (rank == 0 && ok) {
+    // the column and the previous rotations, converted in parallel
     double2* H0c = Ls.H0 + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
     double2* Bc = Bk + (size_t)b * smax * m + (size_t)j * smax;
     if (tid < nb) {
@@ -234,28 +251,36 @@ __global__ void __launch_bounds__(OCT) k_ortho_cl(int N, int L, int j, int m, in
         Bc[q] = cval;
       } else {
         H0c[q - s_cur] = cval;
-        hcol[q - s_cur] = cval;
+        hr[q - s_cur] = C2{(R)cval.x, (R)cval.y};
       }
     }
-    if (tid >= 64 && tid < 64 + j) {  // the previous rotations
-      cs_s[tid - 64] = Ls.cs[(size_t)b * m + tid - 64];
-      sn_s[tid - 64] = Ls.sn[(size_t)b * m + tid - 64];
+    if (tid >= 64 && tid < 64 + j) {
+      const double2 sn = Ls.sn[(size_t)b * m + tid - 64];
+      csr[tid - 64] = (R)Ls.cs[(size_t)b * m + tid - 64];
+      snr[tid - 64] = C2{(R)sn.x, (R)sn.y};
     }
     if (tid == 0) {
       gj = Ls.g[(size_t)b * (m + 1) + j];
       tola = Ls.tolabs[b];
       itd = Ls.iters_done[b];
-      const double nrm = sqrt((double)tot);
-      H0c[j + 1] = make_double2(nrm, 0.0);
-      hcol[j + 1] = make_double2(nrm, 0.0);
+      H0c[j + 1] = make_double2((double)rn, 0.0);
+      hr[j + 1] = C2{rn, R(0)};
     }
     __syncthreads();
   }
   if (!ok && tid == 0 && len > 0) tcu::mbar_wait(mb, 0);  // no copy may land after the CTA has gone
   cl.sync();  // every CTA's partial sums stay readable until all have read them
   // the serial Givens update reads only rank 0's own shared memory, so the
-  // other CTAs of the cluster are already free
-  if (rank == 0 && ok && tid == 0) lsq_column<R>(b, j, m, H, hcol, cs_s, sn_s, gj, tola, itd, Ls);
+  // other CTAs of the cluster are already free; its results are stored in
+  // parallel
+  if (rank == 0) {
+    if (ok && tid == 0) lsq_rotate<R>(b, j, m, hr, csr, snr, gj, tola, itd, Ls);
+    __syncthreads();
+    if (ok && tid <= j + 1) {
+      double2* hg = H + (size_t)b * (m + 1) * m + (size_t)j * (m + 1);
+      hg[tid] = make_double2((double)hr[tid].x, (double)hr[tid].y);
+    }
+  }
 }
 
 }  // namespace kry

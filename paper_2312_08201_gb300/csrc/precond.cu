@@ -661,12 +661,27 @@ int launch_cap_build(lyap_seed* sd, int r, int B, const double* vinv, const Wood
   return LYAP_OK;
 }
 
+// C (m x n) = op(A) B, complex FP32 column-major, on the context's cuBLAS
+// handle (shared by the context's users, hence the lock) and stream st.
+int prec_gemm(lyap_ctx* ctx, cublasOperation_t ta, int m, int n, int k, const float2* A, int lda, const float2* B,
+              int ldb, float2* C, int ldc, cudaStream_t st);
+
 // Compute type of the apply's two GEMMs: FP32 throughout. The basis is
 // flexible (Z = P^{-1} V is stored), so the preconditioner's rounding only
 // shapes the convergence rate; but where the rank-p Woodbury correction is
 // nearly exact (a coupling of rank <= p) TF32 products (11 bits) cost that
 // exactness and the inner iterations rise by half.
 constexpr cublasComputeType_t kPrecGemmCompute = CUBLAS_COMPUTE_32F;
+
+int prec_gemm(lyap_ctx* ctx, cublasOperation_t ta, int m, int n, int k, const float2* A, int lda, const float2* B,
+              int ldb, float2* C, int ldc, cudaStream_t st) {
+  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+  std::lock_guard<std::mutex> lk(ctx->handle_mu);
+  LY_BLAS(cublasSetStream(ctx->blas, st));
+  LY_BLAS(cublasGemmEx(ctx->blas, ta, CUBLAS_OP_N, m, n, k, &one, A, CUDA_C_32F, lda, B, CUDA_C_32F, ldb, &zero, C,
+                       CUDA_C_32F, ldc, kPrecGemmCompute, CUBLAS_GEMM_DEFAULT));
+  return LYAP_OK;
+}
 
 template <typename T2, int K>
 int launch_prec(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* vinv, const int* list,
@@ -680,29 +695,30 @@ int launch_prec(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* 
   const float2* Bm = ws ? (adjoint ? ws->Nl : ws->Ml) : nullptr;
   if constexpr (std::is_same<T2, float2>::value) {
     if (r > 0) {
+      // each step is its own span of the kernel accounting (the GEMMs under
+      // prec_gemm); bytes and flops per system
       const int nk = n * K;
+      const double N = (double)nk;
       float2* C = ws->cpart;               // r x B
       float2* Y = C + (size_t)r * B;        // r x B
       float2* D = Y + (size_t)r * B;        // nk x B
+      int ph = prof_begin(PK_PRECOND, st);
       k_prec_a<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, In, in_ss, Out, out_ss,
                                            0, nullptr, 0, nullptr, B);
-      lyap_ctx* ctx = sd->ctx;
-      const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
-      {
-        std::lock_guard<std::mutex> lk(ctx->handle_mu);  // library handles are shared by the context's users
-        LY_BLAS(cublasSetStream(ctx->blas, st));
-        LY_BLAS(cublasGemmEx(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, r, B, nk, &one, Bm, CUDA_C_32F, ws->ldr, Out,
-                             CUDA_C_32F, (int)out_ss, &zero, C, CUDA_C_32F, r, kPrecGemmCompute, CUBLAS_GEMM_DEFAULT));
-      }
+      prof_end(ph, st, 8.0 * N * K, 16.0 * N, 0, count);
+      ph = prof_begin(PK_PRECGEMM, st);
+      LY_TRY(prec_gemm(sd->ctx, CUBLAS_OP_T, r, B, nk, Bm, ws->ldr, Out, (int)out_ss, C, r, st));
+      prof_end(ph, st, 8.0 * N * r, 0.0, B, nullptr);
+      ph = prof_begin(PK_PRECOND, st);
       k_prec_ysys<<<B, WT, 0, st>>>(list, count, adjoint ? 1 : 0, r, ws->cinv, C, Y);
-      {
-        std::lock_guard<std::mutex> lk(ctx->handle_mu);
-        LY_BLAS(cublasSetStream(ctx->blas, st));
-        LY_BLAS(cublasGemmEx(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, nk, B, r, &one, A, CUDA_C_32F, ws->ldr, Y,
-                             CUDA_C_32F, r, &zero, D, CUDA_C_32F, nk, kPrecGemmCompute, CUBLAS_GEMM_DEFAULT));
-      }
+      prof_end(ph, st, 8.0 * r * r, 8.0 * r * r + 16.0 * r, 0, count);
+      ph = prof_begin(PK_PRECGEMM, st);
+      LY_TRY(prec_gemm(sd->ctx, CUBLAS_OP_N, nk, B, r, A, ws->ldr, Y, r, D, nk, st));
+      prof_end(ph, st, 8.0 * N * r, 0.0, B, nullptr);
+      ph = prof_begin(PK_PRECOND, st);
       k_prec_dsys<K><<<dim3((n + WT - 1) / WT, B), WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, D,
                                                                 Out, out_ss);
+      prof_end(ph, st, 8.0 * N * K, 24.0 * N, 0, count);
       lyap_count_launch(3);
       return LYAP_OK;
     }
@@ -864,7 +880,8 @@ template <typename T2>
 int prec_apply(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* vinv, const int* list,
                const int* count, int B, const T2* In, size_t in_ss, T2* Out, size_t out_ss, cudaStream_t st) {
   if (ws && ws->r <= 0) ws = nullptr;
-  const int ph = prof_begin(PK_PRECOND, st);
+  const bool gemm_form = std::is_same<T2, float2>::value && ws;  // accounts its own steps
+  const int ph = gemm_form ? -1 : prof_begin(PK_PRECOND, st);
   int rc = LYAP_OK;
   switch (sd->k) {
     case 1: rc = launch_prec<T2, 1>(sd, ws, adjoint, vinv, list, count, B, In, in_ss, Out, out_ss, st); break;
@@ -881,8 +898,9 @@ int prec_apply(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* v
   // algorithmic bytes per system: read r, write z, read+write z again when r > 0
   const int r = ws ? ws->r : 0;
   const double N = (double)sd->n * sd->k;
-  prof_end(ph, st, 8.0 * N * sd->k + (r > 0 ? 16.0 * N * r + 8.0 * N * sd->k + 8.0 * r * r : 0.0),
-           N * sizeof(T2) * (r > 0 ? 4.0 : 2.0), 0, count);
+  if (!gemm_form)
+    prof_end(ph, st, 8.0 * N * sd->k + (r > 0 ? 16.0 * N * r + 8.0 * N * sd->k + 8.0 * r * r : 0.0),
+             N * sizeof(T2) * (r > 0 ? 4.0 : 2.0), 0, count);
   LY_CUDA(cudaGetLastError());
   return LYAP_OK;
 }

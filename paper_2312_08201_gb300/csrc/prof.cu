@@ -10,7 +10,8 @@
 namespace {
 
 const char* kNames[PK_COUNT] = {"capmv64", "tc_gemm", "ortho", "precond", "gram", "tsmm",
-                                "ritz",    "epi32",   "lsq",   "cycle",   "panel", "recstart", "capmv_ff", "cap_build", "oz_gemm"};
+                                "ritz",    "epi32",   "lsq",   "cycle",   "panel", "recstart", "capmv_ff", "cap_build", "oz_gemm",
+                                "prec_gemm"};
 
 struct Rec {
   int kernel;
