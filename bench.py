@@ -604,11 +604,8 @@ def main():
                d2h_bytes_per_step=int(nv * 8))
 
     # roofline of the dominant kernel (largest device time in the timed region)
-    # among the library's own kernels; cuBLAS work (prec_gemm, the Woodbury
-    # apply's two GEMMs) is listed under "kernels" but has no roofline here
     pk, how = peaks()
-    own = {kname: d for kname, d in prof.items() if kname != "prec_gemm"}
-    dom_name = max(own, key=lambda kname: own[kname]["total_ms"]) if own else None
+    dom_name = max(prof, key=lambda kname: prof[kname]["total_ms"]) if prof else None
     roof = None
     if dom_name:
         d = prof[dom_name]
@@ -629,7 +626,7 @@ def main():
                         peak_source="FP32 pipe: 152 SMs x 128 lane-instructions/clk x max SM clock "
                                     "(achieved: 49.5 FP32 instructions per float-float complex MAC)",
                         launches=d["launches"], avg_launch_ms=d["total_ms"] / d["launches"])
-        elif dom_name in ("tc_gemm", "oz_gemm"):
+        elif dom_name in ("tc_gemm", "oz_gemm", "prec_gemm"):
             peak = float(pk["bf16_tflops_sustained"])
             ach = d["flops"] / sec / 1e12
             roof = dict(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=None,

@@ -260,6 +260,7 @@ extern "C" int lyap_seed_free(lyap_seed* sd) {
   cudaSetDevice(sd->device);
   delete sd->work;
   lyap_mixed_free(sd);
+  lyap_prec_tc_free(sd);
   delete sd;
   return LYAP_OK;
 }

@@ -149,6 +149,7 @@ struct lyap_seed {
   // O ~ tsvd_N tsvd_M^T, nk x tsvd_r each (FP32), built on first use.
   DevBuf<float2> tsvd_N, tsvd_M;
   int tsvd_r = 0;
+  int tsvd_gen = 0;  // counts rebuilds of tsvd_N / tsvd_M
   DevBuf<float2> cap_work;  // K(v)^{-1} Nl of a chunk of systems while Cap(v)^{-1} is built
   // Recycle spaces: primal/adjoint x FP64/FP32-inner.
   Recycle<double2> rec64, rec64_adj;
@@ -158,6 +159,8 @@ struct lyap_seed {
   struct SeedWork* work = nullptr;
   // Mixed-path operands and buffers (owned; freed with the seed).
   struct MixedState* mixed = nullptr;
+  // Tensor-core operands and panels of the FP32 Woodbury apply (owned).
+  struct PrecTcState* prec_tc = nullptr;
 };
 
 // ------------------------------------------------------------------ helpers

@@ -361,6 +361,7 @@ int refine(lyap_seed* sd, int Bc, const double* vinv, const double2* rhs, double
       if (ms.wpart.count < wood_part_count(sd->n, k, na, r)) LY_TRY(ms.wpart.alloc(wood_part_count(sd->n, k, Bc, r)));
       ms.wood.cinv = ms.wcinv.p;
       ms.wood.cpart = ms.wpart.p;
+      ms.wood.err = ms.err.p;
       // Cap(v)^{-1} of every chunk system was built once by lyap_mixed_chunk
       LY_TRY(wood_bind(sd, r, na, ms.wcinv_full.p, ms.act.p, ms.wood, st));
       op.wood = &ms.wood;
@@ -823,6 +824,7 @@ int lyap_engine_step(lyap_seed* sd, MixedEngine& e, const lyap_opts& o, cudaStre
       if (ms.wpart.count < wood_part_count(n, k, na, e.r)) LY_TRY(ms.wpart.alloc(wood_part_count(n, k, e.cap, e.r)));
       ms.wood.cinv = ms.wcinv.p;
       ms.wood.cpart = ms.wpart.p;
+      ms.wood.err = ms.err.p;
       LY_TRY(wood_bind(sd, e.r, na, e.cinv.p, ms.act.p, ms.wood, st));
       op.wood = &ms.wood;
     }

@@ -1,4 +1,6 @@
 // Truncated-SVD coupling of the preconditioner (eq. (prec)); see precond.cuh.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -10,6 +12,7 @@
 #include "lyap_internal.h"
 #include "precond.cuh"
 #include "prof.h"
+#include "tc_gemm.cuh"
 
 namespace {
 
@@ -560,26 +563,95 @@ __global__ void __launch_bounds__(WT) k_prec_b(int n, const int* __restrict__ li
   }
 }
 
-// FP32 Krylov vectors: the two products of the apply run as GEMMs over all B
-// system columns (C = B^T Z and D = A Y), with the per-system steps around
-// them in the kernels below. Columns of systems that are not listed hold
-// whatever the vectors hold and are never read back.
+// FP32 Krylov vectors: the two products of the apply run on the tensor cores
+// (the tcgen05 BF16x3 GEMM of the inner operator, real-split complex
+// operands), over the active systems in slot order:
+//   k_prec_z    z = K^{-1} r, stored, and its panel row (BF16 hi/lo, real-split)
+//   GEMM 1      c = B^T z, K = 2nk split across CTAs (partial sums per split)
+//   k_prec_ytc  y = Cap^{-1} (sum of the partials), and its panel row
+//   GEMM 2      d = A y
+//   k_prec_dtc  z += K^{-1} d
+// BF16x3 keeps about 16 bits of each product (relative error near 2^-16),
+// far inside what the preconditioner's convergence needs.
 
-// y_b = Cap_b^{-1} c_b (Cap_b^{-T} for the adjoint) for the listed systems,
-// c_b = C[:, b]; one CTA per system slot, Cap^{-1} staged as in k_prec_y.
-__global__ void __launch_bounds__(WT) k_prec_ysys(const int* __restrict__ list, const int* __restrict__ count,
-                                                  int adj, int r, const float2* __restrict__ cinv,
-                                                  const float2* __restrict__ C, float2* __restrict__ Y) {
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// Real-split operand of a product with M (nk x r complex, leading dimension
+// ld): trans = 1 gives M^T (rows 2l, 2l+1; K entries 2q, 2q+1), trans = 0
+// gives M (rows 2q, 2q+1; K entries 2l, 2l+1); each 2 x 2 block is
+// [[Re, -Im], [Im, Re]] of the entry. Padding rows and K entries are zero.
+__global__ void k_split_op(int nk, int r, const float2* __restrict__ M, int ld, int trans, int mpad, int kpad,
+                           __nv_bfloat16* __restrict__ H, __nv_bfloat16* __restrict__ Lo) {
+  const size_t total = (size_t)mpad * kpad;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(idx / kpad), col = (int)(idx % kpad);
+    const int q = trans ? col >> 1 : row >> 1, l = trans ? row >> 1 : col >> 1;
+    float v = 0.f;
+    if (q < nk && l < r) {
+      const float2 m = M[(size_t)q + (size_t)l * ld];
+      const int ri = row & 1, ci = col & 1;
+      v = ri == ci ? m.x : (ri == 0 ? -m.y : m.y);
+    }
+    split_bf16(v, H[idx], Lo[idx]);
+  }
+}
+
+// z = K^{-1} r for slot s (system list[s]), stored, and panel row s.
+template <int K>
+__global__ void __launch_bounds__(WT) k_prec_z(int n, const int* __restrict__ list, const int* __restrict__ count,
+                                               const float2* __restrict__ Gd, int adj, const double* __restrict__ vinv,
+                                               const float2* __restrict__ In, size_t in_ss, float2* __restrict__ Out,
+                                               size_t out_ss, int kpad, __nv_bfloat16* __restrict__ Ph,
+                                               __nv_bfloat16* __restrict__ Pl) {
+  const int j = blockIdx.x * WT + threadIdx.x;
+  const int s = blockIdx.y;
+  if (j >= n || s >= *count) return;
+  const int b = list[s];
+  float vb[K];
+  load_vb<K>(vinv, b, vb);
+  float2 x[K];
+  const float2* in = In + (size_t)b * in_ss;
+#pragma unroll
+  for (int t = 0; t < K; ++t) x[t] = in[(size_t)t * n + j];
+  bsolve<K>(n, j, Gd, adj, vb, x);
+  float2* out = Out + (size_t)b * out_ss;
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    const size_t q = (size_t)t * n + j;
+    out[q] = x[t];
+    const size_t o = (size_t)s * kpad + 2 * q;
+    split_bf16(x[t].x, Ph[o], Pl[o]);
+    split_bf16(x[t].y, Ph[o + 1], Pl[o + 1]);
+  }
+}
+
+// y = Cap^{-1} c (Cap^{-T} c for the adjoint) for slot s, c from the split
+// partials of GEMM 1 (rows 2l, 2l+1 of column s, ldd per column, dstride
+// per split); y goes to panel row s (K entries 2l, 2l+1). One CTA per slot,
+// Cap^{-1} staged as in k_prec_y.
+__global__ void __launch_bounds__(WT) k_prec_ytc(const int* __restrict__ list, const int* __restrict__ count, int adj,
+                                                 int r, const float2* __restrict__ cinv, const float* __restrict__ D1,
+                                                 int ldd, int splits, size_t dstride, int kpad,
+                                                 __nv_bfloat16* __restrict__ Ph, __nv_bfloat16* __restrict__ Pl) {
   __shared__ float2 Cs[RMAX * (RMAX + 1)];
   __shared__ float2 cs[RMAX];
   __shared__ float2 ys[WT / RMAX][RMAX];
   const int s = blockIdx.x;
   if (s >= *count) return;
-  const int b = list[s];
   const int rp = r | 1;
-  const float2* Ci = cinv + (size_t)b * r * r;
+  const float2* Ci = cinv + (size_t)list[s] * r * r;
   for (int e = threadIdx.x; e < r * r; e += WT) Cs[(e % r) + (e / r) * rp] = Ci[e];
-  for (int l = threadIdx.x; l < r; l += WT) cs[l] = C[(size_t)b * r + l];
+  for (int l = threadIdx.x; l < r; l += WT) {
+    float2 c = make_float2(0.f, 0.f);
+    for (int z = 0; z < splits; ++z) {
+      const float* d = D1 + (size_t)z * dstride + (size_t)s * ldd + 2 * l;
+      c = cadd(c, make_float2(d[0], d[1]));
+    }
+    cs[l] = c;
+  }
   __syncthreads();
   constexpr int G = WT / RMAX;
   const int l = threadIdx.x % RMAX, g = threadIdx.x / RMAX;
@@ -597,27 +669,31 @@ __global__ void __launch_bounds__(WT) k_prec_ysys(const int* __restrict__ list, 
     float2 t = ys[0][threadIdx.x];
 #pragma unroll
     for (int u = 1; u < G; ++u) t = cadd(t, ys[u][threadIdx.x]);
-    Y[(size_t)b * r + threadIdx.x] = t;
+    const size_t o = (size_t)s * kpad + 2 * threadIdx.x;
+    split_bf16(t.x, Ph[o], Pl[o]);
+    split_bf16(t.y, Ph[o + 1], Pl[o + 1]);
   }
 }
 
-// z_b += K_b^{-1} D[:, b] (K^T for the adjoint) for the listed systems; one
-// thread per (row j, system slot).
+// z += K^{-1} d for slot s, d from GEMM 2 (rows 2q, 2q+1 of column s).
 template <int K>
-__global__ void __launch_bounds__(WT) k_prec_dsys(int n, const int* __restrict__ list, const int* __restrict__ count,
-                                                  const float2* __restrict__ Gd, int adj,
-                                                  const double* __restrict__ vinv, const float2* __restrict__ D,
-                                                  float2* __restrict__ Out, size_t out_ss) {
+__global__ void __launch_bounds__(WT) k_prec_dtc(int n, const int* __restrict__ list, const int* __restrict__ count,
+                                                 const float2* __restrict__ Gd, int adj,
+                                                 const double* __restrict__ vinv, const float* __restrict__ D2,
+                                                 int ldd, float2* __restrict__ Out, size_t out_ss) {
   const int j = blockIdx.x * WT + threadIdx.x;
   const int s = blockIdx.y;
   if (j >= n || s >= *count) return;
   const int b = list[s];
-  const size_t nk = (size_t)n * K;
   float vb[K];
   load_vb<K>(vinv, b, vb);
   float2 x[K];
+  const float* d = D2 + (size_t)s * ldd;
 #pragma unroll
-  for (int t = 0; t < K; ++t) x[t] = D[(size_t)b * nk + (size_t)t * n + j];
+  for (int t = 0; t < K; ++t) {
+    const size_t q = (size_t)t * n + j;
+    x[t] = make_float2(d[2 * q], d[2 * q + 1]);
+  }
   bsolve<K>(n, j, Gd, adj, vb, x);
   float2* out = Out + (size_t)b * out_ss;
 #pragma unroll
@@ -661,25 +737,83 @@ int launch_cap_build(lyap_seed* sd, int r, int B, const double* vinv, const Wood
   return LYAP_OK;
 }
 
-// C (m x n) = op(A) B, complex FP32 column-major, on the context's cuBLAS
-// handle (shared by the context's users, hence the lock) and stream st.
-int prec_gemm(lyap_ctx* ctx, cublasOperation_t ta, int m, int n, int k, const float2* A, int lda, const float2* B,
-              int ldb, float2* C, int ldc, cudaStream_t st);
+}  // namespace
 
-// Compute type of the apply's two GEMMs: FP32 throughout. The basis is
-// flexible (Z = P^{-1} V is stored), so the preconditioner's rounding only
-// shapes the convergence rate; but where the rank-p Woodbury correction is
-// nearly exact (a coupling of rank <= p) TF32 products (11 bits) cost that
-// exactness and the inner iterations rise by half.
-constexpr cublasComputeType_t kPrecGemmCompute = CUBLAS_COMPUTE_32F;
+// Operands of the two products for rank r (both directions) of the seed's
+// current truncated SVD, and panels for a batch of systems; rebuilt when the
+// rank or the SVD changes, grown with the batch.
+struct PrecTcState {
+  int r = 0, nk = 0, gen = -1, kpad1 = 0, mpad2 = 0, kpad2 = 0;
+  DevBuf<__nv_bfloat16> a1h[2], a1l[2], a2h[2], a2l[2];  // [0] primal, [1] adjoint
+  tc::Maps m1[2], m2[2];
+  int ncap = 0, splits = 1;
+  DevBuf<__nv_bfloat16> b1h, b1l, b2h, b2l;  // ncap x kpad1, ncap x kpad2
+  DevBuf<float> d1, d2;                      // splits x ncap x 128, ncap x mpad2
+};
 
-int prec_gemm(lyap_ctx* ctx, cublasOperation_t ta, int m, int n, int k, const float2* A, int lda, const float2* B,
-              int ldb, float2* C, int ldc, cudaStream_t st) {
-  const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
-  std::lock_guard<std::mutex> lk(ctx->handle_mu);
-  LY_BLAS(cublasSetStream(ctx->blas, st));
-  LY_BLAS(cublasGemmEx(ctx->blas, ta, CUBLAS_OP_N, m, n, k, &one, A, CUDA_C_32F, lda, B, CUDA_C_32F, ldb, &zero, C,
-                       CUDA_C_32F, ldc, kPrecGemmCompute, CUBLAS_GEMM_DEFAULT));
+void lyap_prec_tc_free(lyap_seed* sd) {
+  delete sd->prec_tc;
+  sd->prec_tc = nullptr;
+}
+
+namespace {
+
+int ensure_prec_tc(lyap_seed* sd, const WoodState& ws, int B, cudaStream_t st, PrecTcState** out) {
+  const int nk = sd->n * sd->k, r = ws.r;
+  if (!sd->prec_tc) sd->prec_tc = new PrecTcState();
+  PrecTcState& P = *sd->prec_tc;
+  if (P.r != r || P.nk != nk || P.gen != sd->tsvd_gen) {
+    P.r = r;
+    P.nk = nk;
+    P.gen = sd->tsvd_gen;
+    P.kpad1 = ((2 * nk + tc::BK - 1) / tc::BK) * tc::BK;
+    P.mpad2 = ((2 * nk + tc::BM - 1) / tc::BM) * tc::BM;
+    P.kpad2 = ((2 * r + tc::BK - 1) / tc::BK) * tc::BK;
+    for (int dir = 0; dir < 2; ++dir) {
+      const float2* Bm = dir ? ws.Nl : ws.Ml;  // c = Bm^T z
+      const float2* Am = dir ? ws.Ml : ws.Nl;  // d = Am y
+      LY_TRY(P.a1h[dir].alloc((size_t)tc::BM * P.kpad1));
+      LY_TRY(P.a1l[dir].alloc((size_t)tc::BM * P.kpad1));
+      LY_TRY(P.a2h[dir].alloc((size_t)P.mpad2 * P.kpad2));
+      LY_TRY(P.a2l[dir].alloc((size_t)P.mpad2 * P.kpad2));
+      k_split_op<<<gridn((size_t)tc::BM * P.kpad1), 256, 0, st>>>(nk, r, Bm, ws.ldr, 1, tc::BM, P.kpad1,
+                                                                  P.a1h[dir].p, P.a1l[dir].p);
+      k_split_op<<<gridn((size_t)P.mpad2 * P.kpad2), 256, 0, st>>>(nk, r, Am, ws.ldr, 0, P.mpad2, P.kpad2,
+                                                                   P.a2h[dir].p, P.a2l[dir].p);
+      lyap_count_launch(2);
+      LY_CUDA(cudaGetLastError());
+      LY_TRY(tc::make_map(&P.m1[dir].a_hi, P.a1h[dir].p, tc::BM, P.kpad1, tc::BM));
+      LY_TRY(tc::make_map(&P.m1[dir].a_lo, P.a1l[dir].p, tc::BM, P.kpad1, tc::BM));
+      LY_TRY(tc::make_map(&P.m2[dir].a_hi, P.a2h[dir].p, P.mpad2, P.kpad2, tc::BM));
+      LY_TRY(tc::make_map(&P.m2[dir].a_lo, P.a2l[dir].p, P.mpad2, P.kpad2, tc::BM));
+    }
+    P.ncap = 0;  // the panels' K extents changed
+  }
+  if (B > P.ncap) {
+    const int cap = ((B + tc::BN - 1) / tc::BN) * tc::BN;
+    // K split of GEMM 1: about one CTA per SM over the batch's column tiles
+    const int want = std::max(1, 152 / (cap / tc::BN));
+    P.splits = tc::splits_for(P.kpad1, want);
+    LY_TRY(P.b1h.alloc((size_t)cap * P.kpad1));
+    LY_TRY(P.b1l.alloc((size_t)cap * P.kpad1));
+    LY_TRY(P.b2h.alloc((size_t)cap * P.kpad2));
+    LY_TRY(P.b2l.alloc((size_t)cap * P.kpad2));
+    LY_TRY(P.d1.alloc((size_t)P.splits * cap * tc::BM));
+    LY_TRY(P.d2.alloc((size_t)cap * P.mpad2));
+    // K padding of the panels stays zero (their rows are written up to 2 nk / 2 r)
+    LY_CUDA(cudaMemsetAsync(P.b1h.p, 0, P.b1h.bytes(), st));
+    LY_CUDA(cudaMemsetAsync(P.b1l.p, 0, P.b1l.bytes(), st));
+    LY_CUDA(cudaMemsetAsync(P.b2h.p, 0, P.b2h.bytes(), st));
+    LY_CUDA(cudaMemsetAsync(P.b2l.p, 0, P.b2l.bytes(), st));
+    for (int dir = 0; dir < 2; ++dir) {
+      LY_TRY(tc::make_map(&P.m1[dir].b_hi, P.b1h.p, cap, P.kpad1, tc::BN));
+      LY_TRY(tc::make_map(&P.m1[dir].b_lo, P.b1l.p, cap, P.kpad1, tc::BN));
+      LY_TRY(tc::make_map(&P.m2[dir].b_hi, P.b2h.p, cap, P.kpad2, tc::BN));
+      LY_TRY(tc::make_map(&P.m2[dir].b_lo, P.b2l.p, cap, P.kpad2, tc::BN));
+    }
+    P.ncap = cap;
+  }
+  *out = &P;
   return LYAP_OK;
 }
 
@@ -695,31 +829,35 @@ int launch_prec(lyap_seed* sd, const WoodState* ws, bool adjoint, const double* 
   const float2* Bm = ws ? (adjoint ? ws->Nl : ws->Ml) : nullptr;
   if constexpr (std::is_same<T2, float2>::value) {
     if (r > 0) {
-      // each step is its own span of the kernel accounting (the GEMMs under
-      // prec_gemm); bytes and flops per system
-      const int nk = n * K;
-      const double N = (double)nk;
-      float2* C = ws->cpart;               // r x B
-      float2* Y = C + (size_t)r * B;        // r x B
-      float2* D = Y + (size_t)r * B;        // nk x B
+      // each step is its own span of the kernel accounting (the two
+      // products under prec_gemm); flops and bytes per system
+      if (!ws->err) return LYAP_EINVAL;
+      PrecTcState* P = nullptr;
+      LY_TRY(ensure_prec_tc(sd, *ws, B, st, &P));
+      const int dir = adjoint ? 1 : 0;
+      const double N = (double)n * K;
+      const dim3 gz((n + WT - 1) / WT, B);
       int ph = prof_begin(PK_PRECOND, st);
-      k_prec_a<T2, K><<<grid, WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, In, in_ss, Out, out_ss,
-                                           0, nullptr, 0, nullptr, B);
-      prof_end(ph, st, 8.0 * N * K, 16.0 * N, 0, count);
+      k_prec_z<K><<<gz, WT, 0, st>>>(n, list, count, sd->Gdf.p, dir, vinv, In, in_ss, Out, out_ss, P->kpad1,
+                                     P->b1h.p, P->b1l.p);
+      prof_end(ph, st, 8.0 * N * K, 16.0 * N + 8.0 * N, 0, count);
       ph = prof_begin(PK_PRECGEMM, st);
-      LY_TRY(prec_gemm(sd->ctx, CUBLAS_OP_T, r, B, nk, Bm, ws->ldr, Out, (int)out_ss, C, r, st));
-      prof_end(ph, st, 8.0 * N * r, 0.0, B, nullptr);
+      const size_t dstride = (size_t)P->ncap * tc::BM;
+      LY_TRY(tc::launch_split(P->m1[dir], P->d1.p, tc::BM, 2 * r, tc::BM, P->kpad1, count, 1, B, B, P->splits, dstride,
+                              ws->err, st));
+      prof_end(ph, st, 3.0 * 2.0 * (2.0 * r) * (2.0 * N), 0.0, 0, count);
       ph = prof_begin(PK_PRECOND, st);
-      k_prec_ysys<<<B, WT, 0, st>>>(list, count, adjoint ? 1 : 0, r, ws->cinv, C, Y);
-      prof_end(ph, st, 8.0 * r * r, 8.0 * r * r + 16.0 * r, 0, count);
+      k_prec_ytc<<<B, WT, 0, st>>>(list, count, dir, r, ws->cinv, P->d1.p, tc::BM, P->splits, dstride, P->kpad2,
+                                   P->b2h.p, P->b2l.p);
+      prof_end(ph, st, 8.0 * r * r, 8.0 * r * r + 8.0 * r * P->splits, 0, count);
       ph = prof_begin(PK_PRECGEMM, st);
-      LY_TRY(prec_gemm(sd->ctx, CUBLAS_OP_N, nk, B, r, A, ws->ldr, Y, r, D, nk, st));
-      prof_end(ph, st, 8.0 * N * r, 0.0, B, nullptr);
+      LY_TRY(tc::launch(P->m2[dir], P->d2.p, P->mpad2, 2 * n * K, P->mpad2, P->kpad2, count, 1, B, B, ws->err, st));
+      prof_end(ph, st, 3.0 * 2.0 * (2.0 * N) * (2.0 * r), 0.0, 0, count);
       ph = prof_begin(PK_PRECOND, st);
-      k_prec_dsys<K><<<dim3((n + WT - 1) / WT, B), WT, 0, st>>>(n, list, count, sd->Gdf.p, adjoint ? 1 : 0, vinv, D,
-                                                                Out, out_ss);
+      k_prec_dtc<K><<<gz, WT, 0, st>>>(n, list, count, sd->Gdf.p, dir, vinv, P->d2.p, P->mpad2, Out, out_ss);
       prof_end(ph, st, 8.0 * N * K, 24.0 * N, 0, count);
       lyap_count_launch(3);
+      LY_CUDA(cudaGetLastError());
       return LYAP_OK;
     }
   }
@@ -822,6 +960,7 @@ int lyap_tsvd_prepare(lyap_seed* sd, int r, cudaStream_t st) {
   LY_CUDA(cudaGetLastError());
   LY_CUDA(cudaStreamSynchronize(st));
   sd->tsvd_r = r;
+  ++sd->tsvd_gen;  // operands built from the previous factors are stale
   sd->resident_bytes += sd->tsvd_N.bytes() + sd->tsvd_M.bytes();
   return LYAP_OK;
 }
@@ -843,10 +982,7 @@ int wood_bind(lyap_seed* sd, int r, int B, const float2* cinv_full, const int* i
 
 size_t wood_part_count(int n, int k, int B, int r) {
   const int RT = k <= 4 ? PrecTile<1>::RT : PrecTile<8>::RT;
-  r = std::max(r, 0);
-  const size_t parts = (size_t)((n + RT - 1) / RT) * (size_t)B * (size_t)r;  // row-tile partials (FP64 vectors)
-  const size_t gemm = ((size_t)2 * r + (size_t)n * k) * (size_t)B;          // C, Y, D of the GEMM form
-  return r > 0 ? std::max(parts, gemm) : 0;
+  return (size_t)((n + RT - 1) / RT) * (size_t)B * (size_t)std::max(r, 0);
 }
 
 int wood_prepare(lyap_seed* sd, int r, int B, const double* vinv, bool /*adjoint*/, WoodState& ws, cudaStream_t st) {

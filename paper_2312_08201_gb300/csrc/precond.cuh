@@ -27,7 +27,11 @@ struct WoodState {
   const float2* Nl = nullptr;  // nk x rmax (seed)
   const float2* Ml = nullptr;
   int ldr = 0;  // leading dimension (rows) of Nl/Ml = nk
+  int* err = nullptr;  // device flag for an expired bounded wait (FP32 path's tensor-core products)
 };
+
+// Tensor-core operands of the FP32 path's apply (owned by the seed).
+void lyap_prec_tc_free(lyap_seed* sd);
 
 // Offline: rank-r truncated SVD of the coupling operator (randomized, two
 // power iterations). Builds seed-resident Nl, Ml (FP32) once per rank.

@@ -25,7 +25,7 @@ enum ProfKernel {
                     // its "flops" are FP32 lane instructions
   PK_CAPBUILD = 13, // Woodbury capacitance Cap(v)^{-1} per system
   PK_OZGEMM = 14,   // integer-sliced tensor-core residual product (mixed path)
-  PK_PRECGEMM = 15, // the Woodbury apply's two GEMMs (cuBLAS, FP32 path)
+  PK_PRECGEMM = 15, // the Woodbury apply's two tcgen05 products (FP32 path)
   PK_COUNT = 16
 };
 

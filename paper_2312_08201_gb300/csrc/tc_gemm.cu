@@ -16,6 +16,7 @@
 // runs out after `wait_cycles` with nothing in flight.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -45,8 +46,9 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) { return sdesc(s
 __global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-              float* __restrict__ D, int ldd, int mrows, int ktiles, const int* __restrict__ count, int col_mult,
-              int ncols_host, int* __restrict__ err, int no_tma, long long wait_cycles) {
+              float* __restrict__ D, int ldd, int mrows, int ktiles_all, const int* __restrict__ count, int col_mult,
+              int ncols_host, int* __restrict__ err, int no_tma, long long wait_cycles, int kt_per,
+              size_t split_stride) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -59,6 +61,12 @@ __global__ void __launch_bounds__(192, 1)
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int ncols = count ? (*count) * col_mult : ncols_host;
   if (n0 >= ncols) return;  // uniform for the CTA: nothing initialised yet
+  // split K: CTA z takes k-tiles [kt0, kt0 + ktiles) and writes its own
+  // partial result at D + z * split_stride (the host makes every split
+  // non-empty)
+  const int kt0 = blockIdx.z * kt_per;
+  const int ktiles = min(kt_per, ktiles_all - kt0);
+  D += (size_t)blockIdx.z * split_stride;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -89,10 +97,11 @@ __global__ void __launch_bounds__(192, 1)
         uint8_t* st = smem + s * STAGE_BYTES;
         const uint32_t fb = sm_addr(&full[s]);
         mbar_expect_tx(fb, STAGE_BYTES);
-        tma_load_2d(sm_addr(st), &tmAh, fb, kt * BK, m0);
-        tma_load_2d(sm_addr(st + TILE_A), &tmAl, fb, kt * BK, m0);
-        tma_load_2d(sm_addr(st + 2 * TILE_A), &tmBh, fb, kt * BK, n0);
-        tma_load_2d(sm_addr(st + 2 * TILE_A + TILE_B), &tmBl, fb, kt * BK, n0);
+        const int kx = (kt0 + kt) * BK;
+        tma_load_2d(sm_addr(st), &tmAh, fb, kx, m0);
+        tma_load_2d(sm_addr(st + TILE_A), &tmAl, fb, kx, m0);
+        tma_load_2d(sm_addr(st + 2 * TILE_A), &tmBh, fb, kx, n0);
+        tma_load_2d(sm_addr(st + 2 * TILE_A + TILE_B), &tmBl, fb, kx, n0);
       }
       ctl[0] = kt;
     }
@@ -208,16 +217,34 @@ int make_map(CUtensorMap* map, const void* base, int rows, int kpad, int box_row
 
 int launch(const Maps& m, float* D, int ldd, int mrows, int mpad, int kpad, const int* count, int col_mult,
            int ncols_host, int ncols_cap, int* err, cudaStream_t st, bool inject_no_tma) {
-  if (mpad % BM != 0 || kpad % BK != 0 || ncols_cap <= 0) return LYAP_EINVAL;
+  return launch_split(m, D, ldd, mrows, mpad, kpad, count, col_mult, ncols_host, ncols_cap, 1, 0, err, st,
+                      inject_no_tma);
+}
+
+int launch_split(const Maps& m, float* D, int ldd, int mrows, int mpad, int kpad, const int* count, int col_mult,
+                 int ncols_host, int ncols_cap, int splits, size_t split_stride, int* err, cudaStream_t st,
+                 bool inject_no_tma) {
+  if (mpad % BM != 0 || kpad % BK != 0 || ncols_cap <= 0 || splits < 1) return LYAP_EINVAL;
+  const int ktiles = kpad / BK;
+  const int kt_per = (ktiles + splits - 1) / splits;
+  if ((splits - 1) * kt_per >= ktiles) return LYAP_EINVAL;  // every split takes at least one k-tile
   LY_TRY(lyap_smem_optin(reinterpret_cast<const void*>(k_tc_gemm), SMEM_BYTES));
-  dim3 grid(mpad / BM, (ncols_cap + BN - 1) / BN);
+  dim3 grid(mpad / BM, (ncols_cap + BN - 1) / BN, splits);
   // the injected wait gives up after about 50 us instead of about 2 s
   const long long wait_cycles = inject_no_tma ? 100000LL : tcu::WAIT_CYCLES;
-  k_tc_gemm<<<grid, 192, SMEM_BYTES, st>>>(m.a_hi, m.a_lo, m.b_hi, m.b_lo, D, ldd, mrows, kpad / BK, count, col_mult,
-                                          ncols_host, err, inject_no_tma ? 1 : 0, wait_cycles);
+  k_tc_gemm<<<grid, 192, SMEM_BYTES, st>>>(m.a_hi, m.a_lo, m.b_hi, m.b_lo, D, ldd, mrows, ktiles, count, col_mult,
+                                          ncols_host, err, inject_no_tma ? 1 : 0, wait_cycles, kt_per,
+                                          split_stride);
   lyap_count_launch();
   LY_CUDA(cudaGetLastError());
   return LYAP_OK;
+}
+
+int splits_for(int kpad, int want) {
+  const int ktiles = kpad / BK;
+  int s = std::max(1, std::min(want, ktiles));
+  while (s > 1 && (s - 1) * ((ktiles + s - 1) / s) >= ktiles) --s;
+  return s;
 }
 
 }  // namespace tc

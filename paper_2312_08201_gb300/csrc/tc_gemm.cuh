@@ -34,4 +34,13 @@ int make_map(CUtensorMap* map, const void* base, int rows, int kpad, int box_row
 int launch(const Maps& m, float* D, int ldd, int mrows, int mpad, int kpad, const int* count, int col_mult,
            int ncols_host, int ncols_cap, int* err, cudaStream_t st, bool inject_no_tma = false);
 
+// The same product with K split `splits` ways (grid z): split z sums its
+// share of the k-tiles and writes its partial D at D + z * split_stride
+// (floats); the caller adds the partials. Every split must get at least one
+// k-tile (splits_for picks the largest count <= want that does).
+int launch_split(const Maps& m, float* D, int ldd, int mrows, int mpad, int kpad, const int* count, int col_mult,
+                 int ncols_host, int ncols_cap, int splits, size_t split_stride, int* err, cudaStream_t st,
+                 bool inject_no_tma = false);
+int splits_for(int kpad, int want);
+
 }  // namespace tc
