@@ -244,57 +244,70 @@ size_t ritz_smem_bytes(int m, int /*smax*/) {
 // accumulated product (column-major, ld 16), reduction scratch, D(v)^{-1},
 // then C_b (s rows of N, row stride N + 1).
 
-// Lower Cholesky factor of the 16 x 16 Hermitian matrix Gf (the leading
-// s x s block; identity beyond it) in one warp: lane i keeps row i in
-// registers, and column j's entries reach the other rows by shuffles.
-// Writes L to Lf and 1 / L[j][j] to rdiag; returns nonzero when a pivot is
-// not positive.
-__device__ __forceinline__ int chol16_warp(int s, const float2* Gf, float2* Lf, float* rdiag) {
+// Lower Cholesky factor L of the leading s x s block of the Hermitian matrix
+// Gf (16 x 16, column-major, ld 16; identity beyond the block) in one warp,
+// in shared memory: at step j lane i >= j forms L(i, j), then the lanes
+// update the trailing block, a pair (i, q) with j < q <= i per lane per
+// round. Writes L to Lf (identity beyond the block, zero above the diagonal)
+// and 1 / L(j, j) to rdiag; Gf is overwritten. Returns nonzero when a pivot
+// is not positive. Loops run over s, not 16, and keep nothing in register
+// arrays (a register-array form of the same factorisation ran about 7x
+// slower inside the recycle-start kernel than on its own).
+__device__ __forceinline__ int chol16_warp(int s, float2* Gf, float2* Lf, float* rdiag) {
   const int lane = threadIdx.x & 31;
-  float2 g[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c)
-    g[c] = (lane < s && c < s) ? Gf[lane + c * 16] : make_float2(lane == c ? 1.f : 0.f, 0.f);
+  for (int e = lane; e < 256; e += 32) {
+    const int i = e & 15, c = e >> 4;
+    Lf[e] = (i >= s || c >= s) ? make_float2(i == c ? 1.f : 0.f, 0.f) : make_float2(0.f, 0.f);
+  }
+  if (lane < 16 && lane >= s) rdiag[lane] = 1.f;
+  __syncwarp();
   int bad = 0;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const float d = __shfl_sync(0xffffffffu, g[j].x, j);
+  for (int j = 0; j < s; ++j) {
+    const float d = Gf[j + j * 16].x;
     bad |= !(d > 0.f) || !isfinite(d);
     const float rs = rsqrtf(d);
-    const float2 lij = lane == j ? make_float2(d * rs, 0.f)
-                                 : (lane > j ? make_float2(g[j].x * rs, g[j].y * rs) : make_float2(0.f, 0.f));
-    g[j] = lij;
+    if (lane >= j && lane < s) Lf[lane + j * 16] = lane == j ? make_float2(d * rs, 0.f) : cscale(Gf[lane + j * 16], rs);
     if (lane == 0) rdiag[j] = rs;
-#pragma unroll
-    for (int q = j + 1; q < 16; ++q) {
-      const float2 lq = make_float2(__shfl_sync(0xffffffffu, lij.x, q), __shfl_sync(0xffffffffu, lij.y, q));
-      g[q] = csub(g[q], cmul(lij, cconj(lq)));  // G(i, q) -= L(i, j) conj(L(q, j))
+    __syncwarp();
+    // trailing update G(i, q) -= L(i, j) conj(L(q, j)) for j < q <= i < s
+    const int t = s - 1 - j;  // trailing order
+    for (int e = lane; e < t * (t + 1) / 2; e += 32) {
+      int q = 0, rem = e;  // e -> (i, q) with q <= i, both counted from j + 1
+      while (rem > q) {
+        rem -= q + 1;
+        ++q;
+      }
+      const int ii = j + 1 + q, qq = j + 1 + rem;  // rem <= q
+      const float2 upd = cmul(Lf[ii + j * 16], cconj(Lf[qq + j * 16]));
+      Gf[ii + qq * 16] = csub(Gf[ii + qq * 16], upd);
     }
+    __syncwarp();
   }
-  if (lane < 16) {
-#pragma unroll
-    for (int c = 0; c < 16; ++c) Lf[lane + c * 16] = g[c];
-  }
-  __syncwarp();
   return bad;
 }
 
-// Rf = L^{-H} (upper triangular): lane c solves L x = e_c by forward
-// substitution and writes conj(x) as row c of Rf.
-__device__ __forceinline__ void linvh16_warp(const float2* Lf, const float* rdiag, float2* Rf) {
+// Rf = L^{-H} (upper triangular; identity beyond the s x s block): lane c
+// solves L x = e_c by forward substitution, in shared memory (Xs, 16 x 16),
+// and writes conj(x) as row c of Rf.
+__device__ __forceinline__ void linvh16_warp(int s, const float2* Lf, const float* rdiag, float2* Xs, float2* Rf) {
   const int lane = threadIdx.x & 31;
-  if (lane >= 16) return;
-  float2 x[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    float2 acc = make_float2(i == lane ? 1.f : 0.f, 0.f);
-#pragma unroll
-    for (int p = 0; p < i; ++p) acc = csub(acc, cmul(Lf[i + p * 16], x[p]));
-    const float r = rdiag[i];
-    x[i] = make_float2(acc.x * r, acc.y * r);
+  for (int e = lane; e < 256; e += 32) {
+    const int i = e & 15, c = e >> 4;
+    Rf[e] = (i >= s || c >= s) ? make_float2(i == c ? 1.f : 0.f, 0.f) : make_float2(0.f, 0.f);
   }
-#pragma unroll
-  for (int i = 0; i < 16; ++i) Rf[lane + i * 16] = cconj(x[i]);
+  __syncwarp();
+  if (lane < s) {
+    const int c = lane;
+    for (int i = c; i < s; ++i) {
+      float2 acc = make_float2(i == c ? 1.f : 0.f, 0.f);
+      for (int p = c; p < i; ++p) acc = csub(acc, cmul(Lf[i + p * 16], Xs[p + c * 16]));
+      const float r = rdiag[i];
+      const float2 x = make_float2(acc.x * r, acc.y * r);
+      Xs[i + c * 16] = x;
+      Rf[c + i * 16] = cconj(x);
+    }
+  }
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(RS_T) k_recstart32(int n, int k, int s, const int* __restrict__ list,
@@ -364,10 +377,10 @@ __global__ void __launch_bounds__(RS_T) k_recstart32(int n, int k, int s, const 
       }
     }
     __syncthreads();
-    // G = L L^H, Rf = L^{-H}
+    // G = L L^H, Rf = L^{-H} (the Gram's space is free once L is formed)
     if (warp == 0) {
       const int bad = chol16_warp(s, Gf, Lf, rdiag);
-      linvh16_warp(Lf, rdiag, Rf);
+      linvh16_warp(s, Lf, rdiag, Gf, Rf);
       if (bad && lane == 0) fail[0] = 1;
     }
     __syncthreads();
