@@ -5,8 +5,9 @@
     solved as one lockstep batch;
   * serving: two 400-mass seeds of the serving workload through the server.
 Outputs are sampled against the oracle (one solve at n = 2000 costs about
-half a minute of CPU), the rest against the FP64 GPU path and against
-central differences.
+half a minute of CPU: gradients at the first and last vector, the trace at
+a middle one), the rest against the FP64 GPU path and against central
+differences.
 Tolerances: 1e-10 (FP64 traces), 1e-8 (mixed traces), gradients 1e-8
 (FP64) / 1e-6 (mixed) relative to the largest component, central
 differences 1e-5.
@@ -39,11 +40,18 @@ def test_differentiation_workload_full_size(ctx):
     assert (np.abs(g16 - g64).max(axis=1) <= 1e-6 * scale).all()
     # the oracle on the structured problem (f and its gradient are invariant
     # under the orthogonal similarity)
+    # at the first, a middle and the last of the 256 vectors
     ps, _ = workload_differentiation(dense=False)
-    fo, go = oracle.gradient(ps.A0, ps.U, ps.V, ps.G, ps.E, vs[0])
-    assert rel_err(f64[0], fo) <= 1e-10
-    assert rel_err(f16[0], fo) <= 1e-8
-    assert np.abs(g64[0] - go).max() <= 1e-8 * np.abs(go).max()
+    for i in (0, len(vs) - 1):
+        fo, go = oracle.gradient(ps.A0, ps.U, ps.V, ps.G, ps.E, vs[i])
+        assert rel_err(f64[i], fo) <= 1e-10, i
+        assert rel_err(f16[i], fo) <= 1e-8, i
+        assert np.abs(g64[i] - go).max() <= 1e-8 * np.abs(go).max(), i
+        assert np.abs(g16[i] - go).max() <= 1e-6 * np.abs(go).max(), i
+    i = len(vs) // 2
+    fo = oracle.trace_EX(ps.A0, ps.U, ps.V, ps.G, ps.E, vs[i])
+    assert rel_err(f64[i], fo) <= 1e-10
+    assert rel_err(f16[i], fo) <= 1e-8
     # central differences of GPU traces
     v = vs[1]
     for j in range(p.k):
