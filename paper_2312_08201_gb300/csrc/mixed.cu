@@ -199,16 +199,19 @@ __global__ void k_fill_shared(int nsys, size_t N, const double2* __restrict__ sr
 
 int gx(size_t N) { return (int)std::max<size_t>(1, std::min<size_t>((N + 255) / 256, 64)); }
 
-int ensure_cols(lyap_seed* sd, int ncols) {
+int ensure_cols(lyap_seed* sd, int ncols, cudaStream_t st) {
   MixedState& ms = *sd->mixed;
   if (ncols <= ms.ncap) return LYAP_OK;
   const int cap = ((ncols + tc::BN - 1) / tc::BN) * tc::BN;
   LY_TRY(ms.Bhi.alloc((size_t)cap * ms.kpad));
   LY_TRY(ms.Blo.alloc((size_t)cap * ms.kpad));
   LY_TRY(ms.D.alloc((size_t)cap * ms.mpad));
-  LY_CUDA(cudaMemset(ms.D.p, 0, ms.D.bytes()));      // defined even where a timed-out GEMM wrote nothing
-  LY_CUDA(cudaMemset(ms.Bhi.p, 0, ms.Bhi.bytes()));  // K padding stays zero
-  LY_CUDA(cudaMemset(ms.Blo.p, 0, ms.Blo.bytes()));
+  // on the solve's own stream: a memset on the legacy default stream is not
+  // ordered with the context's non-blocking stream and could land after the
+  // panel or the product it is meant to precede
+  LY_CUDA(cudaMemsetAsync(ms.D.p, 0, ms.D.bytes(), st));      // defined even where a timed-out GEMM wrote nothing
+  LY_CUDA(cudaMemsetAsync(ms.Bhi.p, 0, ms.Bhi.bytes(), st));  // K padding stays zero
+  LY_CUDA(cudaMemsetAsync(ms.Blo.p, 0, ms.Blo.bytes(), st));
   LY_TRY(tc::make_map(&ms.maps.b_hi, ms.Bhi.p, cap, ms.kpad, tc::BN));
   LY_TRY(tc::make_map(&ms.maps.b_lo, ms.Blo.p, cap, ms.kpad, tc::BN));
   ms.ncap = cap;
@@ -220,7 +223,7 @@ int mixed_apply(lyap_seed* sd, bool adjoint, const double* vinv, const int* list
                 const T2* In, size_t in_ss, T2* Out, size_t out_ss, int mode, cudaStream_t st) {
   MixedState& ms = *sd->mixed;
   const int n = sd->n, k = sd->k, kk = k * k;
-  LY_TRY(ensure_cols(sd, nsys * kk * ms.cm));
+  LY_TRY(ensure_cols(sd, nsys * kk * ms.cm, st));
   const float2* P1 = adjoint ? ms.Vb32.p : ms.Ub32.p;
   const float2* P2 = adjoint ? ms.Ub32.p : ms.Vb32.p;
   dim3 g((n + 255) / 256, nsys);

@@ -206,7 +206,7 @@ KrylovWS<T2>::~KrylovWS() {
 }
 
 template <typename T2>
-int KrylovWS<T2>::ensure(int B_, int N_, int m_, int s_) {
+int KrylovWS<T2>::ensure(int B_, int N_, int m_, int s_, cudaStream_t st) {
   if (B_ <= B && N_ == N && m_ == m && s_ == smax && V.p) return LYAP_OK;
   B = B_;
   N = N_;
@@ -250,7 +250,7 @@ int KrylovWS<T2>::ensure(int B_, int N_, int m_, int s_) {
   LY_TRY(hasrec.alloc(Bs));
   LY_TRY(rflag.alloc(Bs));
   LY_TRY(kerr.alloc(1));
-  LY_CUDA(cudaMemset(kerr.p, 0, sizeof(int)));
+  LY_CUDA(cudaMemsetAsync(kerr.p, 0, sizeof(int), st));  // ordered with the solve on st
   return LYAP_OK;
 }
 
@@ -362,7 +362,7 @@ int gcrodr_chunk(const SysOp<T2>& op, int B, const T2* rhs, size_t rhs_ss, Recyc
       rec.c0_valid = true;
     }
   }
-  LY_TRY(ws.ensure(B, N, m, s));
+  LY_TRY(ws.ensure(B, N, m, s, st));
   const int smax = ws.smax;
   const int LD = m + smax + 1;
   const size_t NS = (size_t)N;

@@ -54,7 +54,7 @@ struct KrylovWS {
   int* poll_host = nullptr;  // POLL_RING ints, pinned and mapped
   int* poll_dev = nullptr;   // device view of poll_host
   cudaEvent_t poll_ev[POLL_RING] = {};
-  int ensure(int B, int N, int m, int s);
+  int ensure(int B, int N, int m, int s, cudaStream_t st);
   int ensure_side();
   int ensure_poll();
   size_t bytes() const;
