@@ -109,8 +109,10 @@ extern "C" int lyap_check_explicit(lyap_seed* sd, int nv, const double* v, const
   const size_t nn = (size_t)n * n, N = (size_t)n * k;
   std::vector<double> hv((size_t)nv * k);
   const cudaMemcpyKind kind = mem_kind == LYAP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  LY_CUDA(cudaMemcpy(hv.data(), v, sizeof(double) * hv.size(),
-                     mem_kind == LYAP_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost));
+  // on the context's stream, like every other input of the call
+  LY_CUDA(cudaMemcpyAsync(hv.data(), v, sizeof(double) * hv.size(),
+                          mem_kind == LYAP_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost, st));
+  LY_CUDA(cudaStreamSynchronize(st));
   DevBuf<double> dA, dU, dV, dG, dE, dv, GG, Xr, X0r, T, M, K1, R, Av;
   DevBuf<double2> Gc, Gh, Z1, Z2, WU, UW, Wd;
   LY_TRY(dA.alloc(nn));
